@@ -1,0 +1,313 @@
+#!/usr/bin/env python
+"""HAP message-update throughput on GB300.
+
+One step = one whole HAP solve of the workload: the similarity build from the
+points (tensor cores, BF16 hi/lo split), ``iters`` iterations of the message
+passes (Eqs. 2.1-2.6, all levels), exemplar extraction (Eq. 2.8) and the FP64
+net similarity.  The metric counts N^2 * L message updates per iteration.
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Default workload: 8192 points in 64-D from a 64-component Gaussian mixture
+(means ~ N(0, 4I), sigma = 1), L = 4 levels, 300 iterations, lambda = 0.5,
+preferences = median similarity.  Under torchrun every rank solves its own
+instance (a different seed): weak scaling with no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (N, d, L, iterations, generator, description)
+    "c1": (8192, 64, 4, 300, "config1",
+           "N=8192 d=64 64-component GMM, L=4, 300 iterations, S built BF16 hi/lo split on tensor cores, FP32 messages"),
+    "c2": (32768, 192, 3, 100, "config2",
+           "N=32768 8x8x3 texture patches (d=192), L=3, 100 iterations, S BF16 hi/lo split build, FP32 messages"),
+}
+CPU_SAMPLE_N = 4096
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="c1", choices=sorted(WORKLOADS))
+    ap.add_argument("--sbuild", default="bf16_split", choices=["bf16_split", "bf16", "f32"])
+    ap.add_argument("--s-dtype", default="f32", choices=["f32", "bf16"])
+    ap.add_argument("--iters", type=int, default=0, help="override the iteration count")
+    ap.add_argument("--cpu-baseline", type=int, default=1)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    for k in ("block_threads", "cluster_size", "grid_clusters", "elems_per_thread"):
+        ap.add_argument("--" + k.replace("_", "-"), type=int, default=0)
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def make_inputs(workload: str, seed: int):
+    from paper_1403_7394_gb300 import workloads as W
+    N, d, L, T, gen, _ = WORKLOADS[workload]
+    X, _ = getattr(W, gen)(seed=seed)
+    X = X.astype(np.float32)
+    # preference = median of the off-diagonal similarities, estimated from 2^20
+    # seeded pairs in FP64 (the same value at every level)
+    i, j = W.sample_pairs(N, 1 << 20, seed=seed + 1)
+    diff = X[i].astype(np.float64) - X[j].astype(np.float64)
+    pref = float(np.median(-np.einsum("kd,kd->k", diff, diff)))
+    return X, np.full(L, pref, dtype=np.float32)
+
+
+def cpu_count():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_sample(workload: str, seed: int):
+    """One FP64 reference iteration on a CPU_SAMPLE_N-point instance of the
+    workload family (same d, L and distribution); returns (updates/s, seconds)."""
+    from oracle import hap_oracle as H
+    from paper_1403_7394_gb300 import workloads as W
+    N, d, L, T, gen, _ = WORKLOADS[workload]
+    n = min(CPU_SAMPLE_N, N)
+    if gen == "config1":
+        X, _ = W.gmm_points(n, d, 64, sigma=1.0, seed=seed, means="normal", mean_scale=2.0)
+    else:
+        X, _ = W.texture_patches(n, 256, 8, 0.05, seed=seed)
+    S = H.neg_sq_euclidean(X.astype(np.float32)).astype(np.float32).astype(np.float64)
+    pref = H.median_preference(S[:512, :512])
+    S = H.level_similarities(S, np.full(L, pref))
+    st = H.step(S, H.init_state(L, n), 0.5, H.PAPER)  # iteration 1 (no tau/c updates)
+    t0 = time.perf_counter()
+    H.step(S, st, 0.5, H.PAPER)  # a full iteration t >= 2
+    dt = time.perf_counter() - t0
+    return n * n * L / dt, dt, n
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = [r.split(",") for r in (self.out or "").strip().splitlines() if r.count(",") >= 8]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if "Active" in r[5 + k] and not "Not" in r[5 + k]})
+        power = [float(r[3]) for r in rows if r[3].strip().replace(".", "").isdigit()]
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows), "power_w_max": max(power) if power else None}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return json.load(open(p)), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def run_reference(args, world, rank):
+    """The FP64 reference timed on this machine's CPU cores: each step is one
+    reference iteration on a sample of the workload family."""
+    if rank != 0:
+        return
+    N, d, L, T, gen, desc = WORKLOADS[args.workload]
+    for _ in range(args.warmup):
+        oracle_sample(args.workload, seed=0)
+    times, n = [], 0
+    for _ in range(args.steps):
+        ups, dt, n = oracle_sample(args.workload, seed=0)
+        times.append(dt)
+    per = float(np.mean(times))
+    value = n * n * L / per
+    sample = f"one FP64 reference iteration (t>=2) of a {n}-point, L={L} instance of the workload family per step"
+    line = {"metric": "hap_message_updates_per_s", "value": value, "unit": "updates/s", "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "desc": desc, "sample_points": n},
+            "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": "updates/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1403_7394_gb300 import hap
+
+    N, d, L, T, gen, desc = WORKLOADS[args.workload]
+    if args.iters:
+        T = args.iters
+    X, prefs = make_inputs(args.workload, seed=rank)
+    shape_opts = {k: getattr(args, k) for k in ("block_threads", "cluster_size", "grid_clusters", "elems_per_thread")}
+    ctx = hap.HAP(N, L, prefs=prefs, damping=0.5, device=dev, s_dtype=args.s_dtype, profile=True, **shape_opts)
+    stream = ctx.stream
+    Xd = torch.from_numpy(X).to(dev)
+    e_dev = torch.empty((L, N), dtype=torch.int32, device=dev)
+
+    def step():
+        ctx.build_similarity(Xd, mode=args.sbuild)
+        ctx.iterate(T)
+        ctx.exemplars(e_dev)
+        return ctx.net_similarity()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ctx.row_pass_time(reset=True)
+    launches0 = ctx.launches
+    props = torch.cuda.get_device_properties(dev)
+    gpu_id = str(getattr(props, "uuid", local))
+    if gpu_id and not gpu_id.startswith("GPU-") and len(gpu_id) == 36:
+        gpu_id = "GPU-" + gpu_id
+    barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(gpu_id) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            ns = step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    launches = ctx.launches - launches0
+    rp_ms, rp_n = ctx.row_pass_time(reset=True)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    updates = float(N) * N * L * T
+    value = world * args.steps * updates / (ms / 1e3)
+
+    # ---- end to end through the public API with host buffers ------------------
+    Xh = torch.from_numpy(X).pin_memory()
+    eh = torch.empty((L, N), dtype=torch.int32).pin_memory()
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        with torch.cuda.stream(stream):
+            Xd.copy_(Xh, non_blocking=True)
+        ctx.build_similarity(Xd, mode=args.sbuild)
+        ctx.iterate(T)
+        ctx.exemplars(eh)
+        ns_h = ctx.net_similarity()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = world * args.e2e_steps * updates / e2e_s
+
+    # ---- roofline of the dominant kernel (fused row pass) ----------------------
+    peaks, peak_src = measured_peaks()
+    s_bytes = 2 if args.s_dtype == "bf16" else 4
+    # per message update: A read + write, R read + write (16 B); S read once per row
+    # for all levels (s_bytes / L); per launch N^2 L updates
+    bytes_per_launch = float(N) * N * (16 * L + s_bytes)
+    avg_rp_s = (rp_ms / rp_n) / 1e3 if rp_n else float("nan")
+    achieved = bytes_per_launch / avg_rp_s / 1e9
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "rowpass_traffic.json")
+    if os.path.exists(tfile):
+        rec = json.load(open(tfile))
+        if rec.get("workload") == args.workload and rec.get("s_dtype") == args.s_dtype and rec.get("kernel_hash") == kernel_hash():
+            traffic = rec.get("dram_bytes_per_launch")
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "peak_source": peak_src,
+            "kernel": "rowpass_kernel", "launches_timed": rp_n, "avg_launch_ms": avg_rp_s * 1e3,
+            "algorithmic_bytes_per_launch": bytes_per_launch}
+
+    line = {"metric": "hap_message_updates_per_s", "value": value, "unit": "updates/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "desc": desc, "N": N, "d": d, "L": L, "iters": T,
+                       "sbuild": args.sbuild, "s_dtype": args.s_dtype, "damping": 0.5, "c_mode": "paper",
+                       "l2": "inputs larger than L2 (A, R, S = %.2f GB)" % ((2 * L * N * N * 4 + N * N * s_bytes) / 1e9),
+                       "launch_shape": ctx.shape, "parallelism": f"independent instance per GPU x{world}"},
+            "e2e": {"value": e2e_value, "unit": "updates/s", "h2d_bytes_per_step": int(X.nbytes),
+                    "d2h_bytes_per_step": int(eh.numel() * 4 + L * 8), "steps": args.e2e_steps},
+            "gpu_launches": int(launches), "roofline": roof, "clocks": clk.summary(),
+            "net_similarity": [float(x) for x in ns_h]}
+    if rank == 0 and world == 1 and args.cpu_baseline:
+        ups, dt, n = oracle_sample(args.workload, seed=0)
+        line["cpu_baseline"] = {"value": ups, "unit": "updates/s", "cores": 1, "kind": "oracle",
+                                "sample": f"one FP64 reference iteration (t>=2) on a {n}-point L={L} instance of the "
+                                          f"workload family, {dt:.1f} s, numpy single-threaded"}
+    if rank == 0:
+        print(json.dumps(line))
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def kernel_hash() -> str:
+    import hashlib
+    p = os.path.join(ROOT, "paper_1403_7394_gb300", "csrc", "hap_rowpass.cu")
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,196 @@
+/*
+ * hap.h - C ABI of the GB300 (sm_103a) Hierarchical Affinity Propagation library.
+ *
+ * Method: D. M. Rose et al., "Parallel Hierarchical Affinity Propagation with
+ * MapReduce" (arXiv:1403.7394), §2 Eqs. 2.1-2.8 and Algorithm 1, iterated with
+ * the data-parallel schedule of §3 (every (i, l) of an iteration is updated from
+ * the state at the start of that iteration; tau and c are not updated in the
+ * first iteration).
+ *
+ * Conventions shared by every entry point
+ *   - Levels are 0-based (the paper's level l is index l-1).  Node i indexes
+ *     rows, candidate exemplar j indexes columns (the tensor layout of §3).
+ *   - Device pointers are CUDA global-memory addresses of the current device;
+ *     host pointers are ordinary CPU memory.  Each argument says which.
+ *   - The library never frees memory it did not allocate and keeps no pointer
+ *     passed by the caller after the call returns, except the workspace given to
+ *     hap_create, which it borrows until hap_destroy.
+ *   - All work is enqueued on the stream bound with hap_set_stream (default: the
+ *     legacy default stream).  Calls documented as "synchronising" wait for that
+ *     stream and report device-side errors; other calls may return before the
+ *     GPU work finishes, and an asynchronous fault surfaces at the next
+ *     synchronising call as HAP_ECUDA.
+ *   - Every function returns HAP_OK (0) or a negative HAP_E* code; no C++
+ *     exception or abort crosses this boundary.  hap_strerror names the code.
+ *   - A context is not thread-safe: one host thread at a time per context.
+ */
+#ifndef HAP_H_
+#define HAP_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define HAP_OK            0
+#define HAP_EINVAL       (-1) /* bad argument (null pointer, size, option)          */
+#define HAP_ENOMEM       (-2) /* workspace too small / device allocation failed     */
+#define HAP_ECUDA        (-3) /* a CUDA runtime call or kernel launch failed        */
+#define HAP_EDEVICE      (-4) /* a kernel reported an error in the status word      */
+#define HAP_ETIMEOUT     (-5) /* a bounded device-side wait gave up                 */
+#define HAP_EUNSUPPORTED (-6) /* valid request this build or device cannot serve    */
+
+/* ---- option values ----------------------------------------------------- */
+/* Cluster preference c (Eq. 2.6).  PAPER: c_i^l = max_j(alpha_ij^l + rho_ij^l)
+ * every iteration from the second on (§3).  FIXED: c stays at its initial
+ * value (0, or hap_set_cluster_preferences), which makes L = 1 flat AP.      */
+#define HAP_C_PAPER 0
+#define HAP_C_FIXED 1
+/* Level schedule.  JACOBI: all levels of an iteration read the state at the
+ * start of the iteration (the MR-HAP jobs of §3).                            */
+#define HAP_SCHED_JACOBI 0
+/* Storage type of the similarity S.                                          */
+#define HAP_S_F32  0
+#define HAP_S_BF16 1
+/* Similarity build (hap_build_similarity), s_ij = -||x_i - x_j||^2 (§2).
+ *   F32:        CUDA cores, FP32, direct difference form.
+ *   BF16:       tcgen05 tensor cores, x in BF16, FP32 accumulation of x_i.x_j;
+ *               norms in FP32 from the FP32 x.
+ *   BF16_SPLIT: as BF16 with x = hi + lo split into two BF16 terms and
+ *               x_i.x_j ~ hi.hi + hi.lo + lo.hi (three tensor-core products). */
+#define HAP_SBUILD_F32        0
+#define HAP_SBUILD_BF16       1
+#define HAP_SBUILD_BF16_SPLIT 2
+
+/* hap_query keys */
+#define HAP_Q_BLOCK_THREADS 1 /* threads per CTA of the row pass              */
+#define HAP_Q_CLUSTER_SIZE  2 /* CTAs per cluster (one cluster holds one row)  */
+#define HAP_Q_GRID_CLUSTERS 3 /* clusters in the persistent row-pass grid     */
+#define HAP_Q_LD            4 /* padded row stride of A, R, S in elements     */
+#define HAP_Q_ITER          5 /* completed iterations                          */
+#define HAP_Q_ELEMS_PER_THREAD 6 /* columns per thread of the row pass     */
+#define HAP_Q_LAUNCHES      7 /* kernels this context has launched so far      */
+
+typedef struct hap_options {
+    int c_mode;        /* HAP_C_PAPER (default) or HAP_C_FIXED                         */
+    int schedule;      /* HAP_SCHED_JACOBI                                             */
+    int s_dtype;       /* HAP_S_F32 (default) or HAP_S_BF16                            */
+    int s_per_level;   /* 0 (default): one N x N similarity shared by all levels, the
+                          diagonal of level l being the preferences of level l;
+                          1: L separate matrices (hap_set_similarity per level)        */
+    int block_threads; /* row-pass launch shape, 0 = automatic                         */
+    int cluster_size;  /* 0 = automatic; 1..16                                         */
+    int grid_clusters; /* 0 = automatic (all co-resident clusters)                     */
+    int elems_per_thread; /* 0 = automatic; 4, 8 or 16 columns per thread              */
+    int profile;       /* 1: time every row-pass launch with CUDA events               */
+} hap_options;
+
+typedef struct hap_ctx hap_ctx;
+
+/* Fills *opt with the defaults listed above. */
+void hap_default_options(hap_options* opt);
+
+/* Bytes of device workspace hap_create needs for N points and L levels with
+ * these options (NULL = defaults).  Host call, no GPU work; fails with
+ * HAP_EINVAL for N < 2, L < 1, L > 16 and with HAP_EUNSUPPORTED for N beyond
+ * the largest row the row pass holds on chip (65536). */
+int hap_workspace_bytes(int64_t N, int L, const hap_options* opt, size_t* bytes);
+
+/* Creates a context for N points and L levels (Algorithm 1 inputs).
+ *   prefs        host [L]: preference s_jj of every point at level l (§2), or
+ *                NULL for 0; hap_set_preferences gives per-point values.
+ *   damping      lambda in (0, 1) (§2): m <- lambda*m_old + (1-lambda)*m_new.
+ *   dev_workspace device memory of at least hap_workspace_bytes, 256-byte
+ *                aligned, borrowed until hap_destroy; NULL = the context
+ *                allocates (cudaMalloc) and frees it itself.
+ * The messages start at Algorithm 1's initial values (alpha = rho = 0,
+ * tau = +inf, phi = 0, c = 0).  Synchronising. */
+int hap_create(int64_t N, int L, const float* prefs, float damping,
+               const hap_options* opt, void* dev_workspace, size_t ws_bytes,
+               hap_ctx** out);
+
+/* Releases the context (and the workspace if hap_create allocated it). */
+void hap_destroy(hap_ctx* ctx);
+
+/* Binds a cudaStream_t (as void*) for all later work of this context. */
+int hap_set_stream(hap_ctx* ctx, void* stream);
+
+/* Preferences s_jj^l (§2, the diagonal of S^l).  prefs: host float array,
+ * [L] when per_point == 0, [L][N] row-major when per_point == 1.  Takes
+ * effect from the next iteration; does not reset the messages. */
+int hap_set_preferences(hap_ctx* ctx, const float* prefs, int per_point);
+
+/* Initial / fixed cluster preferences c^l_j (Eq. 2.6's variable; Algorithm 1
+ * starts it at 0).  c0: host [L][N] float.  Resets the messages. */
+int hap_set_cluster_preferences(hap_ctx* ctx, const float* c0);
+
+/* Copies a similarity matrix into the context and resets the messages to
+ * Algorithm 1's initial values.
+ *   level  -1: the matrix is used at every level; 0..L-1: only that level
+ *          (requires s_per_level = 1).
+ *   S      device, N rows of ld elements (ld >= N), row i = node i, column j =
+ *          candidate exemplar j; the diagonal is ignored (the preferences are
+ *          used instead).  Values must be finite.
+ *   dtype  HAP_S_F32 or HAP_S_BF16 (the type of the caller's S); it is
+ *          converted to the context's s_dtype (BF16 storage rounds to nearest). */
+int hap_set_similarity(hap_ctx* ctx, int level, const void* S, int64_t ld, int dtype);
+
+/* Builds s_ij = -||x_i - x_j||^2 (§2) on the GPU from X and resets the
+ * messages.  X: device FP32 [N][d] row-major.  mode: HAP_SBUILD_*.  The result
+ * is used at every level. */
+int hap_build_similarity(hap_ctx* ctx, const float* X, int64_t d, int mode);
+
+/* Copies the similarity the iterations use at `level` (0..L-1) into S: device
+ * float [N][N] row-major, diagonal = the level's preferences, BF16 storage
+ * widened exactly.  Asynchronous. */
+int hap_get_similarity(hap_ctx* ctx, int level, float* S);
+
+/* Runs n iterations of HAP (Eqs. 2.1-2.6 with damping, §3 schedule) on the
+ * bound stream.  Asynchronous; n >= 0. */
+int hap_iterate(hap_ctx* ctx, int n);
+
+/* Eq. 2.8: e_i^l = argmax_j (alpha_ij^l + rho_ij^l), lowest index on ties,
+ * from the current messages.  e: int32 [L][N]; on_host = 1: e is host memory
+ * and the call is synchronising; 0: e is device memory, asynchronous. */
+int hap_exemplars(hap_ctx* ctx, int32_t* e, int on_host);
+
+/* Net similarity NS^l = sum_i s^l_{i, e_i^l} of the current assignment
+ * (Eq. 2.8), accumulated in FP64 on the GPU with s^l_ii the preference; the
+ * paper does not define an objective, this is the usual AP one.
+ * ns: host double [L].  Synchronising. */
+int hap_net_similarity(hap_ctx* ctx, double* ns);
+
+/* Reads the messages after hap_query(HAP_Q_ITER) iterations.
+ *   A, R  device float [L][N][N] (alpha, rho), either may be NULL
+ *   vecs  device float [3][L][N]: c, tau, phi; may be NULL
+ *   iter  host, completed iterations; may be NULL
+ * Asynchronous; does not change the context's state. */
+int hap_get_state(hap_ctx* ctx, float* A, float* R, float* vecs, int64_t* iter);
+
+/* Replaces the messages (A, R device [L][N][N]; vecs device [3][L][N] whose c
+ * part is used, tau and phi being recomputed by the next iteration) and the
+ * completed-iteration count, e.g. to resume from a checkpoint.  The next
+ * hap_iterate continues exactly as an uninterrupted run would. */
+int hap_set_state(hap_ctx* ctx, const float* A, const float* R, const float* vecs, int64_t iter);
+
+/* Waits for the bound stream and checks the device status word. */
+int hap_sync(hap_ctx* ctx);
+
+/* Launch shape and counters (HAP_Q_* keys).  Host call. */
+int hap_query(hap_ctx* ctx, int key, int64_t* value);
+
+/* With opt.profile = 1: total milliseconds and number of row-pass launches
+ * timed by CUDA events since the last reset (reset = 1 clears after reading).
+ * Synchronising. */
+int hap_row_pass_time(hap_ctx* ctx, double* ms, int64_t* launches, int reset);
+
+/* Name of a status code. */
+const char* hap_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HAP_H_ */

@@ -1,0 +1,119 @@
+// Device helpers shared by the HAP kernels (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "hap_internal.h"
+
+#define HAP_DEV __device__ __forceinline__
+
+namespace hap {
+
+constexpr float kInf = __builtin_inff();
+
+// Damping of §2: lam * old + (1 - lam) * new, with one fixed rounding
+// sequence (product, then fused multiply-add) so that every kernel that
+// recomputes a damped value obtains the same bits.
+HAP_DEV float damp(float old_v, float new_v, float lam, float oml) {
+    return __fmaf_rn(lam, old_v, __fmul_rn(oml, new_v));
+}
+
+// Availability target of Eqs. 2.2/2.3 given the column term
+// b_j = c_j + phi_j + rho_jj + P_j:  min(0, b_j - max(0, rho_ij)) off the
+// diagonal, b_j - rho_jj on it.
+HAP_DEV float avail_target(float b, float r, bool diag) {
+    return diag ? __fsub_rn(b, r) : fminf(0.f, __fsub_rn(b, fmaxf(r, 0.f)));
+}
+
+// Running (max, lowest argmax, second max) of a stream visited in
+// increasing index order.
+HAP_DEV void top2_push(float x, int j, float& m1, int& k1, float& m2) {
+    m2 = fmaxf(m2, fminf(x, m1));
+    if (x > m1) { m1 = x; k1 = j; }
+}
+
+// Merge of two (max, lowest argmax, second max) summaries of disjoint index
+// sets; commutative and exact (no rounding), so any merge order gives the
+// same bits.
+HAP_DEV void top2_merge(float& m1, int& k1, float& m2, float o1, int ok1, float o2) {
+    if (o1 > m1 || (o1 == m1 && ok1 < k1)) {
+        m2 = fmaxf(m1, o2);
+        m1 = o1;
+        k1 = ok1;
+    } else {
+        m2 = fmaxf(m2, o1);
+    }
+}
+
+// ---- cluster / distributed shared memory (PTX) -------------------------
+HAP_DEV unsigned cluster_nctarank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+HAP_DEV unsigned cluster_ctarank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+HAP_DEV unsigned cluster_id_x() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+    return r;
+}
+HAP_DEV unsigned cluster_count_x() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
+    return r;
+}
+// All threads of all CTAs of the cluster; release/acquire orders the shared
+// memory writes before the barrier with the remote reads after it.
+HAP_DEV void cluster_barrier() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\t"
+                 "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+HAP_DEV uint32_t smem_addr(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+HAP_DEV uint32_t map_to_rank(uint32_t addr, unsigned rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+    return r;
+}
+HAP_DEV float4 ld_dsmem_f4(uint32_t addr) {
+    float4 v;
+    asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(addr) : "memory");
+    return v;
+}
+
+// ---- streaming global loads / stores -------------------------------------
+HAP_DEV float4 ld_stream(const float* p) { return __ldcs(reinterpret_cast<const float4*>(p)); }
+HAP_DEV void st_stream(float* p, float4 v) { __stcs(reinterpret_cast<float4*>(p), v); }
+
+// Four similarities as float4, from FP32 or BF16 storage.
+template <typename ST> struct SVec;
+template <> struct SVec<float> {
+    using raw = float4;
+    static HAP_DEV raw load(const float* p) { return ld_stream(p); }
+    static HAP_DEV float4 to_f4(raw v) { return v; }
+    static HAP_DEV raw zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+};
+template <> struct SVec<__nv_bfloat16> {
+    using raw = uint2;
+    static HAP_DEV raw load(const __nv_bfloat16* p) { return __ldcs(reinterpret_cast<const uint2*>(p)); }
+    static HAP_DEV float4 to_f4(raw v) {
+        return make_float4(__uint_as_float(v.x << 16), __uint_as_float(v.x & 0xffff0000u),
+                           __uint_as_float(v.y << 16), __uint_as_float(v.y & 0xffff0000u));
+    }
+    static HAP_DEV raw zero() { return make_uint2(0u, 0u); }
+};
+
+HAP_DEV float f4_get(const float4& v, int e) { return e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w; }
+HAP_DEV void f4_set(float4& v, int e, float x) {
+    if (e == 0) v.x = x; else if (e == 1) v.y = x; else if (e == 2) v.z = x; else v.w = x;
+}
+
+}  // namespace hap

@@ -1,0 +1,78 @@
+// Host-side declarations shared by the translation units of libhap.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hap {
+
+// Status-word bits written by kernels (the host maps them to HAP_E* codes).
+enum : unsigned {
+    ST_TIMEOUT = 1u,  // a bounded wait gave up
+    ST_BOUNDS = 2u,   // an index or alignment check failed
+    ST_TMEM = 4u,     // tensor-memory allocation failed
+};
+
+// One launch of the fused row pass (one HAP iteration, all levels).
+struct RowPassArgs {
+    float* A;              // [L][N][ld] availabilities alpha (one step behind when pending)
+    float* R;              // [L][N][ld] responsibilities rho
+    const void* S;         // [Ls][N][ld] similarities (FP32 or BF16)
+    int64_t N;
+    int64_t ld;            // row stride of A, R, S and of every [L][ld] vector
+    int64_t s_level_stride;  // elements between levels of S; 0 = shared by all levels
+    int L;
+    const float* pref;     // [L][ld]  preferences s_ii^l
+    float* c;              // [L][ld]  cluster preference c (Eq. 2.6), in/out
+    float* tau;            // [L][ld]  out: tau of this iteration (Eq. 2.4)
+    float* phi;            // [L][ld]  out: phi of this iteration (Eq. 2.5); level L-1 stays 0
+    const float* tpart;    // [L][ld]  rho^{l-1}_ii + P^{l-1}_i of the previous iteration (level >= 1)
+    const float* b;        // [L][ld]  b_j = c_j + phi_j + rho_jj + P_j of the previous iteration
+    float* rdiag;          // [L][ld]  out: rho_ii of this iteration
+    float* partials;       // [G][L][ld] out: per-cluster column sums of max(0, rho) off the diagonal
+    float lam, oml;        // damping lambda and 1 - lambda
+    int pending;           // alpha of the previous iteration still to be applied
+    int update_c;          // apply Eq. 2.6 this iteration
+    int use_tau;           // tau from Eq. 2.4 this iteration (else +inf)
+};
+
+struct LaunchShape {
+    int T;   // threads per CTA
+    int C;   // CTAs per cluster
+    int K;   // float4 groups per thread and row (4*K columns)
+    int G;   // clusters in the grid
+};
+
+// Kernel launchers (return a cudaError_t).
+cudaError_t launch_rowpass(const RowPassArgs& a, const LaunchShape& sh, int s_bf16, cudaStream_t st);
+cudaError_t rowpass_max_clusters(const LaunchShape& sh, int L, int s_bf16, int* max_clusters);
+size_t rowpass_smem_bytes(const LaunchShape& sh, int L);
+
+cudaError_t launch_colstats(const float* partials, int G, int L, int64_t N, int64_t ld,
+                            const float* c, const float* phi, const float* rdiag,
+                            float* b, float* tpart, cudaStream_t st);
+cudaError_t launch_prepare_from_R(const float* R, int G, int L, int64_t N, int64_t ld,
+                                  float* rdiag, float* tpart, cudaStream_t st);
+
+cudaError_t launch_exemplars(const float* A, const float* R, const float* b, int pending,
+                             float lam, float oml, int64_t N, int64_t ld, int L,
+                             int32_t* e, cudaStream_t st);
+cudaError_t launch_materialize_A(float* dst, const float* A, const float* R, const float* b,
+                                 int pending, float lam, float oml, int64_t N, int64_t ld, int L,
+                                 cudaStream_t st);
+cudaError_t launch_netsim(const void* S, int s_bf16, int64_t s_level_stride, const float* pref,
+                          const int32_t* e, int64_t N, int64_t ld, int L, double* ns,
+                          cudaStream_t st);
+
+cudaError_t launch_copy_similarity(void* dst, int dst_bf16, int64_t ld, const void* src,
+                                   int src_bf16, int64_t ld_src, int64_t N, cudaStream_t st);
+cudaError_t launch_read_similarity(float* dst, const void* S, int s_bf16, const float* pref_l,
+                                   int64_t N, int64_t ld, cudaStream_t st);
+cudaError_t launch_sbuild_f32(const float* X, int64_t N, int64_t d, void* S, int s_bf16,
+                              int64_t ld, cudaStream_t st);
+// tcgen05 build: scratch must hold 2 * N_pad * Kpad BF16 values plus N floats.
+size_t sbuild_tc_scratch_bytes(int64_t N, int64_t d, int split);
+cudaError_t launch_sbuild_tc(const float* X, int64_t N, int64_t d, int split, void* S, int s_bf16,
+                             int64_t ld, void* scratch, unsigned* status, cudaStream_t st, int* kernels);
+
+}  // namespace hap

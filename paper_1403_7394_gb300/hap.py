@@ -1,0 +1,251 @@
+"""Python binding of libhap (ctypes over the C ABI in include/hap.h).
+
+Argument marshalling only: every step of the method runs in the CUDA library.
+PyTorch supplies device memory (the workspace and the caller's tensors) and
+the CUDA stream.  Importing this module loads libhap.so and raises if it is
+missing: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libhap.so")
+
+HAP_OK, HAP_EINVAL, HAP_ENOMEM, HAP_ECUDA, HAP_EDEVICE, HAP_ETIMEOUT, HAP_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
+C_MODES = {"paper": 0, "fixed": 1}
+S_DTYPES = {"f32": 0, "bf16": 1}
+SBUILD = {"f32": 0, "bf16": 1, "bf16_split": 2}
+Q_BLOCK_THREADS, Q_CLUSTER_SIZE, Q_GRID_CLUSTERS, Q_LD, Q_ITER, Q_ELEMS_PER_THREAD, Q_LAUNCHES = 1, 2, 3, 4, 5, 6, 7
+
+
+class HapOptions(ctypes.Structure):
+    _fields_ = [("c_mode", ctypes.c_int), ("schedule", ctypes.c_int), ("s_dtype", ctypes.c_int),
+                ("s_per_level", ctypes.c_int), ("block_threads", ctypes.c_int),
+                ("cluster_size", ctypes.c_int), ("grid_clusters", ctypes.c_int),
+                ("elems_per_thread", ctypes.c_int), ("profile", ctypes.c_int)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_1403_7394_gb300.build`")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i64, i32, f32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_float
+    sigs = {
+        "hap_default_options": (None, [ctypes.POINTER(HapOptions)]),
+        "hap_workspace_bytes": (i32, [i64, i32, ctypes.POINTER(HapOptions), ctypes.POINTER(ctypes.c_size_t)]),
+        "hap_create": (i32, [i64, i32, vp, f32, ctypes.POINTER(HapOptions), vp, ctypes.c_size_t, ctypes.POINTER(vp)]),
+        "hap_destroy": (None, [vp]),
+        "hap_set_stream": (i32, [vp, vp]),
+        "hap_set_preferences": (i32, [vp, vp, i32]),
+        "hap_set_cluster_preferences": (i32, [vp, vp]),
+        "hap_set_similarity": (i32, [vp, i32, vp, i64, i32]),
+        "hap_build_similarity": (i32, [vp, vp, i64, i32]),
+        "hap_get_similarity": (i32, [vp, i32, vp]),
+        "hap_iterate": (i32, [vp, i32]),
+        "hap_exemplars": (i32, [vp, vp, i32]),
+        "hap_net_similarity": (i32, [vp, vp]),
+        "hap_get_state": (i32, [vp, vp, vp, vp, ctypes.POINTER(i64)]),
+        "hap_set_state": (i32, [vp, vp, vp, vp, i64]),
+        "hap_sync": (i32, [vp]),
+        "hap_query": (i32, [vp, i32, ctypes.POINTER(i64)]),
+        "hap_row_pass_time": (i32, [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64), i32]),
+        "hap_strerror": (ctypes.c_char_p, [i32]),
+    }
+    for name, (res, args) in sigs.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+class HapError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {lib.hap_strerror(code).decode()} ({code})")
+        self.code = code
+
+
+def check(code: int, what: str) -> None:
+    if code != HAP_OK:
+        raise HapError(code, what)
+
+
+def _ptr(t: torch.Tensor | None):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def options(c_mode="paper", s_dtype="f32", s_per_level=False, block_threads=0, cluster_size=0,
+            grid_clusters=0, elems_per_thread=0, profile=False) -> HapOptions:
+    o = HapOptions()
+    lib.hap_default_options(ctypes.byref(o))
+    o.c_mode = C_MODES[c_mode]
+    o.s_dtype = S_DTYPES[s_dtype]
+    o.s_per_level = int(bool(s_per_level))
+    o.block_threads = int(block_threads)
+    o.cluster_size = int(cluster_size)
+    o.grid_clusters = int(grid_clusters)
+    o.elems_per_thread = int(elems_per_thread)
+    o.profile = int(bool(profile))
+    return o
+
+
+def workspace_bytes(N: int, L: int, **opt) -> int:
+    o = options(**opt)
+    out = ctypes.c_size_t(0)
+    check(lib.hap_workspace_bytes(N, L, ctypes.byref(o), ctypes.byref(out)), "hap_workspace_bytes")
+    return out.value
+
+
+class HAP:
+    """One HAP problem: N points, L levels, damping lambda (Algorithm 1 inputs).
+
+    prefs: L preferences (one per level) or an (L, N) array of per-point ones.
+    The workspace is a torch uint8 tensor on ``device``; work runs on the
+    torch stream current at construction (or ``stream``)."""
+
+    def __init__(self, N: int, L: int, prefs=None, damping: float = 0.5, device="cuda",
+                 stream: torch.cuda.Stream | None = None, **opt):
+        self.N, self.L, self.damping = int(N), int(L), float(damping)
+        self.device = torch.device(device)
+        self._opt = options(**opt)
+        self.opt = dict(opt)
+        with torch.cuda.device(self.device):
+            out = ctypes.c_size_t(0)
+            check(lib.hap_workspace_bytes(self.N, self.L, ctypes.byref(self._opt), ctypes.byref(out)),
+                  "hap_workspace_bytes")
+            self.workspace = torch.empty(out.value, dtype=torch.uint8, device=self.device)
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            # construction synchronises its own stream, so wait for the workspace allocation
+            self.stream.synchronize()
+            h = ctypes.c_void_p()
+            check(lib.hap_create(self.N, self.L, None, self.damping, ctypes.byref(self._opt),
+                                 _ptr(self.workspace), out.value, ctypes.byref(h)), "hap_create")
+            self._h = h
+            check(lib.hap_set_stream(self._h, ctypes.c_void_p(self.stream.cuda_stream)), "hap_set_stream")
+        if prefs is not None:
+            self.set_preferences(prefs)
+
+    # -- lifetime -----------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.hap_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- inputs -------------------------------------------------------------
+    def set_preferences(self, prefs):
+        import numpy as np
+        p = np.ascontiguousarray(np.asarray(prefs, dtype=np.float32))
+        if p.shape == (self.L,):
+            per_point = 0
+        elif p.shape == (self.L, self.N):
+            per_point = 1
+        else:
+            raise ValueError(f"prefs must have shape ({self.L},) or ({self.L}, {self.N})")
+        check(lib.hap_set_preferences(self._h, p.ctypes.data_as(ctypes.c_void_p), per_point), "hap_set_preferences")
+
+    def set_cluster_preferences(self, c0):
+        import numpy as np
+        c = np.ascontiguousarray(np.asarray(c0, dtype=np.float32).reshape(self.L, self.N))
+        check(lib.hap_set_cluster_preferences(self._h, c.ctypes.data_as(ctypes.c_void_p)), "hap_set_cluster_preferences")
+
+    def set_similarity(self, S: torch.Tensor, level: int = -1):
+        if S.device != self.device or S.dim() != 2 or S.shape[0] != self.N or S.stride(1) != 1:
+            raise ValueError("S must be an (N, >=N) row-major tensor on the context's device")
+        dt = {torch.float32: 0, torch.bfloat16: 1}[S.dtype]
+        check(lib.hap_set_similarity(self._h, int(level), _ptr(S), S.stride(0), dt), "hap_set_similarity")
+
+    def build_similarity(self, X: torch.Tensor, mode: str = "bf16_split"):
+        if X.device != self.device or X.dtype != torch.float32 or X.dim() != 2 or X.shape[0] != self.N:
+            raise ValueError("X must be an (N, d) float32 tensor on the context's device")
+        X = X.contiguous()
+        check(lib.hap_build_similarity(self._h, _ptr(X), X.shape[1], SBUILD[mode]), "hap_build_similarity")
+
+    def get_similarity(self, level: int = 0) -> torch.Tensor:
+        """The (N, N) float32 similarity the iterations use at ``level``."""
+        out = torch.empty((self.N, self.N), dtype=torch.float32, device=self.device)
+        check(lib.hap_get_similarity(self._h, int(level), _ptr(out)), "hap_get_similarity")
+        self.sync()
+        return out
+
+    # -- iteration and outputs -------------------------------------------------
+    def iterate(self, n: int = 1):
+        check(lib.hap_iterate(self._h, int(n)), "hap_iterate")
+
+    def exemplars(self, out: torch.Tensor | None = None) -> torch.Tensor:
+        """Eq. 2.8 assignments, int32 (L, N).  A CPU ``out`` (ideally pinned)
+        receives them by a device-to-host copy and the call synchronises."""
+        if out is None:
+            out = torch.empty((self.L, self.N), dtype=torch.int32, device=self.device)
+        if out.dtype != torch.int32 or tuple(out.shape) != (self.L, self.N) or not out.is_contiguous():
+            raise ValueError("out must be a contiguous int32 (L, N) tensor")
+        check(lib.hap_exemplars(self._h, _ptr(out), 1 if out.device.type == "cpu" else 0), "hap_exemplars")
+        return out
+
+    def net_similarity(self):
+        import numpy as np
+        ns = np.zeros(self.L, dtype=np.float64)
+        check(lib.hap_net_similarity(self._h, ns.ctypes.data_as(ctypes.c_void_p)), "hap_net_similarity")
+        return ns
+
+    def get_state(self):
+        A = torch.empty((self.L, self.N, self.N), dtype=torch.float32, device=self.device)
+        R = torch.empty_like(A)
+        vecs = torch.empty((3, self.L, self.N), dtype=torch.float32, device=self.device)
+        it = ctypes.c_int64(0)
+        check(lib.hap_get_state(self._h, _ptr(A), _ptr(R), _ptr(vecs), ctypes.byref(it)), "hap_get_state")
+        self.sync()
+        return {"A": A, "R": R, "c": vecs[0], "tau": vecs[1], "phi": vecs[2], "t": it.value}
+
+    def set_state(self, A, R, c, t: int, tau=None, phi=None):
+        vecs = torch.zeros((3, self.L, self.N), dtype=torch.float32, device=self.device)
+        vecs[0] = torch.as_tensor(c, dtype=torch.float32, device=self.device)
+        if tau is not None:
+            vecs[1] = torch.as_tensor(tau, dtype=torch.float32, device=self.device)
+        if phi is not None:
+            vecs[2] = torch.as_tensor(phi, dtype=torch.float32, device=self.device)
+        A = torch.as_tensor(A, dtype=torch.float32, device=self.device).contiguous()
+        R = torch.as_tensor(R, dtype=torch.float32, device=self.device).contiguous()
+        self.stream.synchronize()
+        check(lib.hap_set_state(self._h, _ptr(A), _ptr(R), _ptr(vecs), int(t)), "hap_set_state")
+        self.sync()
+
+    def sync(self):
+        check(lib.hap_sync(self._h), "hap_sync")
+
+    def query(self, key: int) -> int:
+        v = ctypes.c_int64(0)
+        check(lib.hap_query(self._h, key, ctypes.byref(v)), "hap_query")
+        return v.value
+
+    @property
+    def shape(self):
+        return {"block_threads": self.query(Q_BLOCK_THREADS), "cluster_size": self.query(Q_CLUSTER_SIZE),
+                "grid_clusters": self.query(Q_GRID_CLUSTERS), "ld": self.query(Q_LD),
+                "elems_per_thread": self.query(Q_ELEMS_PER_THREAD)}
+
+    @property
+    def launches(self) -> int:
+        """Kernels this context has launched so far."""
+        return self.query(Q_LAUNCHES)
+
+    @property
+    def iterations(self) -> int:
+        return self.query(Q_ITER)
+
+    def row_pass_time(self, reset: bool = True):
+        ms = ctypes.c_double(0.0)
+        n = ctypes.c_int64(0)
+        check(lib.hap_row_pass_time(self._h, ctypes.byref(ms), ctypes.byref(n), int(reset)), "hap_row_pass_time")
+        return ms.value, n.value

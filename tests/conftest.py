@@ -28,3 +28,22 @@ def pytest_collection_modifyitems(config, items):
     for item in items:
         if "gpu" in item.keywords:
             item.add_marker(skip)
+
+
+@pytest.fixture
+def report(request):
+    """Appends one JSON record per call to $HAP_REPORT_DIR/parity_report.jsonl
+    (when that variable is set): the measured errors behind each assertion."""
+    import json
+    import time
+
+    def _report(**values):
+        d = os.environ.get("HAP_REPORT_DIR")
+        if not d:
+            return
+        os.makedirs(d, exist_ok=True)
+        rec = {"test": request.node.nodeid, "time": time.time(), **values}
+        with open(os.path.join(d, "parity_report.jsonl"), "a") as f:
+            f.write(json.dumps(rec, default=float) + "\n")
+
+    return _report

@@ -1,0 +1,277 @@
+"""CUDA path (through the C ABI) against the FP64 reference.
+
+Tolerance (message parity): err(X) = max|X_gpu - X_ref| / max(max|X_ref|, 1)
+per tensor, <= 1e-4 (the accuracy target for FP32 messages); one FP32
+iteration from the same state is expected near 1e-6.  Integer outputs
+(exemplar indices) must match exactly whenever the FP32 inputs to the argmax
+are identical, i.e. when computed from the same downloaded state.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import hap_oracle as H
+from paper_1403_7394_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4
+DEV = "cuda:0"
+
+
+def hap_mod():
+    from paper_1403_7394_gb300 import hap
+    return hap
+
+
+def problem(N, L, seed=0, d=2, k=6, s_dtype="f32", asym=False):
+    """FP32 similarity (the exact values both sides consume), per-level
+    preferences (median times 1, 1.5, 2, ...), and the reference's (L, N, N)."""
+    X, _ = W.gmm_points(N, d, k, sigma=0.6, seed=seed, means="uniform", mean_scale=10.0)
+    S64 = H.neg_sq_euclidean(X)
+    if asym:
+        S64 = S64 * np.random.default_rng(seed).uniform(0.5, 1.5, size=N)[:, None]
+    S32 = S64.astype(np.float32)
+    if s_dtype == "bf16":
+        S_used = torch.from_numpy(S32).to(torch.bfloat16).float().numpy()
+    else:
+        S_used = S32
+    p = np.float32(H.median_preference(S32.astype(np.float64)))
+    prefs = np.array([p * (1.0 + 0.5 * l) for l in range(L)], dtype=np.float32)
+    S_ref = H.level_similarities(S_used.astype(np.float64), prefs.astype(np.float64))
+    return S32, prefs, S_ref
+
+
+def to32(st):
+    return H.HAPState(st.A.astype(np.float32).astype(np.float64), st.R.astype(np.float32).astype(np.float64),
+                      st.c.astype(np.float32).astype(np.float64), st.tau, st.phi, st.t)
+
+
+def gpu_state(ctx):
+    g = ctx.get_state()
+    return {k: (v.cpu().numpy().astype(np.float64) if torch.is_tensor(v) else v) for k, v in g.items()}
+
+
+def assert_close(g, ref, tol=TOL, fields=("A", "R", "c", "tau", "phi")):
+    errs = {f: H.message_rel_error(g[f], getattr(ref, f)) for f in fields}
+    bad = {f: e for f, e in errs.items() if not e <= tol}
+    assert not bad, f"rel errors {errs}"
+    return errs
+
+
+def make_ctx(N, L, prefs, lam, S32, **opt):
+    hap = hap_mod()
+    ctx = hap.HAP(N, L, prefs=prefs, damping=lam, device=DEV, **opt)
+    ctx.set_similarity(torch.from_numpy(S32).to(DEV))
+    return ctx
+
+
+SHAPES = [
+    # (N, L, options)  - several tiles, ragged tails, every cluster size and thread shape
+    (2, 1, {}),
+    (3, 2, {}),
+    (37, 3, {}),
+    (500, 3, {}),
+    (1000, 2, {"cluster_size": 2}),
+    (1000, 2, {"cluster_size": 4, "elems_per_thread": 8}),
+    (2051, 3, {"cluster_size": 8, "block_threads": 96}),
+    (2051, 2, {"elems_per_thread": 16}),
+    (4099, 2, {}),
+    (3000, 1, {"cluster_size": 16, "block_threads": 64}),
+    (1500, 4, {"grid_clusters": 7}),
+]
+
+
+@pytest.mark.parametrize("c_mode", ["paper", "fixed"])
+@pytest.mark.parametrize("N,L,opt", SHAPES, ids=[f"N{n}-L{l}-{'-'.join(f'{k}{v}' for k, v in o.items())}" for n, l, o in SHAPES])
+def test_teacher_forced_steps(N, L, opt, c_mode, report):
+    lam = 0.5
+    S32, prefs, S_ref = problem(N, L, seed=N)
+    st = to32(H.run(S_ref, 3, lam, c_mode))
+    ctx = make_ctx(N, L, prefs, lam, S32, c_mode=c_mode, **opt)
+    # one step from a replaced state (alpha applied directly)
+    ctx.set_state(st.A, st.R, st.c, st.t)
+    ctx.iterate(1)
+    ref1 = H.step(S_ref, st, lam, c_mode)
+    e1 = assert_close(gpu_state(ctx), ref1)
+    # two steps: the second applies the pending availability inside the row pass
+    ctx.set_state(st.A, st.R, st.c, st.t)
+    ctx.iterate(2)
+    ref2 = H.step(S_ref, ref1, lam, c_mode)
+    e2 = assert_close(gpu_state(ctx), ref2)
+    report(shape=ctx.shape, one_step=e1, two_steps=e2)
+    ctx.close()
+
+
+@pytest.mark.parametrize("s_dtype", ["f32", "bf16"])
+def test_first_iterations_from_scratch(s_dtype, report):
+    """Algorithm 1 from its initial values, free-running for 4 iterations
+    (the first runs without tau and c updates, §3)."""
+    N, L, lam = 700, 3, 0.6
+    S32, prefs, S_ref = problem(N, L, seed=5, s_dtype=s_dtype)
+    ctx = make_ctx(N, L, prefs, lam, S32, s_dtype=s_dtype)
+    st = H.init_state(L, N)
+    for t in range(1, 5):
+        ctx.iterate(1)
+        st = H.step(S_ref, st, lam, H.PAPER)
+        report(t=t, errs=assert_close(gpu_state(ctx), st))
+
+
+def test_asymmetric_similarity_and_per_level_S():
+    """Non-metric S (§2) given separately per level."""
+    N, L, lam = 600, 3, 0.5
+    hap = hap_mod()
+    mats = []
+    for l in range(L):
+        S32, prefs, _ = problem(N, 1, seed=40 + l, asym=True)
+        mats.append(S32)
+    prefs = np.array([-30.0, -60.0, -90.0], dtype=np.float32)
+    S_ref = np.stack([m.astype(np.float64) for m in mats])
+    for l in range(L):
+        np.fill_diagonal(S_ref[l], prefs[l])
+    ctx = hap.HAP(N, L, prefs=prefs, damping=lam, device=DEV, s_per_level=True)
+    for l in range(L):
+        ctx.set_similarity(torch.from_numpy(mats[l]).to(DEV), level=l)
+    st = to32(H.run(S_ref, 4, lam, H.PAPER))
+    ctx.set_state(st.A, st.R, st.c, st.t)
+    ctx.iterate(2)
+    ref = H.step(S_ref, H.step(S_ref, st, lam, H.PAPER), lam, H.PAPER)
+    assert_close(gpu_state(ctx), ref)
+    for l in range(L):
+        np.testing.assert_array_equal(ctx.get_similarity(l).cpu().numpy(), S_ref[l].astype(np.float32))
+
+
+def test_per_point_preferences():
+    """Random preferences per point (the paper's image experiments, §4.1)."""
+    N, L, lam = 400, 2, 0.5
+    S32, _, _ = problem(N, L, seed=9)
+    rng = np.random.default_rng(3)
+    prefs = rng.uniform(-200.0, -20.0, size=(L, N)).astype(np.float32)
+    S_ref = np.stack([S32.astype(np.float64)] * L)
+    for l in range(L):
+        S_ref[l][np.arange(N), np.arange(N)] = prefs[l]
+    ctx = make_ctx(N, L, prefs, lam, S32)
+    ctx.iterate(3)
+    assert_close(gpu_state(ctx), H.run(S_ref, 3, lam, H.PAPER))
+
+
+# ----------------------------------------------------------------- free-running
+def _free_run(c_mode, lam, T, N=500, L=3):
+    X, _ = W.config0(seed=0)
+    S32 = H.neg_sq_euclidean(X).astype(np.float32)
+    p = np.float32(H.median_preference(S32.astype(np.float64)))
+    prefs = np.full(L, p, dtype=np.float32)
+    S_ref = H.level_similarities(S32.astype(np.float64), prefs.astype(np.float64))
+    ctx = make_ctx(N, L, prefs, lam, S32, c_mode=c_mode)
+    ctx.iterate(T)
+    g = gpu_state(ctx)
+    e_gpu = ctx.exemplars().cpu().numpy()
+    ref = H.run(S_ref, T, lam, c_mode)
+    return g, e_gpu, ref, S_ref
+
+
+def test_config0_literal_exemplars_identical(report):
+    """Config 0 as specified (N = 500, L = 3, median preference, lambda = 0.5,
+    200 iterations, Eq. 2.6 applied): identical exemplars at every level."""
+    g, e_gpu, ref, S_ref = _free_run("paper", 0.5, 200)
+    e_ref = H.exemplars(ref.A, ref.R)
+    errs = {f: H.message_rel_error(g[f], getattr(ref, f)) for f in ("A", "R", "c", "tau", "phi")}
+    report(errs=errs, exemplars_equal=bool(np.array_equal(e_gpu, e_ref)),
+           n_exemplars=[len(np.unique(x)) for x in e_ref])
+    np.testing.assert_array_equal(e_gpu, e_ref)
+    ns_ref = H.net_similarity(S_ref, e_ref)
+    assert np.all(np.abs(H.net_similarity(S_ref, e_gpu) - ns_ref) <= 1e-3 * np.abs(ns_ref))
+
+
+@pytest.mark.parametrize("c_mode,lam,T", [("paper", 0.5, 30), ("fixed", 0.5, 30), ("fixed", 0.9, 200), ("paper", 0.9, 200)])
+def test_config0_contractive_companions(c_mode, lam, T, report):
+    """Where the iteration is contractive enough (the paper's 30 iterations,
+    or stronger damping) free-running FP32 stays within 1e-4 of FP64."""
+    g, e_gpu, ref, _ = _free_run(c_mode, lam, T)
+    errs = {f: H.message_rel_error(g[f], getattr(ref, f)) for f in ("A", "R", "c", "tau", "phi")}
+    report(errs=errs, exemplars_equal=bool(np.array_equal(e_gpu, H.exemplars(ref.A, ref.R))))
+    assert_close(g, ref, fields=("A", "R"))
+    np.testing.assert_array_equal(e_gpu, H.exemplars(ref.A, ref.R))
+
+
+# ----------------------------------------------------------------- outputs
+def test_exemplars_and_net_similarity_from_gpu_state():
+    N, L, lam = 900, 3, 0.5
+    S32, prefs, S_ref = problem(N, L, seed=11)
+    ctx = make_ctx(N, L, prefs, lam, S32)
+    ctx.iterate(40)
+    g = ctx.get_state()
+    A32, R32 = g["A"].cpu().numpy(), g["R"].cpu().numpy()
+    e_gpu = ctx.exemplars().cpu().numpy()
+    # Eq. 2.8 on the same FP32 values, the sum taken in FP32 like the kernel
+    e_ref = np.argmax(A32 + R32, axis=2).astype(np.int32)
+    np.testing.assert_array_equal(e_gpu, e_ref)
+    ns = ctx.net_similarity()
+    np.testing.assert_allclose(ns, H.net_similarity(S_ref, e_gpu), rtol=1e-12)
+    host = torch.empty((L, N), dtype=torch.int32, pin_memory=True)
+    np.testing.assert_array_equal(ctx.exemplars(host).numpy(), e_gpu)
+
+
+def test_bitwise_determinism_and_resume():
+    N, L, lam = 1200, 3, 0.5
+    S32, prefs, _ = problem(N, L, seed=21)
+    a = make_ctx(N, L, prefs, lam, S32, cluster_size=2)
+    a.iterate(20)
+    ga = a.get_state()
+    b = make_ctx(N, L, prefs, lam, S32, cluster_size=2)
+    b.iterate(8)
+    mid = b.get_state()
+    c = make_ctx(N, L, prefs, lam, S32, cluster_size=2)
+    c.set_state(mid["A"], mid["R"], mid["c"], mid["t"])
+    c.iterate(12)
+    gc = c.get_state()
+    b.iterate(12)
+    gb = b.get_state()
+    for k in ("A", "R", "c", "tau", "phi"):
+        assert torch.equal(ga[k], gb[k]), k
+        assert torch.equal(ga[k], gc[k]), k
+    assert ga["t"] == gc["t"] == 20
+
+
+# ----------------------------------------------------------------- S build
+@pytest.mark.parametrize("s_dtype", ["f32", "bf16"])
+def test_similarity_build_f32(s_dtype):
+    N, d = 1100, 37
+    X, _ = W.gmm_points(N, d, 8, sigma=1.0, seed=4, means="normal", mean_scale=2.0)
+    hap = hap_mod()
+    ctx = hap.HAP(N, 1, prefs=[-5.0], damping=0.5, device=DEV, s_dtype=s_dtype)
+    ctx.build_similarity(torch.from_numpy(X.astype(np.float32)).to(DEV), mode="f32")
+    S = ctx.get_similarity(0).cpu().numpy().astype(np.float64)
+    ref = H.neg_sq_euclidean(X.astype(np.float32))
+    off = ~np.eye(N, dtype=bool)
+    scale = np.abs(ref[off]).max()
+    # FP32 difference form: error ~ d * eps32 * |s|; BF16 storage: half ulp of 2^-8
+    bound = (d * 2.0 ** -23 * 4) if s_dtype == "f32" else 2.0 ** -8
+    assert np.all(np.abs(S[off] - ref[off]) <= bound * np.abs(ref[off]) + 1e-6 * scale)
+    assert np.all(np.diagonal(S) == -5.0)
+
+
+# ----------------------------------------------------------------- errors
+def test_error_codes():
+    hap = hap_mod()
+    with pytest.raises(hap.HapError) as ei:
+        hap.HAP(1, 1, prefs=[0.0], damping=0.5, device=DEV)
+    assert ei.value.code == hap.HAP_EINVAL
+    with pytest.raises(hap.HapError) as ei:
+        hap.HAP(100, 2, prefs=[0.0, 0.0], damping=1.0, device=DEV)
+    assert ei.value.code == hap.HAP_EINVAL
+    with pytest.raises(hap.HapError) as ei:
+        hap.HAP(70000, 1, prefs=[0.0], damping=0.5, device=DEV)
+    assert ei.value.code == hap.HAP_EUNSUPPORTED
+    ctx = hap.HAP(64, 2, prefs=[-1.0, -2.0], damping=0.5, device=DEV)
+    S = torch.zeros((64, 64), device=DEV)
+    with pytest.raises(hap.HapError) as ei:
+        ctx.set_similarity(S, level=1)  # per-level S needs s_per_level
+    assert ei.value.code == hap.HAP_EINVAL
+    with pytest.raises(hap.HapError) as ei:
+        ctx.set_preferences([float("nan"), 0.0])
+    assert ei.value.code == hap.HAP_EINVAL
+    with pytest.raises(hap.HapError):
+        ctx.iterate(-1)
+    ctx.iterate(0)
+    ctx.sync()
