@@ -252,14 +252,14 @@ def main():
         ctx.build_similarity(Xd, mode=args.sbuild)
         ctx.iterate(T)
         ctx.exemplars(eh)
-        ns_h = ctx.net_similarity()
+        ns = ctx.net_similarity()
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
+    e2e_s = max(time.perf_counter() - t0, 1e-9)
     if world > 1:
         t = torch.tensor([e2e_s], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         e2e_s = float(t.item())
-    e2e_value = world * args.e2e_steps * updates / e2e_s
+    e2e_value = world * args.e2e_steps * updates / e2e_s if args.e2e_steps else None
 
     # ---- roofline of the dominant kernel (fused row pass) ----------------------
     peaks, peak_src = measured_peaks()
@@ -290,7 +290,7 @@ def main():
             "e2e": {"value": e2e_value, "unit": "updates/s", "h2d_bytes_per_step": int(X.nbytes),
                     "d2h_bytes_per_step": int(eh.numel() * 4 + L * 8), "steps": args.e2e_steps},
             "gpu_launches": int(launches), "roofline": roof, "clocks": clk.summary(),
-            "net_similarity": [float(x) for x in ns_h]}
+            "net_similarity": [float(x) for x in ns]}
     if rank == 0 and world == 1 and args.cpu_baseline:
         ups, dt, n = oracle_sample(args.workload, seed=0)
         line["cpu_baseline"] = {"value": ups, "unit": "updates/s", "cores": 1, "kind": "oracle",

@@ -84,7 +84,7 @@ typedef struct hap_options {
     int block_threads; /* row-pass launch shape, 0 = automatic                         */
     int cluster_size;  /* 0 = automatic; 1..16                                         */
     int grid_clusters; /* 0 = automatic (all co-resident clusters)                     */
-    int elems_per_thread; /* 0 = automatic; 4, 8 or 16 columns per thread              */
+    int elems_per_thread; /* 0 = automatic (8); 4, 8 or 16 columns per thread          */
     int profile;       /* 1: time every row-pass launch with CUDA events               */
 } hap_options;
 

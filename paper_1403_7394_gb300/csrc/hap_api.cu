@@ -58,34 +58,45 @@ struct Layout {
 
 int64_t padded_ld(int64_t N) { return (N + 31) / 32 * 32; }
 
-// Row-pass launch shape: one cluster holds a whole row, C CTAs x T threads x
-// 4K columns >= ld; then as many clusters as fit on the GPU at once.
+// Row-pass launch shape: one cluster holds a whole row (C CTAs x T threads x
+// 4K columns >= ld), the fewest CTAs per cluster whose shared memory fits;
+// then as many clusters as can be resident at once (persistent grid).
 int choose_shape(int64_t N, int L, const hap_options& o, LaunchShape* out) {
     const int64_t ld = padded_ld(N);
     const int64_t q4 = ld / 4;  // float4 columns
-    int K = o.elems_per_thread ? o.elems_per_thread / 4 : 1;
+    // 8 columns per thread by default: enough work per step to amortise the
+    // per-row reduction, few enough registers for 512-thread CTAs.
+    const int K = o.elems_per_thread ? o.elems_per_thread / 4 : 2;
     if (K != 1 && K != 2 && K != 4) return HAP_EINVAL;
+    if (o.elems_per_thread && o.elems_per_thread != 4 * K) return HAP_EINVAL;
     const int maxT = K == 1 ? 1024 : K == 2 ? 512 : 256;
-    int C = o.cluster_size;
-    if (C == 0) {
-        C = 1;
-        while ((int64_t)C * maxT * K < q4 && C < 16) C *= 2;
+    int dev = 0, smem_limit = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&smem_limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return HAP_ECUDA;
     }
-    if (C < 1 || C > 16) return HAP_EINVAL;
-    int T = o.block_threads;
-    if (T == 0) {
-        const int64_t per = (q4 + (int64_t)C * K - 1) / ((int64_t)C * K);
-        T = (int)((per + 31) / 32 * 32);
-        if (T < 32) T = 32;
+    const int s_elem = o.s_dtype == HAP_S_BF16 ? 2 : 4;
+    const int sizes[5] = {1, 2, 4, 8, 16};
+    for (int c : sizes) {
+        if (o.cluster_size && c != o.cluster_size) continue;
+        if (o.cluster_size < 0 || o.cluster_size > 16) return HAP_EINVAL;
+        int T = o.block_threads;
+        if (T == 0) {
+            const int64_t per = (q4 + (int64_t)c * K - 1) / ((int64_t)c * K);
+            T = (int)((per + 31) / 32 * 32);
+            if (T < 32) T = 32;
+            if (T > maxT) continue;
+        } else if (T < 32 || T > maxT || T % 32) {
+            return HAP_EINVAL;
+        }
+        if ((int64_t)c * T * K * 4 < ld) continue;
+        LaunchShape sh{T, c, K, 0};
+        if (rowpass_smem_bytes(sh, L, s_elem == 2) > (size_t)smem_limit) continue;
+        *out = sh;
+        return HAP_OK;
     }
-    if (T < 32 || T > maxT || T % 32) return HAP_EINVAL;
-    if ((int64_t)C * T * K * 4 < ld) return HAP_EUNSUPPORTED;
-    if ((size_t)L * K * T * 16 > 200 * 1024) return HAP_EUNSUPPORTED;
-    out->T = T;
-    out->C = C;
-    out->K = K;
-    out->G = 0;
-    return HAP_OK;
+    return HAP_EUNSUPPORTED;
 }
 
 int finish_shape(int64_t N, int L, const hap_options& o, LaunchShape* sh) {
@@ -166,6 +177,7 @@ int reset_messages(hap_ctx* h) {
     const size_t mat = (size_t)h->L * h->N * h->ld * sizeof(float);
     const size_t vec = (size_t)h->L * h->ld * sizeof(float);
     CU(cudaMemsetAsync(h->A, 0, mat, h->stream));
+    CU(launch_fill_alpha_padding(h->A, (int64_t)h->L * h->N, h->N, h->ld, h->stream));
     CU(cudaMemsetAsync(h->R, 0, mat, h->stream));
     CU(cudaMemcpyAsync(h->c, h->c0, vec, cudaMemcpyDeviceToDevice, h->stream));
     CU(cudaMemsetAsync(h->phi, 0, vec, h->stream));
@@ -400,6 +412,7 @@ int hap_iterate(hap_ctx* h, int n) {
     a.b = h->b;
     a.rdiag = h->rdiag;
     a.partials = h->partials;
+    a.status = h->status;
     a.lam = h->lam;
     a.oml = 1.0f - h->lam;
     const int s_bf16 = h->opt.s_dtype == HAP_S_BF16;

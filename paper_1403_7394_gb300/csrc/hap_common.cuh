@@ -89,6 +89,75 @@ HAP_DEV float4 ld_dsmem_f4(uint32_t addr) {
     return v;
 }
 
+// ---- mbarrier, bulk copies (TMA), asynchronous remote stores ---------------
+HAP_DEV void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(bar), "r"(count) : "memory");
+}
+HAP_DEV void fence_mbarrier_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+HAP_DEV void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bar), "r"(bytes) : "memory");
+}
+HAP_DEV bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile("{\n\t.reg .pred p;\n\t"
+                 "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+    return done != 0;
+}
+HAP_DEV uint64_t global_timer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Waits for the phase with the given parity to complete, for at most about
+// two seconds; on expiry records ST_TIMEOUT in the status word and returns
+// false so the caller can skip the rest of its waits and leave.
+HAP_DEV bool mbar_wait(uint32_t bar, uint32_t parity, unsigned* status) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_timer_ns();
+    for (uint32_t it = 1;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 255u) == 0u && global_timer_ns() - t0 > 2000000000ull) {
+            atomicOr(status, ST_TIMEOUT);
+            return false;
+        }
+    }
+}
+// Bulk (non-tensor) TMA copy global -> this CTA's shared memory, completing
+// `bytes` of transaction count on the mbarrier.  16-byte aligned addresses,
+// size a multiple of 16.
+HAP_DEV void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 :: "r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
+}
+// 16-byte store into a (possibly remote) CTA's shared memory that completes
+// 16 bytes of transaction count on that CTA's mbarrier.
+HAP_DEV void st_async_f4(uint32_t remote_addr, float4 v, uint32_t remote_bar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];"
+                 :: "r"(remote_addr), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "r"(remote_bar) : "memory");
+}
+
+// ---- exact warp reductions -------------------------------------------------
+HAP_DEV float redux_max(float v) {
+    float r;
+    asm volatile("redux.sync.max.f32 %0, %1, 0xffffffff;" : "=f"(r) : "f"(v));
+    return r;
+}
+// Warp-wide (max, lowest argmax, second max) and plain max, all lanes get
+// the result.  Lanes summarise disjoint index sets.
+HAP_DEV void warp_top2(float& m1, int& k1, float& m2, float& cm) {
+    const float wm1 = redux_max(m1);
+    const int wk1 = __reduce_min_sync(0xffffffffu, m1 == wm1 ? k1 : 0x7fffffff);
+    const float wm2 = redux_max((m1 == wm1 && k1 == wk1) ? m2 : m1);
+    cm = redux_max(cm);
+    m1 = wm1;
+    k1 = wk1;
+    m2 = wm2;
+}
+
 // ---- streaming global loads / stores -------------------------------------
 HAP_DEV float4 ld_stream(const float* p) { return __ldcs(reinterpret_cast<const float4*>(p)); }
 HAP_DEV void st_stream(float* p, float4 v) { __stcs(reinterpret_cast<float4*>(p), v); }
@@ -112,6 +181,7 @@ template <> struct SVec<__nv_bfloat16> {
 };
 
 HAP_DEV float f4_get(const float4& v, int e) { return e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w; }
+HAP_DEV float4 f4_splat(float x) { return make_float4(x, x, x, x); }
 HAP_DEV void f4_set(float4& v, int e, float x) {
     if (e == 0) v.x = x; else if (e == 1) v.y = x; else if (e == 2) v.z = x; else v.w = x;
 }

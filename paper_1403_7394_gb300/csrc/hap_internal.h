@@ -30,6 +30,7 @@ struct RowPassArgs {
     const float* b;        // [L][ld]  b_j = c_j + phi_j + rho_jj + P_j of the previous iteration
     float* rdiag;          // [L][ld]  out: rho_ii of this iteration
     float* partials;       // [G][L][ld] out: per-cluster column sums of max(0, rho) off the diagonal
+    unsigned* status;      // device status word (ST_* bits)
     float lam, oml;        // damping lambda and 1 - lambda
     int pending;           // alpha of the previous iteration still to be applied
     int update_c;          // apply Eq. 2.6 this iteration
@@ -46,7 +47,8 @@ struct LaunchShape {
 // Kernel launchers (return a cudaError_t).
 cudaError_t launch_rowpass(const RowPassArgs& a, const LaunchShape& sh, int s_bf16, cudaStream_t st);
 cudaError_t rowpass_max_clusters(const LaunchShape& sh, int L, int s_bf16, int* max_clusters);
-size_t rowpass_smem_bytes(const LaunchShape& sh, int L);
+size_t rowpass_smem_bytes(const LaunchShape& sh, int L, int s_bf16);
+cudaError_t launch_fill_alpha_padding(float* A, int64_t rows, int64_t N, int64_t ld, cudaStream_t st);
 
 cudaError_t launch_colstats(const float* partials, int G, int L, int64_t N, int64_t ld,
                             const float* c, const float* phi, const float* rdiag,

@@ -28,178 +28,233 @@
 
 namespace hap {
 
+constexpr int kStages = 3;  // row slices in flight per CTA (TMA ring depth)
+
+// Shared memory of one row-pass CTA: kStages x {A, R, S slices} | per-thread
+// column sums [L][K][T] float4 | exchange slots [2][C][32] float4 | mbarriers.
+__host__ __device__ inline size_t rowpass_smem_layout(int T, int K, int C, int L, int s_elem, size_t* stage_bytes,
+                                                      size_t* a_bytes) {
+    const size_t W = (size_t)4 * K * T;
+    const size_t a = (W * 4 + 127) / 128 * 128;
+    const size_t sb = (W * s_elem + 127) / 128 * 128;
+    if (stage_bytes) *stage_bytes = 2 * a + sb;
+    if (a_bytes) *a_bytes = a;
+    return kStages * (2 * a + sb) + (size_t)L * W * 4 + (size_t)2 * C * 32 * 16 + (kStages + 2) * 8;
+}
+
+template <typename ST>
+HAP_DEV float4 load_s_smem(const ST* p);
+template <>
+HAP_DEV float4 load_s_smem<float>(const float* p) { return *reinterpret_cast<const float4*>(p); }
+template <>
+HAP_DEV float4 load_s_smem<__nv_bfloat16>(const __nv_bfloat16* p) {
+    return SVec<__nv_bfloat16>::to_f4(*reinterpret_cast<const uint2*>(p));
+}
+
 template <typename ST, int K, int MAXT>
 __global__ void __launch_bounds__(MAXT, 1) rowpass_kernel(const RowPassArgs p) {
-    using SV = SVec<ST>;
-    using raw_t = typename SV::raw;
-    extern __shared__ float4 acc_s[];  // [L][K][T] per-thread column sums
-    __shared__ float4 red[2][32];      // per-warp partial (m1, m2, c, k1), double-buffered
-    __shared__ float4 cred[2];         // per-CTA partial, read by the cluster
-
+    extern __shared__ __align__(128) unsigned char sm[];
     const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = T >> 5;
     const unsigned C = cluster_nctarank(), rank = cluster_ctarank();
     const unsigned g = cluster_id_x(), G = cluster_count_x();
     const int L = p.L;
-    const int64_t N = p.N, ld = p.ld;
+    const int N = (int)p.N;
+    const int64_t ld = p.ld;
     const float lam = p.lam, oml = p.oml;
     const bool pending = p.pending != 0;
     const bool s_each_level = p.s_level_stride != 0;
     const ST* Sb = reinterpret_cast<const ST*>(p.S);
 
-    int64_t col[K];
+    // ---- shared memory carve-up ------------------------------------------------
+    size_t stage_bytes, a_bytes;
+    rowpass_smem_layout(T, K, (int)C, L, (int)sizeof(ST), &stage_bytes, &a_bytes);
+    float4* acc = reinterpret_cast<float4*>(sm + kStages * stage_bytes);  // [L][K][T]
+    float4* xbuf = acc + (size_t)L * K * T;                             // [2][C][32]
+    const uint32_t bar0 = smem_addr(xbuf + 2 * C * 32);                 // full[kStages], xfull[2]
+    const uint32_t sm0 = smem_addr(sm);
+
+    // ---- columns of this thread: slice of CTA `rank`, 4 consecutive per group
+    const int W = 4 * K * T;
+    const int slice0 = (int)rank * W;
+    const int slice_len = max(0, min(W, (int)ld - slice0));
+    int col[K];
     bool ok[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-        col[k] = (int64_t)rank * (4LL * K * T) + 4LL * (k * T + tid);
-        ok[k] = col[k] < ld;
+        col[k] = slice0 + 4 * (k * T + tid);
+        ok[k] = col[k] < (int)ld;
     }
-    for (int q = tid; q < L * K * T; q += T) acc_s[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int q = tid; q < L * K * T; q += T) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (tid == 0) {
+        for (int q = 0; q < kStages + 2; ++q) mbar_init(bar0 + 8 * q, 1);
+        fence_mbarrier_init();
+    }
+    if (C > 1) cluster_barrier(); else __syncthreads();
 
-    const int64_t my_rows = N > (int64_t)g ? (N - 1 - (int64_t)g) / G + 1 : 0;
-    const int64_t nsteps = my_rows * L;
+    const int my_rows = N > (int)g ? (N - 1 - (int)g) / (int)G + 1 : 0;
+    const int nsteps = my_rows * L;
 
-    // Registers of the step being loaded (software pipeline depth 1).
-    float4 na[K], nr[K], nb[K];
-    raw_t ns[K];
-    auto issue = [&](int64_t row, int l, bool load_s) {
-        const int64_t off = ((int64_t)l * N + row) * ld;
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-            if (ok[k]) {
-                na[k] = ld_stream(p.A + off + col[k]);
-                nr[k] = ld_stream(p.R + off + col[k]);
-                nb[k] = pending ? __ldg(reinterpret_cast<const float4*>(p.b + (int64_t)l * ld + col[k]))
-                                : make_float4(0.f, 0.f, 0.f, 0.f);
-            } else {
-                na[k] = nr[k] = nb[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-        }
-        if (load_s) {
-            const int64_t soff = (int64_t)l * p.s_level_stride + row * ld;
-#pragma unroll
-            for (int k = 0; k < K; ++k) ns[k] = ok[k] ? SV::load(Sb + soff + col[k]) : SV::zero();
+    // One elected thread streams the A, R (and, when needed, S) row slices of
+    // step q into ring stage q % kStages.
+    auto issue = [&](int q) {
+        const int row = (int)g + (q / L) * (int)G, l = q % L, st = q % kStages;
+        const bool load_s = s_each_level || l == 0;
+        const uint32_t bar = bar0 + 8 * st;
+        const uint32_t dst = sm0 + (uint32_t)(st * stage_bytes);
+        const uint32_t bytes = (uint32_t)slice_len * (8u + (load_s ? (uint32_t)sizeof(ST) : 0u));
+        mbar_arrive_expect_tx(bar, bytes);
+        if (slice_len > 0) {
+            const int64_t off = ((int64_t)l * N + row) * ld + slice0;
+            bulk_g2s(dst, p.A + off, (uint32_t)slice_len * 4u, bar);
+            bulk_g2s(dst + (uint32_t)a_bytes, p.R + off, (uint32_t)slice_len * 4u, bar);
+            if (load_s)
+                bulk_g2s(dst + 2u * (uint32_t)a_bytes, Sb + (int64_t)l * p.s_level_stride + (int64_t)row * ld + slice0,
+                         (uint32_t)slice_len * (uint32_t)sizeof(ST), bar);
         }
     };
+    if (tid == 0)
+        for (int q = 0; q < min(kStages, nsteps); ++q) issue(q);
 
-    if (nsteps > 0) issue(g, 0, true);
-    raw_t srow[K];
+    float4 srow[K];
 #pragma unroll
-    for (int k = 0; k < K; ++k) srow[k] = SV::zero();
+    for (int k = 0; k < K; ++k) srow[k] = make_float4(0.f, 0.f, 0.f, 0.f);
     float c_prev = 0.f;
-    int64_t row = g;
-    int l = 0;
+    bool bad = false;
+    int row = (int)g, l = 0;
 
-    for (int64_t s = 0; s < nsteps; ++s) {
-        float4 a[K], r[K], bb[K];
+    // Per-column b of the pending availability update and per-row scalars
+    // (preference, fixed c, tau's column part), loaded one step ahead.
+    float4 nb[K];
+    float npref = 0.f, nc = 0.f, ntp = 0.f;
+    auto prefetch = [&](int prow, int pl) {
+        const int64_t pv = (int64_t)pl * ld;
 #pragma unroll
-        for (int k = 0; k < K; ++k) { a[k] = na[k]; r[k] = nr[k]; bb[k] = nb[k]; }
-        if (s_each_level || l == 0) {
-#pragma unroll
-            for (int k = 0; k < K; ++k) srow[k] = ns[k];
-        }
-        int64_t nrow = row;
-        int nl = l + 1;
-        if (nl == L) { nl = 0; nrow += G; }
-        if (s + 1 < nsteps) issue(nrow, nl, s_each_level || nl == 0);
+        for (int k = 0; k < K; ++k)
+            nb[k] = (pending && ok[k]) ? __ldg(reinterpret_cast<const float4*>(p.b + pv + col[k])) : f4_splat(0.f);
+        npref = __ldg(p.pref + pv + prow);
+        nc = p.update_c ? 0.f : p.c[pv + prow];
+        ntp = (p.use_tau && pl > 0) ? __ldg(p.tpart + pv + prow) : 0.f;
+    };
+    if (nsteps > 0) prefetch(row, 0);
 
-        const int64_t i = row;
-        const int64_t off = ((int64_t)l * N + row) * ld;
+    for (int s = 0; s < nsteps; ++s) {
+        const int st = s % kStages;
+        const unsigned char* base = sm + (size_t)st * stage_bytes;
+        const float* sA = reinterpret_cast<const float*>(base);
+        const float* sR = reinterpret_cast<const float*>(base + a_bytes);
+        const ST* sS = reinterpret_cast<const ST*>(base + 2 * a_bytes);
+        if (!bad) bad = !mbar_wait(bar0 + 8 * st, (uint32_t)(s / kStages) & 1u, p.status);
+
+        const bool new_s = s_each_level || l == 0;
         const int64_t voff = (int64_t)l * ld;
-        const float pref_i = p.pref[voff + i];
+        const int64_t off = ((int64_t)l * N + row) * ld;
+        float4 bcur[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) bcur[k] = nb[k];
+        const float pref_i = npref, c_fixed = nc, tpart_i = ntp;
+        {
+            int prow = row, pl = l + 1;
+            if (pl == L) { pl = 0; prow += (int)G; }
+            if (s + 1 < nsteps) prefetch(prow, pl);
+        }
 
-        // ---- pass 1: pending availability, row statistics --------------------
+        // ---- pass 1: pending availability (Eqs. 2.2/2.3), row statistics ------
         float m1 = -kInf, m2 = -kInf, cm = -kInf;
         int k1 = 0x7fffffff;
-        float4 sv[K];
+        float4 rr[K], ss[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            float4 s4 = SV::to_f4(srow[k]);
-            float4 an = a[k];
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int64_t j = col[k] + e;
-                const bool diag = (j == i);
-                const float sj = diag ? pref_i : f4_get(s4, e);
-                f4_set(s4, e, sj);
-                float aj = f4_get(a[k], e);
-                const float rj = f4_get(r[k], e);
-                if (pending) aj = damp(aj, avail_target(f4_get(bb[k], e), rj, diag), lam, oml);
-                f4_set(an, e, aj);
-                if (j < N) {
-                    top2_push(__fadd_rn(aj, sj), (int)j, m1, k1, m2);
-                    cm = fmaxf(cm, __fadd_rn(aj, rj));
-                }
+            const int q = k * T + tid;
+            float4 a4 = f4_splat(-kInf), r4 = f4_splat(0.f), s4 = f4_splat(0.f);
+            if (ok[k]) {
+                a4 = reinterpret_cast<const float4*>(sA)[q];
+                r4 = reinterpret_cast<const float4*>(sR)[q];
+                if (new_s) srow[k] = load_s_smem<ST>(sS + 4 * q);
+                s4 = srow[k];
             }
-            sv[k] = s4;
-            if (pending && ok[k]) st_stream(p.A + off + col[k], an);
+            float4 an = a4;
+            const float4 b4 = bcur[k];
+            if (pending) {
+                an.x = damp(a4.x, avail_target(b4.x, r4.x, false), lam, oml);
+                an.y = damp(a4.y, avail_target(b4.y, r4.y, false), lam, oml);
+                an.z = damp(a4.z, avail_target(b4.z, r4.z, false), lam, oml);
+                an.w = damp(a4.w, avail_target(b4.w, r4.w, false), lam, oml);
+            }
+            const int dd = row - col[k];
+            if ((unsigned)dd < 4u) {  // this float4 holds the diagonal element
+                f4_set(s4, dd, pref_i);
+                if (pending) f4_set(an, dd, damp(f4_get(a4, dd), avail_target(f4_get(b4, dd), f4_get(r4, dd), true), lam, oml));
+            }
+            if (pending && ok[k] && !bad) st_stream(p.A + off + col[k], an);
+            top2_push(__fadd_rn(an.x, s4.x), col[k] + 0, m1, k1, m2);
+            top2_push(__fadd_rn(an.y, s4.y), col[k] + 1, m1, k1, m2);
+            top2_push(__fadd_rn(an.z, s4.z), col[k] + 2, m1, k1, m2);
+            top2_push(__fadd_rn(an.w, s4.w), col[k] + 3, m1, k1, m2);
+            cm = fmaxf(cm, fmaxf(fmaxf(__fadd_rn(an.x, r4.x), __fadd_rn(an.y, r4.y)),
+                                 fmaxf(__fadd_rn(an.z, r4.z), __fadd_rn(an.w, r4.w))));
+            rr[k] = r4;
+            ss[k] = s4;
         }
 
-        // ---- exact reduction: warp, CTA, cluster -----------------------------
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const float o1 = __shfl_xor_sync(0xffffffffu, m1, o);
-            const int ok1 = __shfl_xor_sync(0xffffffffu, k1, o);
-            const float o2 = __shfl_xor_sync(0xffffffffu, m2, o);
-            const float oc = __shfl_xor_sync(0xffffffffu, cm, o);
-            top2_merge(m1, k1, m2, o1, ok1, o2);
-            cm = fmaxf(cm, oc);
+        // ---- exact reduction over the cluster: warp redux, then every warp's
+        // summary sent to every CTA's shared memory (st.async + mbarrier) ------
+        warp_top2(m1, k1, m2, cm);
+        const int par = s & 1;
+        const uint32_t xbar = bar0 + 8 * (kStages + par);
+        if (lane == 0) {
+            const float4 v = make_float4(m1, m2, cm, __int_as_float(k1));
+            const uint32_t slot = smem_addr(xbuf + (par * C + rank) * 32 + warp);
+            for (unsigned q = 0; q < C; ++q) st_async_f4(map_to_rank(slot, q), v, map_to_rank(xbar, q));
         }
-        const int par = (int)(s & 1);
-        if (lane == 0) red[par][warp] = make_float4(m1, m2, cm, __int_as_float(k1));
-        __syncthreads();
+        if (tid == 0) mbar_arrive_expect_tx(xbar, (uint32_t)(C * nw * 16));
+        if (!bad) bad = !mbar_wait(xbar, (uint32_t)(s >> 1) & 1u, p.status);
         m1 = m2 = cm = -kInf;
         k1 = 0x7fffffff;
-        for (int w = 0; w < nw; ++w) {
-            const float4 v = red[par][w];
-            top2_merge(m1, k1, m2, v.x, __float_as_int(v.w), v.y);
-            cm = fmaxf(cm, v.z);
-        }
-        if (C > 1) {
-            if (tid == 0) cred[par] = make_float4(m1, m2, cm, __int_as_float(k1));
-            cluster_barrier();
-            m1 = m2 = cm = -kInf;
-            k1 = 0x7fffffff;
-            const uint32_t base = smem_addr(&cred[par]);
-            for (unsigned q = 0; q < C; ++q) {
-                const float4 v = ld_dsmem_f4(map_to_rank(base, q));
+        for (int q = lane; q < (int)C * 32; q += 32) {
+            if ((q & 31) < nw) {
+                const float4 v = xbuf[par * C * 32 + q];
                 top2_merge(m1, k1, m2, v.x, __float_as_int(v.w), v.y);
                 cm = fmaxf(cm, v.z);
             }
         }
+        warp_top2(m1, k1, m2, cm);
+        // every warp of this CTA has read stage st: refill it
+        if (tid == 0 && s + kStages < nsteps) issue(s + kStages);
 
-        // ---- inter-level messages of (i, l) ----------------------------------
-        const float cval = p.update_c ? cm : p.c[voff + i];
-        const float tauv = (p.use_tau && l > 0) ? __fadd_rn(c_prev, p.tpart[voff + i]) : kInf;
+        // ---- inter-level messages of (i, l): Eqs. 2.4-2.6 --------------------
+        const float cval = p.update_c ? cm : c_fixed;
+        const float tauv = (p.use_tau && l > 0) ? __fadd_rn(c_prev, tpart_i) : kInf;
         c_prev = cval;
-        if (rank == 0 && tid == 0) {
-            if (p.update_c) p.c[voff + i] = cval;
-            p.tau[voff + i] = tauv;
-            if (l > 0) p.phi[voff - ld + i] = m1;
+        if (rank == 0 && tid == 0 && !bad) {
+            if (p.update_c) p.c[voff + row] = cval;
+            p.tau[voff + row] = tauv;
+            if (l > 0) p.phi[voff - ld + row] = m1;
         }
 
-        // ---- pass 2: responsibilities and column sums ------------------------
+        // ---- pass 2: responsibilities (Eq. 2.1) and column sums -----------------
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            float4 rn4, add;
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int64_t j = col[k] + e;
-                const float mx = (j == (int64_t)k1) ? m2 : m1;
-                const float rh = __fadd_rn(f4_get(sv[k], e), fminf(tauv, -mx));
-                const float rn = damp(f4_get(r[k], e), rh, lam, oml);
-                f4_set(rn4, e, rn);
-                if (j == i) p.rdiag[voff + i] = rn;
-                f4_set(add, e, (j != i && j < N) ? fmaxf(rn, 0.f) : 0.f);
+            const int dk = k1 - col[k];
+            const float4 r4 = rr[k], s4 = ss[k];
+            float4 rn;
+            rn.x = damp(r4.x, __fadd_rn(s4.x, fminf(tauv, -(dk == 0 ? m2 : m1))), lam, oml);
+            rn.y = damp(r4.y, __fadd_rn(s4.y, fminf(tauv, -(dk == 1 ? m2 : m1))), lam, oml);
+            rn.z = damp(r4.z, __fadd_rn(s4.z, fminf(tauv, -(dk == 2 ? m2 : m1))), lam, oml);
+            rn.w = damp(r4.w, __fadd_rn(s4.w, fminf(tauv, -(dk == 3 ? m2 : m1))), lam, oml);
+            float4 add = make_float4(fmaxf(rn.x, 0.f), fmaxf(rn.y, 0.f), fmaxf(rn.z, 0.f), fmaxf(rn.w, 0.f));
+            const int dd = row - col[k];
+            if ((unsigned)dd < 4u) {
+                f4_set(add, dd, 0.f);
+                if (!bad) p.rdiag[voff + row] = f4_get(rn, dd);
             }
-            if (ok[k]) st_stream(p.R + off + col[k], rn4);
-            float4& acc = acc_s[(l * K + k) * T + tid];
-            acc.x = __fadd_rn(acc.x, add.x);
-            acc.y = __fadd_rn(acc.y, add.y);
-            acc.z = __fadd_rn(acc.z, add.z);
-            acc.w = __fadd_rn(acc.w, add.w);
+            if (ok[k] && !bad) st_stream(p.R + off + col[k], rn);
+            float4& a = acc[(l * K + k) * T + tid];
+            a.x = __fadd_rn(a.x, add.x);
+            a.y = __fadd_rn(a.y, add.y);
+            a.z = __fadd_rn(a.z, add.z);
+            a.w = __fadd_rn(a.w, add.w);
         }
-        row = nrow;
-        l = nl;
+        if (++l == L) { l = 0; row += (int)G; }
     }
 
     // ---- per-cluster column partials ------------------------------------------
@@ -208,10 +263,18 @@ __global__ void __launch_bounds__(MAXT, 1) rowpass_kernel(const RowPassArgs p) {
         for (int k = 0; k < K; ++k)
             if (ok[k])
                 *reinterpret_cast<float4*>(p.partials + ((int64_t)g * L + ll) * ld + col[k]) =
-                    acc_s[(ll * K + k) * T + tid];
+                    acc[(ll * K + k) * T + tid];
     }
-    // No CTA may leave while a peer can still read its shared memory.
+    // No CTA may leave while a peer can still write into its shared memory.
     if (C > 1) cluster_barrier();
+}
+
+// Columns j in [N, ld) of alpha hold -inf so that padding never wins the row
+// maxima of alpha + s and alpha + rho (no per-element masks in the row pass).
+__global__ void fill_alpha_padding_kernel(float* A, int64_t rows, int64_t N, int64_t ld) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.y + threadIdx.y;
+    if (r >= rows) return;
+    for (int64_t j = N + threadIdx.x; j < ld; j += blockDim.x) A[r * ld + j] = -kInf;
 }
 
 // P_j as the fixed-order sum of the cluster partials; b and tau's column part.
@@ -262,7 +325,7 @@ __global__ void prepare_from_R_kernel(const float* __restrict__ R, int G, int L,
 template <typename ST, int K, int MAXT>
 static cudaError_t launch_one(const RowPassArgs& a, const LaunchShape& sh, cudaStream_t st) {
     auto kern = rowpass_kernel<ST, K, MAXT>;
-    const size_t smem = rowpass_smem_bytes(sh, a.L);
+    const size_t smem = rowpass_smem_bytes(sh, a.L, sizeof(ST) == 2);
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     if (sh.C > 8) {
@@ -287,7 +350,7 @@ static cudaError_t launch_one(const RowPassArgs& a, const LaunchShape& sh, cudaS
 template <typename ST, int K, int MAXT>
 static cudaError_t max_clusters_one(const LaunchShape& sh, int L, int* out) {
     auto kern = rowpass_kernel<ST, K, MAXT>;
-    const size_t smem = rowpass_smem_bytes(sh, L);
+    const size_t smem = rowpass_smem_bytes(sh, L, sizeof(ST) == 2);
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     if (sh.C > 8) {
@@ -308,8 +371,15 @@ static cudaError_t max_clusters_one(const LaunchShape& sh, int L, int* out) {
     return cudaOccupancyMaxActiveClusters(out, kern, &cfg);
 }
 
-size_t rowpass_smem_bytes(const LaunchShape& sh, int L) {
-    return (size_t)L * sh.K * sh.T * sizeof(float4);
+size_t rowpass_smem_bytes(const LaunchShape& sh, int L, int s_bf16) {
+    return rowpass_smem_layout(sh.T, sh.K, sh.C, L, s_bf16 ? 2 : 4, nullptr, nullptr);
+}
+
+cudaError_t launch_fill_alpha_padding(float* A, int64_t rows, int64_t N, int64_t ld, cudaStream_t st) {
+    if (ld == N) return cudaSuccess;
+    const dim3 block(32, 8);
+    fill_alpha_padding_kernel<<<(unsigned)((rows + 7) / 8), block, 0, st>>>(A, rows, N, ld);
+    return cudaGetLastError();
 }
 
 #define HAP_ROWPASS_DISPATCH(FN, ...)                                               \
