@@ -187,6 +187,46 @@ int hap_query(hap_ctx* ctx, int key, int64_t* value);
  * Synchronising. */
 int hap_row_pass_time(hap_ctx* ctx, double* ms, int64_t* launches, int reset);
 
+/* Allocation-free iterations on caller-owned messages.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc - for example a plugin inside a host application that owns and
+ * pre-partitions all device memory, or a latency-sensitive loop that cannot
+ * afford cudaMalloc's implicit device-wide synchronisation.  It runs the same
+ * kernels as hap_iterate, but keeps the row pass's scratch (column partials,
+ * b, tau's column part, rho_jj, a status word) in one fixed device array of
+ * this library, hap_noalloc_scratch_bytes() bytes (about 4.3 MB), which every
+ * GPU that loads the library holds until the process exits.
+ *
+ * Limits: L * ld <= 16384 (for example N = 4096 with L = 4), where
+ * ld = N rounded up to a multiple of 32; larger problems return
+ * HAP_EUNSUPPORTED.  At most 64 row-pass clusters are used.
+ *
+ * Arguments (all device memory on the current device unless stated):
+ *   S      [N][ld] similarity shared by all levels, FP32 (s_dtype HAP_S_F32)
+ *          or BF16 (HAP_S_BF16); columns N..ld-1 must hold finite values and
+ *          the diagonal is ignored.
+ *   pref   float [L][ld]: preferences s_ii^l (first N of each row used).
+ *   A, R   float [L][N][ld] alpha and rho after t0 iterations, in/out; the
+ *          call writes -inf into A's columns N..ld-1.  After the call they
+ *          hold the messages after t0 + n iterations.
+ *   c      float [L][ld] cluster preference (in: the value after t0
+ *          iterations, or the initial / fixed c; out: after t0 + n).
+ *   tau, phi float [L][ld], out (phi's last level is set to 0).
+ *   t0     completed iterations before the call (0 = Algorithm 1's start,
+ *          A = R = 0); n iterations are run; stream is a cudaStream_t.
+ * The call is synchronising and calls no allocating routine.  The first call
+ * on each device looks up the array's device address (once per device, with
+ * that device current); make that first call before any stream capture.
+ * Every call shares the one array and leaves its contents behind; the call
+ * clears what must start at zero.  Calls that overlap on the GPU (other host
+ * threads or streams, the same device) race on the array. */
+int hap_iterate_noalloc(int64_t N, int L, float damping, int c_mode, const void* S, int s_dtype,
+                        const float* pref, float* A, float* R, float* c, float* tau, float* phi,
+                        int64_t t0, int n, void* stream);
+
+/* Size in bytes of the fixed scratch array used by hap_iterate_noalloc. */
+size_t hap_noalloc_scratch_bytes(void);
+
 /* Name of a status code. */
 const char* hap_strerror(int code);
 

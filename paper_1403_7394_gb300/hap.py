@@ -54,6 +54,8 @@ def _load():
         "hap_query": (i32, [vp, i32, ctypes.POINTER(i64)]),
         "hap_row_pass_time": (i32, [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64), i32]),
         "hap_strerror": (ctypes.c_char_p, [i32]),
+        "hap_iterate_noalloc": (i32, [i64, i32, f32, i32, vp, i32, vp, vp, vp, vp, vp, vp, i64, i32, vp]),
+        "hap_noalloc_scratch_bytes": (ctypes.c_size_t, []),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(lib, name)
@@ -249,3 +251,21 @@ class HAP:
         n = ctypes.c_int64(0)
         check(lib.hap_row_pass_time(self._h, ctypes.byref(ms), ctypes.byref(n), int(reset)), "hap_row_pass_time")
         return ms.value, n.value
+
+
+def iterate_noalloc(N: int, L: int, damping: float, c_mode: str, S: torch.Tensor, pref: torch.Tensor,
+                    A: torch.Tensor, R: torch.Tensor, c: torch.Tensor, tau: torch.Tensor, phi: torch.Tensor,
+                    t0: int, n: int, stream: torch.cuda.Stream | None = None) -> None:
+    """hap_iterate_noalloc on caller-owned tensors (padded layout, ld = N
+    rounded up to 32): S (N, ld) float32/bfloat16, pref/c/tau/phi (L, ld),
+    A/R (L, N, ld) float32.  Runs n iterations after t0, allocating nothing."""
+    ld = (N + 31) // 32 * 32
+    for name, t, shape in (("S", S, (N, ld)), ("pref", pref, (L, ld)), ("A", A, (L, N, ld)), ("R", R, (L, N, ld)),
+                           ("c", c, (L, ld)), ("tau", tau, (L, ld)), ("phi", phi, (L, ld))):
+        if tuple(t.shape) != shape or not t.is_contiguous() or t.device.type != "cuda":
+            raise ValueError(f"{name} must be a contiguous CUDA tensor of shape {shape}")
+    dt = {torch.float32: 0, torch.bfloat16: 1}[S.dtype]
+    st = stream if stream is not None else torch.cuda.current_stream(S.device)
+    check(lib.hap_iterate_noalloc(int(N), int(L), float(damping), C_MODES[c_mode], _ptr(S), dt, _ptr(pref),
+                                  _ptr(A), _ptr(R), _ptr(c), _ptr(tau), _ptr(phi), int(t0), int(n),
+                                  ctypes.c_void_p(st.cuda_stream)), "hap_iterate_noalloc")
