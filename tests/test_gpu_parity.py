@@ -265,6 +265,37 @@ def test_similarity_build_f32(s_dtype):
     assert np.all(np.diagonal(S) == -5.0)
 
 
+@pytest.mark.parametrize("mode", ["bf16_split", "bf16"])
+@pytest.mark.parametrize("N,d,s_dtype", [(1100, 37, "f32"), (1100, 64, "f32"), (700, 192, "f32"), (1100, 64, "bf16"), (129, 5, "f32")])
+def test_similarity_build_tensor_cores(mode, N, d, s_dtype, report):
+    """s_ij = 2 x_i.x_j - |x_i|^2 - |x_j|^2 with x_i.x_j on tcgen05 in BF16.
+    Error bounds from the arithmetic, with u = 2^-8 the BF16 unit roundoff:
+      split: x = hi + lo + r, |r| <= u^2 |x|; the dropped lo.lo and the r terms
+             give |dot err| <= 3 u^2 |x_i||x_j| <= 1.5 u^2 (n_i + n_j), so
+             |s err| <= 3 u^2 (n_i + n_j), allowed 2^-13 (n_i + n_j);
+      plain: |dot err| <= 2u |x_i||x_j| <= u (n_i + n_j), |s err| <= 2u (n_i + n_j);
+    plus FP32 rounding of s (and half an ulp of BF16 when S is stored in BF16)."""
+    X, _ = W.gmm_points(N, d, 8, sigma=1.0, seed=d, means="normal", mean_scale=2.0)
+    X32 = X.astype(np.float32)
+    hap = hap_mod()
+    ctx = hap.HAP(N, 1, prefs=[-5.0], damping=0.5, device=DEV, s_dtype=s_dtype)
+    ctx.build_similarity(torch.from_numpy(X32).to(DEV), mode=mode)
+    S = ctx.get_similarity(0).cpu().numpy().astype(np.float64)
+    ref = H.neg_sq_euclidean(X32)
+    nrm = np.einsum("id,id->i", X32.astype(np.float64), X32.astype(np.float64))
+    off = ~np.eye(N, dtype=bool)
+    nn = nrm[:, None] + nrm[None, :]
+    coef = 2.0 ** -13 if mode == "bf16_split" else 2.0 * 2.0 ** -8
+    bound = coef * nn + 2.0 ** -22 * np.abs(ref)
+    if s_dtype == "bf16":
+        bound = bound + 2.0 ** -8 * np.abs(ref)
+    err = np.abs(S - ref)
+    report(mode=mode, N=N, d=d, s_dtype=s_dtype, max_err_over_bound=float((err / bound)[off].max()),
+           max_rel_err=float((err / np.maximum(np.abs(ref), 1e-12))[off].max()))
+    assert np.all(err[off] <= bound[off])
+    assert np.all(np.diagonal(S) == -5.0)
+
+
 # ----------------------------------------------------------------- errors
 def test_error_codes():
     hap = hap_mod()
