@@ -269,12 +269,7 @@ def main():
     bytes_per_launch = float(N) * N * (16 * L + s_bytes)
     avg_rp_s = (rp_ms / rp_n) / 1e3 if rp_n else float("nan")
     achieved = bytes_per_launch / avg_rp_s / 1e9
-    traffic = None
-    tfile = os.path.join(ROOT, "profiles", "rowpass_traffic.json")
-    if os.path.exists(tfile):
-        rec = json.load(open(tfile))
-        if rec.get("workload") == args.workload and rec.get("s_dtype") == args.s_dtype and rec.get("kernel_hash") == kernel_hash():
-            traffic = rec.get("dram_bytes_per_launch")
+    traffic = ncu_traffic(args.workload, args.s_dtype)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "peak_source": peak_src,
             "kernel": "rowpass_kernel", "launches_timed": rp_n, "avg_launch_ms": avg_rp_s * 1e3,
@@ -301,6 +296,19 @@ def main():
     ctx.close()
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def ncu_traffic(workload: str, s_dtype: str):
+    """DRAM bytes per row-pass launch from the committed ncu summary, if it was
+    taken on this workload with the current row-pass source (else None)."""
+    import re
+    p = os.path.join(ROOT, "profiles", f"rowpass_{workload}_ncu.md")
+    if not os.path.exists(p):
+        return None
+    fields = dict(re.findall(r"^\s+(\w+): (\S+)$", open(p).read(), flags=re.M))
+    if fields.get("kernel_hash") != kernel_hash() or fields.get("s_dtype") != s_dtype:
+        return None
+    return float(fields["dram_bytes_per_launch"])
 
 
 def kernel_hash() -> str:
