@@ -252,6 +252,64 @@ def run(S, iterations: int, lam: float, c_mode: str = PAPER, c0=None,
     return st
 
 
+def step_sharded(S, st: HAPState, rows, lam: float, c_mode: str, allreduce,
+                 carry: dict | None = None):
+    """One iteration of ``step`` computed by the shard that owns ``rows`` of a
+    row-partitioned problem: every row quantity (rho, alpha, c, tau, phi of
+    node i) is computed for owned rows only, and everything another shard
+    needs - the positive column sums and the owned diagonal, c and phi values
+    (zero elsewhere) - crosses shards through ONE sum all-reduce per
+    iteration (``allreduce(x)`` returns the element-wise sum of x over all
+    shards).  Only the owned rows of st.A / st.R are read or written.
+
+    ``carry`` holds the previous iteration's reduced column statistics of rho
+    ({"P": (L, N), "Rdiag": (L, N)}); None at the first iteration of a run
+    (or after a restart, when they are recomputed with one extra reduction)."""
+    S = np.asarray(S, dtype=np.float64)
+    L, n, _ = S.shape
+    rows = np.asarray(rows)
+    t = st.t + 1
+    A, R = st.A, st.R
+    if carry is None:  # column statistics of the current rho (Eqs. 2.2-2.4 sums)
+        part = np.zeros((2, L, n))
+        for l in range(L):
+            Rp = np.maximum(R[l][rows], 0.0)
+            Rp[np.arange(rows.size), rows] = 0.0
+            part[0, l] = Rp.sum(axis=0)
+            part[1, l, rows] = R[l][rows, rows]
+        part = allreduce(part)
+        carry = {"P": part[0], "Rdiag": part[1]}
+    c = st.c.copy()
+    if t >= 2 and c_mode == PAPER:                              # Eq. 2.6, owned rows
+        c[:, rows] = np.max(A[:, rows] + R[:, rows], axis=2)
+    tau = np.full((L, n), np.inf)
+    if t >= 2:                                                  # Eq. 2.4, owned rows
+        for l in range(1, L):
+            tau[l, rows] = c[l - 1, rows] + carry["Rdiag"][l - 1, rows] + carry["P"][l - 1, rows]
+    phi = np.zeros((L, n))
+    for l in range(L - 1):                                      # Eq. 2.5, owned rows
+        phi[l, rows] = np.max(A[l + 1][rows] + S[l + 1][rows], axis=1)
+    R_new = R.copy()
+    for l in range(L):                                          # Eq. 2.1, owned rows
+        R_new[l][rows] = responsibility_update(S[l][rows], A[l][rows], R[l][rows], tau[l, rows], lam)
+    # the one exchange: column sums of the new rho, and the owned c, phi, rho_jj
+    part = np.zeros((4, L, n))
+    for l in range(L):
+        Rp = np.maximum(R_new[l][rows], 0.0)
+        Rp[np.arange(rows.size), rows] = 0.0
+        part[0, l] = Rp.sum(axis=0)
+        part[1, l, rows] = R_new[l][rows, rows]
+        part[2, l, rows] = c[l, rows]
+        part[3, l, rows] = phi[l, rows]
+    part = allreduce(part)
+    A_new = A.copy()
+    for l in range(L):                                          # Eqs. 2.2, 2.3, owned rows
+        A_new[l][rows] = availability_update(A[l][rows], R_new[l][rows], rows, part[2, l], part[3, l],
+                                             part[1, l], part[0, l], lam)
+    out = HAPState(A=A_new, R=R_new, c=part[2], tau=tau, phi=part[3], t=t)
+    return out, {"P": part[0], "Rdiag": part[1]}
+
+
 # ---------------------------------------------------------------------------
 # Outputs (Eq. 2.8) and the objective
 # ---------------------------------------------------------------------------
