@@ -320,3 +320,66 @@ def test_error_codes():
         ctx.iterate(-1)
     ctx.iterate(0)
     ctx.sync()
+
+
+# ----------------------------------------------------------------- full size
+def test_full_size_teacher_forced_sampled_rows(report):
+    """The benchmark workload (N = 8192 points in 64-D, L = 4, S from the
+    tensor-core BF16-split build) in the benchmark's default launch shape: one
+    iteration from the GPU's own state at t = 5, checked on 48 sampled rows
+    per level against the reference's equations (c, tau, phi, rho on whole
+    rows; alpha from the column statistics of the GPU's new rho)."""
+    hap = hap_mod()
+    N, d, L, lam = 8192, 64, 4, 0.5
+    X, _ = W.config1(seed=0)
+    X32 = X.astype(np.float32)
+    i, j = W.sample_pairs(N, 1 << 16, seed=1)
+    diff = X32[i].astype(np.float64) - X32[j].astype(np.float64)
+    pref = np.float32(np.median(-np.einsum("kd,kd->k", diff, diff)))
+    prefs = np.full(L, pref, dtype=np.float32)
+    ctx = hap.HAP(N, L, prefs=prefs, damping=lam, device=DEV)
+    ctx.build_similarity(torch.from_numpy(X32).to(DEV), mode="bf16_split")
+    ctx.iterate(5)
+    g0 = ctx.get_state()
+    S32 = ctx.get_similarity(0).cpu().numpy()
+    ctx.iterate(1)
+    g1 = ctx.get_state()
+    rows = np.sort(np.random.default_rng(2).choice(N, 48, replace=False))
+    A0 = g0["A"].cpu().numpy()
+    R0 = g0["R"].cpu().numpy()
+    R1 = g1["R"].cpu().numpy()
+    c0 = g0["c"].cpu().numpy().astype(np.float64)
+    S = S32.astype(np.float64)
+    # inter-level vectors of iteration 6 from the GPU's state after 5 (Eqs. 2.4-2.6)
+    c = np.stack([H.cluster_preference_update(A0[l:l + 1].astype(np.float64), R0[l:l + 1].astype(np.float64))[0]
+                  for l in range(L)])
+    Rdiag0 = np.stack([np.diagonal(R0[l]).astype(np.float64) for l in range(L)])
+    P0 = np.stack([H.positive_column_sums(R0[l].astype(np.float64)) for l in range(L)])
+    tau = np.full((L, N), np.inf)
+    for l in range(1, L):
+        tau[l] = c[l - 1] + Rdiag0[l - 1] + P0[l - 1]
+    phi = np.zeros((L, N))
+    for l in range(L - 1):
+        Sl = S.copy()
+        np.fill_diagonal(Sl, prefs[l + 1])
+        phi[l] = np.max(A0[l + 1].astype(np.float64) + Sl, axis=1)
+    errs = {}
+    for fld, ref in (("c", c), ("tau", tau), ("phi", phi)):
+        errs[fld] = H.message_rel_error(g1[fld].cpu().numpy().astype(np.float64), ref)
+    eR, eA = 0.0, 0.0
+    for l in range(L):
+        Sl = S[rows].copy()
+        Sl[np.arange(len(rows)), rows] = prefs[l]
+        Rn = H.responsibility_update(Sl, A0[l][rows].astype(np.float64), R0[l][rows].astype(np.float64),
+                                     tau[l][rows], lam)
+        eR = max(eR, H.message_rel_error(R1[l][rows].astype(np.float64), Rn))
+        # alpha of iteration 6 for the sampled rows, from the column statistics
+        # of the GPU's rho_6 (teacher forcing through the column sums)
+        R1l = R1[l].astype(np.float64)
+        An = H.availability_update(A0[l][rows].astype(np.float64), R1l[rows], rows, c[l], phi[l],
+                                   np.diagonal(R1l).copy(), H.positive_column_sums(R1l), lam)
+        eA = max(eA, H.message_rel_error(g1["A"][l][rows].cpu().numpy().astype(np.float64), An))
+    errs["R"], errs["A"] = eR, eA
+    report(shape=ctx.shape, errs=errs)
+    assert all(e <= TOL for e in errs.values()), errs
+    assert ctx.shape["elems_per_thread"] == 8 and ctx.shape["cluster_size"] == 2
