@@ -73,6 +73,7 @@ extern "C" {
 #define HAP_Q_ITER          5 /* completed iterations                          */
 #define HAP_Q_ELEMS_PER_THREAD 6 /* columns per thread of the row pass     */
 #define HAP_Q_LAUNCHES      7 /* kernels this context has launched so far      */
+#define HAP_Q_BATCH_ITEMS_PER_CTA 8 /* batch scheduling granularity (tuned)      */
 
 typedef struct hap_options {
     int c_mode;        /* HAP_C_PAPER (default) or HAP_C_FIXED                         */
@@ -140,7 +141,9 @@ int hap_set_similarity(hap_ctx* ctx, int level, const void* S, int64_t ld, int d
 
 /* Builds s_ij = -||x_i - x_j||^2 (§2) on the GPU from X and resets the
  * messages.  X: device FP32 [N][d] row-major.  mode: HAP_SBUILD_*.  The result
- * is used at every level. */
+ * is used at every level.  The tensor-core modes pack their BF16 operands into
+ * the message storage, which the workspace sizes for d <= 256; beyond that
+ * they may return HAP_EUNSUPPORTED (HAP_SBUILD_F32 has no limit). */
 int hap_build_similarity(hap_ctx* ctx, const float* X, int64_t d, int mode);
 
 /* Copies the similarity the iterations use at `level` (0..L-1) into S: device
@@ -186,6 +189,47 @@ int hap_query(hap_ctx* ctx, int key, int64_t* value);
  * timed by CUDA events since the last reset (reset = 1 clears after reading).
  * Synchronising. */
 int hap_row_pass_time(hap_ctx* ctx, double* ms, int64_t* launches, int reset);
+
+/* ---- batched instances ----------------------------------------------------
+ * Many independent HAP problems of uneven N and L advanced together: every
+ * iteration is ONE persistent row-pass launch over all instances plus one
+ * batched column-statistics launch, replayed from a CUDA graph from the second
+ * iteration on.  Instance b has N[b] points (2 <= N[b] <= 4096) and L[b] levels
+ * (1..16); rows of small instances are processed up to 16 per step by row
+ * groups of one CTA.  Same equations and schedule as hap_iterate.  The
+ * context allocates its own device memory (hap_batch_destroy frees it).
+ *   N, L   host arrays of B entries.
+ * Options used: c_mode, s_dtype (opt may be NULL). */
+typedef struct hap_batch hap_batch;
+int hap_batch_create(int B, const int64_t* N, const int* L, float damping, const hap_options* opt,
+                     hap_batch** out);
+void hap_batch_destroy(hap_batch* batch);
+int hap_batch_set_stream(hap_batch* batch, void* stream);
+/* One preference per (instance, level): host float array of sum_b L[b]
+ * entries, instance-major. */
+int hap_batch_set_preferences(hap_batch* batch, const float* prefs);
+/* Builds every instance's s_ij = -||x_i - x_j||^2 from X: device FP32
+ * [sum_b N[b]][d], instance-major rows; mode HAP_SBUILD_*.  Resets messages. */
+int hap_batch_build_similarity(hap_batch* batch, const float* X, int64_t d, int mode);
+/* Copies instance b's similarity (device, N[b] rows of ld elements, dtype
+ * HAP_S_*).  Resets the messages of every instance. */
+int hap_batch_set_similarity(hap_batch* batch, int b, const void* S, int64_t ld, int dtype);
+/* n iterations of every instance; asynchronous. */
+int hap_batch_iterate(hap_batch* batch, int n);
+/* Eq. 2.8 for every instance: int32, instance-major [sum_b L[b] N[b]]
+ * ([L[b]][N[b]] per instance); on_host as for hap_exemplars. */
+int hap_batch_exemplars(hap_batch* batch, int32_t* e, int on_host);
+/* FP64 net similarity per (instance, level): host double [sum_b L[b]].
+ * Synchronising; reports device errors. */
+int hap_batch_net_similarity(hap_batch* batch, double* ns);
+/* Instance b's messages, as hap_get_state (device buffers for N[b], L[b]). */
+int hap_batch_get_state(hap_batch* batch, int b, float* A, float* R, float* vecs, int64_t* iter);
+/* Autotuner: times one steady-state iteration for several work-split
+ * granularities (items per CTA) and keeps the fastest; resets the messages
+ * to Algorithm 1's start.  best_ms (may be NULL) receives its time. */
+int hap_batch_tune(hap_batch* batch, double* best_ms);
+int hap_batch_query(hap_batch* batch, int key, int64_t* value);
+int hap_batch_sync(hap_batch* batch);
 
 /* Allocation-free iterations on caller-owned messages.  The paper has no
  * counterpart: this entry point exists for callers that cannot call

@@ -53,8 +53,12 @@ constexpr size_t kAlign = 256;
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
-    size_t A, R, S, pref, c, c0, tau, phi, tpart, b, rdiag, partials, e, ns, status, total;
+    size_t A, R, xs, S, pref, c, c0, tau, phi, tpart, b, rdiag, partials, e, ns, status, total;
 };
+
+// d up to which the tensor-core build always finds operand scratch in the
+// alpha and rho storage plus a reserve placed right after rho
+constexpr int64_t kBuildMaxD = 256;
 
 int64_t padded_ld(int64_t N) { return (N + 31) / 32 * 32; }
 
@@ -124,6 +128,8 @@ Layout make_layout(int64_t N, int L, const hap_options& o, const LaunchShape& sh
     auto take = [&](size_t bytes) { size_t at = off; off = align_up(off + bytes); return at; };
     y.A = take(mat);
     y.R = take(mat);
+    const size_t need = sbuild_tc_scratch_bytes(N, kBuildMaxD, 1), have = align_up(mat) + mat;
+    y.xs = take(need > have ? need - have : 0);
     y.S = take((size_t)s_levels * N * ld * s_elem);
     y.pref = take(vec);
     y.c = take(vec);
@@ -366,9 +372,11 @@ int hap_build_similarity(hap_ctx* h, const float* X, int64_t d, int mode) {
         h->launches += 1;
     } else if (mode == HAP_SBUILD_BF16 || mode == HAP_SBUILD_BF16_SPLIT) {
         const int split = mode == HAP_SBUILD_BF16_SPLIT;
-        // the (not yet used) availability storage serves as operand scratch
+        // the alpha and rho storage and the reserve after it (contiguous, reset
+        // after the build) serve as operand scratch
         const size_t need = sbuild_tc_scratch_bytes(h->N, d, split);
-        if (need > (size_t)h->L * h->N * h->ld * sizeof(float)) return HAP_EUNSUPPORTED;
+        const size_t cap = (size_t)(static_cast<char*>(h->S) - reinterpret_cast<char*>(h->A));
+        if (need > cap) return HAP_EUNSUPPORTED;
         int nk = 0;
         cudaError_t err = launch_sbuild_tc(X, h->N, d, split, h->S, s_bf16, h->ld, h->A, h->status, h->stream, &nk);
         if (err == cudaErrorNotSupported) return HAP_EUNSUPPORTED;

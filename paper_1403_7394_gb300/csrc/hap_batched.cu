@@ -1,0 +1,884 @@
+// Batched HAP: many independent instances of uneven N and L advanced by ONE
+// persistent row-pass launch per iteration (plus one batched column-statistics
+// launch), replayed from a CUDA graph.
+//
+// Work items are (instance, band) pairs: band g of an instance owns the row
+// blocks g, g + G, g + 2G, ... (a block = `rps` consecutive rows, which are
+// contiguous in memory, so one TMA bulk copy per tensor moves a whole block).
+// A 512-thread CTA is split into rps row groups of tg = 512 / rps threads;
+// each group holds one row of the block (tg * 8 >= ld), so instances with
+// small N process up to 16 rows per step.  Each CTA walks a list of items
+// assigned by a host-side longest-processing-time scheduler; the TMA ring
+// runs ahead across item boundaries.  Per-group column sums of max(0, rho)
+// stay in shared memory and are combined in group order into the band's
+// partials; a batched kernel sums bands in order (fixed-order reductions,
+// bitwise reproducible for a fixed schedule).  The equations are those of
+// the single-instance row pass (Eqs. 2.1-2.6 with damping, §3 schedule).
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "hap.h"
+#include "hap_common.cuh"
+#include "hap_internal.h"
+
+namespace hap {
+namespace {
+
+constexpr int kBT = 512;       // threads per CTA
+constexpr int kBK = 2;         // float4 groups per thread and row (8 columns)
+constexpr int kBStages = 3;    // TMA ring depth
+constexpr int kBMaxLd = kBT * 4 * kBK;  // 4096: longest row one CTA holds
+
+struct BInst {
+    float* A;
+    float* R;
+    const void* S;
+    const float* pref;
+    float* c;
+    float* tau;
+    float* phi;
+    float* tpart;
+    float* b;
+    float* rdiag;
+    float* partials;  // [G][L][ld]
+    int N, L, ld, rps, tg, G;
+};
+struct BItem {
+    int inst, band, nsteps;
+};
+struct BatchArgs {
+    const BInst* inst;
+    const BItem* items;
+    const int* cta_begin;  // items of CTA p: [cta_begin[p], cta_begin[p + 1])
+    unsigned* status;
+    float lam, oml;
+    int pending, update_c, use_tau;
+};
+
+size_t batched_smem_bytes(int maxL, int s_elem) {
+    const size_t W = (size_t)kBT * 4 * kBK;
+    const size_t a = W * 4, sb = W * s_elem;
+    return kBStages * (2 * a + sb) + (size_t)maxL * W * 4 + 2 * 32 * 16 + kBStages * 8;
+}
+
+template <typename ST>
+HAP_DEV float4 bload_s(const ST* p);
+template <>
+HAP_DEV float4 bload_s<float>(const float* p) { return *reinterpret_cast<const float4*>(p); }
+template <>
+HAP_DEV float4 bload_s<__nv_bfloat16>(const __nv_bfloat16* p) {
+    return SVec<__nv_bfloat16>::to_f4(*reinterpret_cast<const uint2*>(p));
+}
+
+template <typename ST>
+__global__ void __launch_bounds__(kBT, 1) rowpass_batched_kernel(const BatchArgs p, int maxL) {
+    extern __shared__ __align__(128) unsigned char sm[];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int W = kBT * 4 * kBK;
+    constexpr uint32_t A_BYTES = W * 4, S_BYTES = W * sizeof(ST);
+    constexpr uint32_t STAGE = 2 * A_BYTES + S_BYTES;
+    float4* acc = reinterpret_cast<float4*>(sm + kBStages * STAGE);  // [maxL][K][kBT] (row groups side by side)
+    float4* red = acc + (size_t)maxL * kBK * kBT;                      // [2][16]
+    const uint32_t bar0 = smem_addr(red + 2 * 16);
+    const uint32_t sm0 = smem_addr(sm);
+    const float lam = p.lam, oml = p.oml;
+    const bool pending = p.pending != 0;
+
+    const int it0 = p.cta_begin[blockIdx.x], it1 = p.cta_begin[blockIdx.x + 1];
+    if (tid == 0) {
+        for (int q = 0; q < kBStages; ++q) mbar_init(bar0 + 8 * q, 1);
+        fence_mbarrier_init();
+    }
+    __syncthreads();
+    bool bad = false;
+
+    // ---- producer (thread 0): a cursor over (item, step) ahead of the consumers
+    int pi = it0, pq = 0, issued = 0;
+    auto issue_next = [&]() {
+        while (pi < it1 && pq >= p.items[pi].nsteps) { ++pi; pq = 0; }
+        if (pi >= it1) return false;
+        const BItem itm = p.items[pi];
+        const BInst in = p.inst[itm.inst];
+        const int m = pq / in.L, l = pq % in.L;
+        const int i0 = (itm.band + m * in.G) * in.rps;
+        const int nrows = min(in.rps, in.N - i0);
+        const int st = issued % kBStages;
+        const uint32_t bar = bar0 + 8 * st, dst = sm0 + (uint32_t)st * STAGE;
+        const bool load_s = l == 0;
+        const uint32_t n = (uint32_t)nrows * (uint32_t)in.ld;
+        mbar_arrive_expect_tx(bar, n * (8u + (load_s ? (uint32_t)sizeof(ST) : 0u)));
+        const int64_t off = ((int64_t)l * in.N + i0) * in.ld;
+        bulk_g2s(dst, in.A + off, n * 4u, bar);
+        bulk_g2s(dst + A_BYTES, in.R + off, n * 4u, bar);
+        if (load_s) bulk_g2s(dst + 2 * A_BYTES, static_cast<const ST*>(in.S) + (int64_t)i0 * in.ld, n * (uint32_t)sizeof(ST), bar);
+        ++pq;
+        ++issued;
+        return true;
+    };
+    if (tid == 0)
+        for (int q = 0; q < kBStages; ++q)
+            if (!issue_next()) break;
+
+    int step = 0;  // consumer step counter of this CTA (ring position)
+    for (int it = it0; it < it1; ++it) {
+        const BItem itm = p.items[it];
+        const BInst in = p.inst[itm.inst];
+        const int tg = in.tg, r = tid / tg, t = tid - r * tg;
+        const int L = in.L, N = in.N;
+        const int64_t ld = in.ld;
+        int col[kBK];
+        bool ok[kBK];
+#pragma unroll
+        for (int k = 0; k < kBK; ++k) {
+            col[k] = 4 * (k * tg + t);
+            ok[k] = col[k] < (int)ld;
+        }
+        for (int q = tid; q < L * kBK * kBT; q += kBT) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 srow[kBK];
+#pragma unroll
+        for (int k = 0; k < kBK; ++k) srow[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        float c_prev = 0.f;
+        for (int q = 0; q < itm.nsteps; ++q, ++step) {
+            const int m = q / L, l = q % L;
+            const int i0 = (itm.band + m * in.G) * in.rps;
+            const int row = i0 + r;
+            const bool rv = row < N;  // this group's row exists
+            const int st = step % kBStages;
+            const unsigned char* base = sm + (size_t)st * STAGE;
+            const float* sA = reinterpret_cast<const float*>(base) + (size_t)r * ld;
+            const float* sR = reinterpret_cast<const float*>(base + A_BYTES) + (size_t)r * ld;
+            const ST* sS = reinterpret_cast<const ST*>(base + 2 * A_BYTES) + (size_t)r * ld;
+            if (!bad) bad = !mbar_wait(bar0 + 8 * st, (uint32_t)(step / kBStages) & 1u, p.status);
+            const int64_t voff = (int64_t)l * ld;
+            const int64_t off = ((int64_t)l * N + row) * ld;
+            const float pref_i = rv ? in.pref[voff + row] : 0.f;
+
+            float m1 = -kInf, m2 = -kInf, cm = -kInf;
+            int k1 = 0x7fffffff;
+            float4 rr[kBK], ss[kBK];
+#pragma unroll
+            for (int k = 0; k < kBK; ++k) {
+                float4 a4 = f4_splat(-kInf), r4 = f4_splat(0.f), s4 = f4_splat(0.f);
+                const bool live = ok[k] && rv;
+                if (live) {
+                    a4 = *reinterpret_cast<const float4*>(sA + col[k]);
+                    r4 = *reinterpret_cast<const float4*>(sR + col[k]);
+                    if (l == 0) srow[k] = bload_s<ST>(sS + col[k]);
+                    s4 = srow[k];
+                }
+                float4 an = a4;
+                float4 b4 = f4_splat(0.f);
+                if (pending) {
+                    if (live) b4 = __ldg(reinterpret_cast<const float4*>(in.b + voff + col[k]));
+                    an.x = damp(a4.x, avail_target(b4.x, r4.x, false), lam, oml);
+                    an.y = damp(a4.y, avail_target(b4.y, r4.y, false), lam, oml);
+                    an.z = damp(a4.z, avail_target(b4.z, r4.z, false), lam, oml);
+                    an.w = damp(a4.w, avail_target(b4.w, r4.w, false), lam, oml);
+                }
+                const int dd = row - col[k];
+                if ((unsigned)dd < 4u) {
+                    f4_set(s4, dd, pref_i);
+                    if (pending) f4_set(an, dd, damp(f4_get(a4, dd), avail_target(f4_get(b4, dd), f4_get(r4, dd), true), lam, oml));
+                }
+                if (pending && live && !bad) st_stream(in.A + off + col[k], an);
+                top2_push(__fadd_rn(an.x, s4.x), col[k] + 0, m1, k1, m2);
+                top2_push(__fadd_rn(an.y, s4.y), col[k] + 1, m1, k1, m2);
+                top2_push(__fadd_rn(an.z, s4.z), col[k] + 2, m1, k1, m2);
+                top2_push(__fadd_rn(an.w, s4.w), col[k] + 3, m1, k1, m2);
+                cm = fmaxf(cm, fmaxf(fmaxf(__fadd_rn(an.x, r4.x), __fadd_rn(an.y, r4.y)),
+                                     fmaxf(__fadd_rn(an.z, r4.z), __fadd_rn(an.w, r4.w))));
+                rr[k] = r4;
+                ss[k] = s4;
+            }
+            // ---- exact reduction within the row group ----------------------------
+            warp_top2(m1, k1, m2, cm);
+            const int par = step & 1;
+            if (lane == 0) red[par * 16 + warp] = make_float4(m1, m2, cm, __int_as_float(k1));
+            __syncthreads();
+            if (tid == 0 && issued < step + 1 + kBStages) issue_next();  // stage `st` is free
+            const int gw = tg >> 5, w0 = (r * tg) >> 5;
+            m1 = m2 = cm = -kInf;
+            k1 = 0x7fffffff;
+            for (int w = 0; w < gw; ++w) {
+                const float4 v = red[par * 16 + w0 + w];
+                top2_merge(m1, k1, m2, v.x, __float_as_int(v.w), v.y);
+                cm = fmaxf(cm, v.z);
+            }
+            // ---- inter-level messages (Eqs. 2.4-2.6) ---------------------------
+            const float cval = p.update_c ? cm : (rv ? in.c[voff + row] : 0.f);
+            const float tauv = (p.use_tau && l > 0 && rv) ? __fadd_rn(c_prev, in.tpart[voff + row]) : kInf;
+            c_prev = cval;
+            if (rv && t == 0 && !bad) {
+                if (p.update_c) in.c[voff + row] = cval;
+                in.tau[voff + row] = tauv;
+                if (l > 0) in.phi[voff - ld + row] = m1;
+            }
+            // ---- responsibilities (Eq. 2.1) and column sums ------------------------
+            const float mm1 = fminf(tauv, -m1), mm2 = fminf(tauv, -m2);
+#pragma unroll
+            for (int k = 0; k < kBK; ++k) {
+                const float4 r4 = rr[k], s4 = ss[k];
+                float4 rn;
+                rn.x = damp(r4.x, __fadd_rn(s4.x, mm1), lam, oml);
+                rn.y = damp(r4.y, __fadd_rn(s4.y, mm1), lam, oml);
+                rn.z = damp(r4.z, __fadd_rn(s4.z, mm1), lam, oml);
+                rn.w = damp(r4.w, __fadd_rn(s4.w, mm1), lam, oml);
+                const int dk = k1 - col[k];
+                if ((unsigned)dk < 4u) f4_set(rn, dk, damp(f4_get(r4, dk), __fadd_rn(f4_get(s4, dk), mm2), lam, oml));
+                float4 add = make_float4(fmaxf(rn.x, 0.f), fmaxf(rn.y, 0.f), fmaxf(rn.z, 0.f), fmaxf(rn.w, 0.f));
+                if (!rv) add = f4_splat(0.f);
+                const int dd = row - col[k];
+                if ((unsigned)dd < 4u) {
+                    f4_set(add, dd, 0.f);
+                    if (!bad) in.rdiag[voff + row] = f4_get(rn, dd);
+                }
+                if (ok[k] && rv && !bad) st_stream(in.R + off + col[k], rn);
+                float4& a = acc[(l * kBK + k) * kBT + tid];
+                a.x = __fadd_rn(a.x, add.x);
+                a.y = __fadd_rn(a.y, add.y);
+                a.z = __fadd_rn(a.z, add.z);
+                a.w = __fadd_rn(a.w, add.w);
+            }
+        }
+        // ---- band partials: row groups combined in group order ------------------
+        __syncthreads();
+        const int rps = in.rps;
+        for (int q = tid; q < L * kBK * tg; q += kBT) {
+            const int ll = q / (kBK * tg), rem = q - ll * kBK * tg, k = rem / tg, tt = rem - k * tg;
+            const int cc = 4 * (k * tg + tt);
+            if (cc >= (int)ld) continue;
+            float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int rg = 0; rg < rps; ++rg) {
+                const float4 v = acc[(ll * kBK + k) * kBT + rg * tg + tt];
+                s.x = __fadd_rn(s.x, v.x);
+                s.y = __fadd_rn(s.y, v.y);
+                s.z = __fadd_rn(s.z, v.z);
+                s.w = __fadd_rn(s.w, v.w);
+            }
+            *reinterpret_cast<float4*>(in.partials + ((int64_t)itm.band * L + ll) * ld + cc) = s;
+        }
+        __syncthreads();
+    }
+}
+
+// Column statistics of every instance: one thread per (instance, level, column).
+struct BCol {
+    const float* partials;
+    const float* c;
+    const float* phi;
+    const float* rdiag;
+    float* b;
+    float* tpart;
+    int N, L, ld, G;
+    int64_t first;  // first flat index of this instance
+};
+__global__ void colstats_batched_kernel(const BCol* __restrict__ cols, int B, int64_t total) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= total) return;
+    int lo = 0, hi = B - 1;
+    while (lo < hi) {  // last instance whose first index <= idx
+        const int mid = (lo + hi + 1) >> 1;
+        if (cols[mid].first <= idx) lo = mid; else hi = mid - 1;
+    }
+    const BCol in = cols[lo];
+    const int64_t rel = idx - in.first;
+    const int l = (int)(rel / in.N);
+    const int64_t j = rel - (int64_t)l * in.N;
+    const float* pp = in.partials + (int64_t)l * in.ld + j;
+    float P = 0.f;
+    for (int q = 0; q < in.G; ++q) P = __fadd_rn(P, pp[(int64_t)q * in.L * in.ld]);
+    const int64_t v = (int64_t)l * in.ld + j;
+    const float rd = in.rdiag[v];
+    in.b[v] = __fadd_rn(__fadd_rn(__fadd_rn(in.c[v], in.phi[v]), rd), P);
+    if (l + 1 < in.L) in.tpart[v + in.ld] = __fadd_rn(rd, P);
+}
+
+// Eq. 2.8 for every (instance, level, row): one warp per row.
+__global__ void exemplars_batched_kernel(const BInst* __restrict__ inst, const int64_t* __restrict__ row_first,
+                                         const int64_t* __restrict__ e_first, int B, int64_t total_rows,
+                                         int pending, float lam, float oml, int32_t* __restrict__ e) {
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (gw >= total_rows) return;
+    int lo = 0, hi = B - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (row_first[mid] <= gw) lo = mid; else hi = mid - 1;
+    }
+    const BInst in = inst[lo];
+    const int64_t rel = gw - row_first[lo];
+    const int l = (int)(rel / in.N);
+    const int64_t i = rel - (int64_t)l * in.N;
+    const float* Ar = in.A + rel * in.ld;
+    const float* Rr = in.R + rel * in.ld;
+    float best = -kInf;
+    int bi = 0x7fffffff;
+    for (int64_t j = lane; j < in.N; j += 32) {
+        const float r = Rr[j];
+        float a = Ar[j];
+        if (pending) a = damp(a, avail_target(in.b[(int64_t)l * in.ld + j], r, j == i), lam, oml);
+        const float v = __fadd_rn(a, r);
+        if (v > best) { best = v; bi = (int)j; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const float ov = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+    }
+    if (lane == 0) e[e_first[lo] + rel] = bi;
+}
+
+// NS^l of every (instance, level) in FP64, fixed-order tree per block.
+template <typename ST>
+__global__ void netsim_batched_kernel(const BInst* __restrict__ inst, const int* __restrict__ lev_inst,
+                                      const int* __restrict__ lev_l, const int64_t* __restrict__ e_first,
+                                      const int32_t* __restrict__ e, double* __restrict__ ns) {
+    __shared__ double part[256];
+    const int q = blockIdx.x, b = lev_inst[q], l = lev_l[q];
+    const BInst in = inst[b];
+    const ST* S = static_cast<const ST*>(in.S);
+    double accd = 0.0;
+    for (int64_t i = threadIdx.x; i < in.N; i += blockDim.x) {
+        const int64_t ej = e[e_first[b] + (int64_t)l * in.N + i];
+        accd += (ej == i) ? (double)in.pref[(int64_t)l * in.ld + i] : (double)(float)S[i * in.ld + ej];
+    }
+    part[threadIdx.x] = accd;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) part[threadIdx.x] += part[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) ns[q] = part[0];
+}
+
+}  // namespace
+}  // namespace hap
+
+using namespace hap;
+
+struct hap_batch {
+    int B = 0;
+    std::vector<int64_t> N;
+    std::vector<int> L, ld;
+    hap_options opt{};
+    float lam = 0.5f;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    bool own_ws = false;
+    int s_bf16 = 0;
+    int maxL = 1;
+    std::vector<BInst> inst;         // host copy of the descriptors
+    std::vector<size_t> inst_bytes;  // workspace bytes per instance (before partials)
+    BInst* d_inst = nullptr;
+    BCol* d_cols = nullptr;
+    BItem* d_items = nullptr;
+    int* d_cta_begin = nullptr;
+    int64_t* d_row_first = nullptr;
+    int64_t* d_e_first = nullptr;
+    int* d_lev_inst = nullptr;
+    int* d_lev_l = nullptr;
+    int32_t* d_e = nullptr;
+    double* d_ns = nullptr;
+    unsigned* status = nullptr;
+    void* build_scratch = nullptr;   // operands of the tensor-core build
+    size_t build_scratch_bytes = 0;
+    std::vector<float*> c0;          // per instance initial c (device)
+    int64_t total_cols = 0, total_rows = 0, total_levels = 0;
+    int grid = 0;                    // persistent CTAs
+    int items_per_cta = 2;           // scheduling granularity (autotuned)
+    int64_t iter = 0;
+    bool pending = false;
+    cudaGraphExec_t graph = nullptr;
+    int64_t launches = 0;
+};
+
+namespace {
+
+constexpr size_t kAl = 256;
+size_t al(size_t x) { return (x + kAl - 1) / kAl * kAl; }
+
+#define BCU(x)                              \
+    do {                                    \
+        if ((x) != cudaSuccess) {           \
+            cudaGetLastError();             \
+            return HAP_ECUDA;               \
+        }                                   \
+    } while (0)
+
+// rows per step for a row of ld columns: groups of tg >= ld / 8 threads
+void group_shape(int ld, int* rps, int* tg) {
+    int t = 32;
+    while (t * 4 * kBK < ld) t *= 2;
+    *tg = t;
+    *rps = kBT / t;
+}
+
+// Bands per instance (total ~ items_per_cta x grid, proportional to work) and
+// a longest-processing-time assignment of items to the persistent CTAs.
+int schedule(hap_batch* h) {
+    const int B = h->B;
+    std::vector<double> work(B);
+    double tot = 0;
+    for (int b = 0; b < B; ++b) {
+        work[b] = (double)h->N[b] * h->N[b] * h->L[b];
+        tot += work[b];
+    }
+    const double target = tot / ((double)h->grid * h->items_per_cta);
+    std::vector<BItem> items;
+    std::vector<double> iw;
+    for (int b = 0; b < B; ++b) {
+        const int nblk = (int)((h->N[b] + h->inst[b].rps - 1) / h->inst[b].rps);
+        int G = (int)(work[b] / target + 0.5);
+        G = std::max(1, std::min(G, nblk));
+        h->inst[b].G = G;
+        for (int g = 0; g < G; ++g) {
+            const int blocks = nblk > g ? (nblk - 1 - g) / G + 1 : 0;
+            items.push_back(BItem{b, g, blocks * h->L[b]});
+            iw.push_back((double)blocks * h->inst[b].rps * h->N[b] * h->L[b]);
+        }
+    }
+    std::vector<int> order(items.size());
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return iw[a] > iw[b]; });
+    std::vector<std::vector<int>> per(h->grid);
+    std::vector<double> load(h->grid, 0.0);
+    for (int o : order) {
+        const int p = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        per[p].push_back(o);
+        load[p] += iw[o] + 1e3;  // + per-item overhead
+    }
+    std::vector<BItem> flat;
+    std::vector<int> begin(h->grid + 1, 0);
+    for (int p = 0; p < h->grid; ++p) {
+        begin[p] = (int)flat.size();
+        for (int o : per[p]) flat.push_back(items[o]);
+    }
+    begin[h->grid] = (int)flat.size();
+    if (h->d_items) cudaFree(h->d_items);
+    if (h->d_cta_begin) cudaFree(h->d_cta_begin);
+    BCU(cudaMalloc(&h->d_items, std::max<size_t>(1, flat.size()) * sizeof(BItem)));
+    BCU(cudaMalloc(&h->d_cta_begin, begin.size() * sizeof(int)));
+    BCU(cudaMemcpy(h->d_items, flat.data(), flat.size() * sizeof(BItem), cudaMemcpyHostToDevice));
+    BCU(cudaMemcpy(h->d_cta_begin, begin.data(), begin.size() * sizeof(int), cudaMemcpyHostToDevice));
+    BCU(cudaMemcpy(h->d_inst, h->inst.data(), B * sizeof(BInst), cudaMemcpyHostToDevice));
+    std::vector<BCol> cols(B);
+    int64_t first = 0;
+    for (int b = 0; b < B; ++b) {
+        const BInst& in = h->inst[b];
+        cols[b] = BCol{in.partials, in.c, in.phi, in.rdiag, in.b, in.tpart, in.N, in.L, in.ld, in.G, first};
+        first += (int64_t)in.L * in.N;
+    }
+    BCU(cudaMemcpy(h->d_cols, cols.data(), B * sizeof(BCol), cudaMemcpyHostToDevice));
+    if (h->graph) {
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
+    return HAP_OK;
+}
+
+int batch_reset(hap_batch* h) {
+    for (int b = 0; b < h->B; ++b) {
+        const BInst& in = h->inst[b];
+        const size_t mat = (size_t)in.L * in.N * in.ld * 4, vec = (size_t)in.L * in.ld * 4;
+        BCU(cudaMemsetAsync(in.A, 0, mat, h->stream));
+        BCU(launch_fill_alpha_padding(in.A, (int64_t)in.L * in.N, in.N, in.ld, h->stream));
+        BCU(cudaMemsetAsync(in.R, 0, mat, h->stream));
+        BCU(cudaMemcpyAsync(in.c, h->c0[b], vec, cudaMemcpyDeviceToDevice, h->stream));
+        BCU(cudaMemsetAsync(in.phi, 0, vec, h->stream));
+        BCU(cudaMemsetAsync(in.tpart, 0, vec, h->stream));
+        BCU(cudaMemsetAsync(in.b, 0, vec, h->stream));
+        BCU(cudaMemsetAsync(in.rdiag, 0, vec, h->stream));
+        std::vector<float> inf(in.L * (size_t)in.ld, __builtin_inff());
+        BCU(cudaMemcpyAsync(in.tau, inf.data(), vec, cudaMemcpyHostToDevice, h->stream));
+        BCU(cudaStreamSynchronize(h->stream));
+    }
+    h->iter = 0;
+    h->pending = false;
+    return HAP_OK;
+}
+
+cudaError_t launch_batched_iteration(hap_batch* h, int pending, int update_c, int use_tau, cudaStream_t st) {
+    BatchArgs a;
+    a.inst = h->d_inst;
+    a.items = h->d_items;
+    a.cta_begin = h->d_cta_begin;
+    a.status = h->status;
+    a.lam = h->lam;
+    a.oml = 1.0f - h->lam;
+    a.pending = pending;
+    a.update_c = update_c;
+    a.use_tau = use_tau;
+    const size_t smem = batched_smem_bytes(h->maxL, h->s_bf16 ? 2 : 4);
+    if (h->s_bf16)
+        rowpass_batched_kernel<__nv_bfloat16><<<h->grid, kBT, smem, st>>>(a, h->maxL);
+    else
+        rowpass_batched_kernel<float><<<h->grid, kBT, smem, st>>>(a, h->maxL);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    const unsigned blocks = (unsigned)((h->total_cols + 255) / 256);
+    colstats_batched_kernel<<<blocks, 256, 0, st>>>(h->d_cols, h->B, h->total_cols);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+extern "C" {
+
+int hap_batch_create(int B, const int64_t* N, const int* L, float damping, const hap_options* opt,
+                     hap_batch** out) {
+    if (!out || B < 1 || !N || !L || !(damping > 0.f && damping < 1.f)) return HAP_EINVAL;
+    *out = nullptr;
+    hap_options o;
+    hap_default_options(&o);
+    if (opt) o = *opt;
+    if (o.c_mode != HAP_C_PAPER && o.c_mode != HAP_C_FIXED) return HAP_EINVAL;
+    hap_batch* h = new (std::nothrow) hap_batch();
+    if (!h) return HAP_ENOMEM;
+    h->B = B;
+    h->opt = o;
+    h->lam = damping;
+    h->s_bf16 = o.s_dtype == HAP_S_BF16;
+    h->N.assign(N, N + B);
+    h->L.assign(L, L + B);
+    size_t total = 0;
+    int maxL = 1;
+    for (int b = 0; b < B; ++b) {
+        if (N[b] < 2 || L[b] < 1 || L[b] > 16) { delete h; return HAP_EINVAL; }
+        const int64_t ldb = (N[b] + 31) / 32 * 32;
+        if (ldb > kBMaxLd) { delete h; return HAP_EUNSUPPORTED; }
+        h->ld.push_back((int)ldb);
+        maxL = std::max(maxL, L[b]);
+    }
+    h->maxL = maxL;
+    int dev = 0, sms = 0, smem_limit = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&smem_limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const size_t smem = batched_smem_bytes(maxL, h->s_bf16 ? 2 : 4);
+    if (smem > (size_t)smem_limit) { delete h; return HAP_EUNSUPPORTED; }
+    // the shared-memory opt-in is set here, never inside a stream capture
+    if (cudaFuncSetAttribute(rowpass_batched_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaFuncSetAttribute(rowpass_batched_kernel<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return HAP_ECUDA;
+    }
+    h->grid = sms;
+    // workspace: per instance A, R, S, 8 vectors, partials sized for the most
+    // bands any schedule gives it (its row-block count, at most grid*items)
+    std::vector<size_t> off(B);
+    h->inst.resize(B);
+    for (int b = 0; b < B; ++b) {
+        int rps, tg;
+        group_shape(h->ld[b], &rps, &tg);
+        h->inst[b].rps = rps;
+        h->inst[b].tg = tg;
+        const int nblk = (int)((N[b] + rps - 1) / rps);
+        const size_t mat = (size_t)L[b] * N[b] * h->ld[b] * 4;
+        const size_t vec = (size_t)L[b] * h->ld[b] * 4;
+        const size_t s = (size_t)N[b] * h->ld[b] * (h->s_bf16 ? 2 : 4);
+        off[b] = total;
+        total += al(mat) * 2 + al(s) + 8 * al(vec) + al((size_t)nblk * vec);
+    }
+    int64_t ecount = 0, levels = 0;
+    for (int b = 0; b < B; ++b) { ecount += (int64_t)L[b] * N[b]; levels += L[b]; }
+    const size_t e_off = total;
+    total += al((size_t)ecount * 4) + al((size_t)levels * 8) + al(16);
+    size_t xs = 0;
+    for (int b = 0; b < B; ++b) xs = std::max(xs, sbuild_tc_scratch_bytes(N[b], 256, 1));
+    const size_t xs_off = total;
+    total += al(xs);
+    if (cudaMalloc(&h->ws, total) != cudaSuccess) { cudaGetLastError(); delete h; return HAP_ENOMEM; }
+    h->own_ws = true;
+    h->ws_bytes = total;
+    char* base = static_cast<char*>(h->ws);
+    for (int b = 0; b < B; ++b) {
+        BInst& in = h->inst[b];
+        const size_t mat = al((size_t)L[b] * N[b] * h->ld[b] * 4), vec = al((size_t)L[b] * h->ld[b] * 4);
+        const size_t s = al((size_t)N[b] * h->ld[b] * (h->s_bf16 ? 2 : 4));
+        char* p = base + off[b];
+        in.A = reinterpret_cast<float*>(p); p += mat;
+        in.R = reinterpret_cast<float*>(p); p += mat;
+        in.S = p; p += s;
+        float* v[8];
+        for (int q = 0; q < 8; ++q) { v[q] = reinterpret_cast<float*>(p); p += vec; }
+        in.pref = v[0]; in.c = v[1]; in.tau = v[2]; in.phi = v[3]; in.tpart = v[4]; in.b = v[5]; in.rdiag = v[6];
+        h->c0.push_back(v[7]);
+        in.partials = reinterpret_cast<float*>(p);
+        in.N = (int)N[b];
+        in.L = L[b];
+        in.ld = h->ld[b];
+        in.G = 1;
+    }
+    h->d_e = reinterpret_cast<int32_t*>(base + e_off);
+    h->d_ns = reinterpret_cast<double*>(base + e_off + al((size_t)ecount * 4));
+    h->status = reinterpret_cast<unsigned*>(base + e_off + al((size_t)ecount * 4) + al((size_t)levels * 8));
+    h->build_scratch = base + xs_off;
+    h->build_scratch_bytes = al(xs);
+    h->total_cols = ecount;
+    h->total_rows = ecount;
+    h->total_levels = levels;
+    std::vector<int64_t> row_first(B), e_first(B);
+    std::vector<int> lev_inst, lev_l;
+    int64_t acc = 0;
+    for (int b = 0; b < B; ++b) {
+        row_first[b] = acc;
+        e_first[b] = acc;
+        acc += (int64_t)L[b] * N[b];
+        for (int l = 0; l < L[b]; ++l) { lev_inst.push_back(b); lev_l.push_back(l); }
+    }
+    bool okm = cudaMalloc(&h->d_inst, B * sizeof(BInst)) == cudaSuccess &&
+               cudaMalloc(&h->d_cols, B * sizeof(BCol)) == cudaSuccess &&
+               cudaMalloc(&h->d_row_first, B * sizeof(int64_t)) == cudaSuccess &&
+               cudaMalloc(&h->d_e_first, B * sizeof(int64_t)) == cudaSuccess &&
+               cudaMalloc(&h->d_lev_inst, levels * sizeof(int)) == cudaSuccess &&
+               cudaMalloc(&h->d_lev_l, levels * sizeof(int)) == cudaSuccess &&
+               cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
+    if (!okm) { cudaGetLastError(); hap_batch_destroy(h); return HAP_ENOMEM; }
+    cudaMemcpy(h->d_row_first, row_first.data(), B * sizeof(int64_t), cudaMemcpyHostToDevice);
+    cudaMemcpy(h->d_e_first, e_first.data(), B * sizeof(int64_t), cudaMemcpyHostToDevice);
+    cudaMemcpy(h->d_lev_inst, lev_inst.data(), levels * sizeof(int), cudaMemcpyHostToDevice);
+    cudaMemcpy(h->d_lev_l, lev_l.data(), levels * sizeof(int), cudaMemcpyHostToDevice);
+    for (int b = 0; b < B; ++b) {
+        const BInst& in = h->inst[b];
+        const size_t vec = (size_t)in.L * in.ld * 4;
+        cudaMemset(const_cast<float*>(in.pref), 0, vec);
+        cudaMemset(h->c0[b], 0, vec);
+        cudaMemset(const_cast<void*>(in.S), 0, (size_t)in.N * in.ld * (h->s_bf16 ? 2 : 4));
+    }
+    cudaMemset(h->status, 0, 16);
+    int rc = schedule(h);
+    if (!rc) rc = batch_reset(h);
+    if (rc) { hap_batch_destroy(h); return rc; }
+    *out = h;
+    return HAP_OK;
+}
+
+void hap_batch_destroy(hap_batch* h) {
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    cudaFree(h->d_inst);
+    cudaFree(h->d_cols);
+    cudaFree(h->d_items);
+    cudaFree(h->d_cta_begin);
+    cudaFree(h->d_row_first);
+    cudaFree(h->d_e_first);
+    cudaFree(h->d_lev_inst);
+    cudaFree(h->d_lev_l);
+    if (h->own_ws) cudaFree(h->ws);
+    delete h;
+}
+
+int hap_batch_set_stream(hap_batch* h, void* stream) {
+    if (!h) return HAP_EINVAL;
+    h->stream = static_cast<cudaStream_t>(stream);
+    return HAP_OK;
+}
+
+int hap_batch_set_preferences(hap_batch* h, const float* prefs) {
+    if (!h || !prefs) return HAP_EINVAL;
+    int64_t q = 0;
+    for (int b = 0; b < h->B; ++b) {
+        const BInst& in = h->inst[b];
+        std::vector<float> host((size_t)in.L * in.ld, 0.f);
+        for (int l = 0; l < in.L; ++l) {
+            const float v = prefs[q++];
+            if (!(v > -__builtin_inff() && v < __builtin_inff())) return HAP_EINVAL;
+            for (int i = 0; i < in.N; ++i) host[(size_t)l * in.ld + i] = v;
+        }
+        BCU(cudaMemcpyAsync(const_cast<float*>(in.pref), host.data(), host.size() * 4, cudaMemcpyHostToDevice, h->stream));
+        BCU(cudaStreamSynchronize(h->stream));
+    }
+    return HAP_OK;
+}
+
+int hap_batch_build_similarity(hap_batch* h, const float* X, int64_t d, int mode) {
+    if (!h || !X || d < 1) return HAP_EINVAL;
+    // operand scratch of the tensor-core build, reused in stream order
+    const size_t scratch_cap = h->build_scratch_bytes;
+    int64_t row0 = 0;
+    for (int b = 0; b < h->B; ++b) {
+        const BInst& in = h->inst[b];
+        const float* Xb = X + row0 * d;
+        row0 += in.N;
+        if (mode == HAP_SBUILD_F32) {
+            BCU(launch_sbuild_f32(Xb, in.N, d, const_cast<void*>(in.S), h->s_bf16, in.ld, h->stream));
+            h->launches += 1;
+        } else if (mode == HAP_SBUILD_BF16 || mode == HAP_SBUILD_BF16_SPLIT) {
+            const int split = mode == HAP_SBUILD_BF16_SPLIT;
+            if (sbuild_tc_scratch_bytes(in.N, d, split) > scratch_cap) return HAP_EUNSUPPORTED;
+            int nk = 0;
+            cudaError_t err = launch_sbuild_tc(Xb, in.N, d, split, const_cast<void*>(in.S), h->s_bf16, in.ld,
+                                               h->build_scratch, h->status, h->stream, &nk);
+            if (err == cudaErrorNotSupported) return HAP_EUNSUPPORTED;
+            BCU(err);
+            h->launches += nk;
+        } else {
+            return HAP_EINVAL;
+        }
+    }
+    return batch_reset(h);
+}
+
+int hap_batch_set_similarity(hap_batch* h, int b, const void* S, int64_t ld, int dtype) {
+    if (!h || b < 0 || b >= h->B || !S || ld < h->N[b] || (dtype != HAP_S_F32 && dtype != HAP_S_BF16)) return HAP_EINVAL;
+    const BInst& in = h->inst[b];
+    BCU(launch_copy_similarity(const_cast<void*>(in.S), h->s_bf16, in.ld, S, dtype == HAP_S_BF16, ld, in.N, h->stream));
+    h->launches += 1;
+    return batch_reset(h);
+}
+
+int hap_batch_iterate(hap_batch* h, int n) {
+    if (!h || n < 0) return HAP_EINVAL;
+    for (int it = 0; it < n; ++it) {
+        const int64_t t = h->iter + 1;
+        const int update_c = (h->opt.c_mode == HAP_C_PAPER && t >= 2) ? 1 : 0;
+        if (t >= 2 && h->pending) {
+            // steady state: one CUDA graph of (batched row pass, batched column statistics)
+            if (!h->graph) {
+                cudaGraph_t g = nullptr;
+                BCU(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+                cudaError_t err = launch_batched_iteration(h, 1, update_c, 1, h->cap_stream);
+                cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &g);
+                if (err != cudaSuccess || e2 != cudaSuccess) { cudaGetLastError(); if (g) cudaGraphDestroy(g); return HAP_ECUDA; }
+                err = cudaGraphInstantiate(&h->graph, g, 0);
+                cudaGraphDestroy(g);
+                BCU(err);
+            }
+            BCU(cudaGraphLaunch(h->graph, h->stream));
+        } else {
+            BCU(launch_batched_iteration(h, h->pending ? 1 : 0, update_c, t >= 2 ? 1 : 0, h->stream));
+        }
+        h->launches += 2;
+        h->pending = true;
+        h->iter = t;
+    }
+    return HAP_OK;
+}
+
+int hap_batch_exemplars(hap_batch* h, int32_t* e, int on_host) {
+    if (!h || !e || (on_host != 0 && on_host != 1)) return HAP_EINVAL;
+    const unsigned blocks = (unsigned)((h->total_rows * 32 + 255) / 256);
+    exemplars_batched_kernel<<<blocks, 256, 0, h->stream>>>(h->d_inst, h->d_row_first, h->d_e_first, h->B, h->total_rows,
+                                                           h->pending, h->lam, 1.0f - h->lam, h->d_e);
+    BCU(cudaGetLastError());
+    h->launches += 1;
+    BCU(cudaMemcpyAsync(e, h->d_e, (size_t)h->total_rows * 4, on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                        h->stream));
+    if (on_host) BCU(cudaStreamSynchronize(h->stream));
+    return HAP_OK;
+}
+
+int hap_batch_net_similarity(hap_batch* h, double* ns) {
+    if (!h || !ns) return HAP_EINVAL;
+    const unsigned blocks = (unsigned)((h->total_rows * 32 + 255) / 256);
+    exemplars_batched_kernel<<<blocks, 256, 0, h->stream>>>(h->d_inst, h->d_row_first, h->d_e_first, h->B, h->total_rows,
+                                                           h->pending, h->lam, 1.0f - h->lam, h->d_e);
+    BCU(cudaGetLastError());
+    if (h->s_bf16)
+        netsim_batched_kernel<__nv_bfloat16><<<(unsigned)h->total_levels, 256, 0, h->stream>>>(
+            h->d_inst, h->d_lev_inst, h->d_lev_l, h->d_e_first, h->d_e, h->d_ns);
+    else
+        netsim_batched_kernel<float><<<(unsigned)h->total_levels, 256, 0, h->stream>>>(
+            h->d_inst, h->d_lev_inst, h->d_lev_l, h->d_e_first, h->d_e, h->d_ns);
+    BCU(cudaGetLastError());
+    h->launches += 2;
+    BCU(cudaMemcpyAsync(ns, h->d_ns, (size_t)h->total_levels * 8, cudaMemcpyDeviceToHost, h->stream));
+    BCU(cudaStreamSynchronize(h->stream));
+    unsigned st = 0;
+    BCU(cudaMemcpy(&st, h->status, 4, cudaMemcpyDeviceToHost));
+    if (st & ST_TIMEOUT) return HAP_ETIMEOUT;
+    if (st) return HAP_EDEVICE;
+    return HAP_OK;
+}
+
+int hap_batch_get_state(hap_batch* h, int b, float* A, float* R, float* vecs, int64_t* iter) {
+    if (!h || b < 0 || b >= h->B) return HAP_EINVAL;
+    const BInst& in = h->inst[b];
+    const int64_t N = in.N, L = in.L, ld = in.ld;
+    if (A) {
+        BCU(launch_materialize_A(A, in.A, in.R, in.b, h->pending, h->lam, 1.0f - h->lam, N, ld, (int)L, h->stream));
+        h->launches += 1;
+    }
+    if (R)
+        BCU(cudaMemcpy2DAsync(R, N * 4, in.R, ld * 4, N * 4, (size_t)(L * N), cudaMemcpyDeviceToDevice, h->stream));
+    if (vecs) {
+        const float* src[3] = {in.c, in.tau, in.phi};
+        for (int q = 0; q < 3; ++q)
+            BCU(cudaMemcpy2DAsync(vecs + (size_t)q * L * N, N * 4, src[q], ld * 4, N * 4, (size_t)L,
+                                  cudaMemcpyDeviceToDevice, h->stream));
+    }
+    if (iter) *iter = h->iter;
+    return HAP_OK;
+}
+
+// Autotuner: times one steady-state iteration (CUDA events) for each
+// scheduling granularity in {1, 2, 3, 4, 6} items per CTA and keeps the
+// fastest; the messages are reset to Algorithm 1's start afterwards.
+int hap_batch_tune(hap_batch* h, double* best_ms) {
+    if (!h) return HAP_EINVAL;
+    const int cands[5] = {1, 2, 3, 4, 6};
+    double best = 1e30;
+    int best_c = h->items_per_cta;
+    cudaEvent_t e0, e1;
+    BCU(cudaEventCreate(&e0));
+    BCU(cudaEventCreate(&e1));
+    for (int c : cands) {
+        h->items_per_cta = c;
+        int rc = schedule(h);
+        if (rc) return rc;
+        rc = batch_reset(h);
+        if (rc) return rc;
+        BCU(launch_batched_iteration(h, 0, 0, 0, h->stream));  // warm-up (t = 1)
+        BCU(cudaEventRecord(e0, h->stream));
+        for (int r = 0; r < 3; ++r) BCU(launch_batched_iteration(h, 1, h->opt.c_mode == HAP_C_PAPER, 1, h->stream));
+        BCU(cudaEventRecord(e1, h->stream));
+        BCU(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        BCU(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms / 3 < best) {
+            best = ms / 3;
+            best_c = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->items_per_cta = best_c;
+    int rc = schedule(h);
+    if (!rc) rc = batch_reset(h);
+    if (best_ms) *best_ms = best;
+    return rc;
+}
+
+int hap_batch_query(hap_batch* h, int key, int64_t* value) {
+    if (!h || !value) return HAP_EINVAL;
+    switch (key) {
+        case HAP_Q_ITER: *value = h->iter; return HAP_OK;
+        case HAP_Q_LAUNCHES: *value = h->launches; return HAP_OK;
+        case HAP_Q_GRID_CLUSTERS: *value = h->grid; return HAP_OK;
+        case HAP_Q_BATCH_ITEMS_PER_CTA: *value = h->items_per_cta; return HAP_OK;
+        default: return HAP_EINVAL;
+    }
+}
+
+int hap_batch_sync(hap_batch* h) {
+    if (!h) return HAP_EINVAL;
+    BCU(cudaStreamSynchronize(h->stream));
+    unsigned st = 0;
+    BCU(cudaMemcpy(&st, h->status, 4, cudaMemcpyDeviceToHost));
+    if (st & ST_TIMEOUT) return HAP_ETIMEOUT;
+    if (st) return HAP_EDEVICE;
+    return HAP_OK;
+}
+
+}  // extern "C"

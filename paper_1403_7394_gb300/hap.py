@@ -20,6 +20,7 @@ C_MODES = {"paper": 0, "fixed": 1}
 S_DTYPES = {"f32": 0, "bf16": 1}
 SBUILD = {"f32": 0, "bf16": 1, "bf16_split": 2}
 Q_BLOCK_THREADS, Q_CLUSTER_SIZE, Q_GRID_CLUSTERS, Q_LD, Q_ITER, Q_ELEMS_PER_THREAD, Q_LAUNCHES = 1, 2, 3, 4, 5, 6, 7
+Q_BATCH_ITEMS_PER_CTA = 8
 
 
 class HapOptions(ctypes.Structure):
@@ -55,6 +56,19 @@ def _load():
         "hap_row_pass_time": (i32, [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64), i32]),
         "hap_strerror": (ctypes.c_char_p, [i32]),
         "hap_iterate_noalloc": (i32, [i64, i32, f32, i32, vp, i32, vp, vp, vp, vp, vp, vp, i64, i32, vp]),
+        "hap_batch_create": (i32, [i32, vp, vp, f32, ctypes.POINTER(HapOptions), ctypes.POINTER(vp)]),
+        "hap_batch_destroy": (None, [vp]),
+        "hap_batch_set_stream": (i32, [vp, vp]),
+        "hap_batch_set_preferences": (i32, [vp, vp]),
+        "hap_batch_build_similarity": (i32, [vp, vp, i64, i32]),
+        "hap_batch_set_similarity": (i32, [vp, i32, vp, i64, i32]),
+        "hap_batch_iterate": (i32, [vp, i32]),
+        "hap_batch_exemplars": (i32, [vp, vp, i32]),
+        "hap_batch_net_similarity": (i32, [vp, vp]),
+        "hap_batch_get_state": (i32, [vp, i32, vp, vp, vp, ctypes.POINTER(i64)]),
+        "hap_batch_tune": (i32, [vp, ctypes.POINTER(ctypes.c_double)]),
+        "hap_batch_query": (i32, [vp, i32, ctypes.POINTER(i64)]),
+        "hap_batch_sync": (i32, [vp]),
         "hap_noalloc_scratch_bytes": (ctypes.c_size_t, []),
     }
     for name, (res, args) in sigs.items():
@@ -269,3 +283,102 @@ def iterate_noalloc(N: int, L: int, damping: float, c_mode: str, S: torch.Tensor
     check(lib.hap_iterate_noalloc(int(N), int(L), float(damping), C_MODES[c_mode], _ptr(S), dt, _ptr(pref),
                                   _ptr(A), _ptr(R), _ptr(c), _ptr(tau), _ptr(phi), int(t0), int(n),
                                   ctypes.c_void_p(st.cuda_stream)), "hap_iterate_noalloc")
+
+
+class HAPBatch:
+    """Many independent HAP problems (N[b] points, L[b] levels) advanced by one
+    persistent launch per iteration (hap_batch_* in the C ABI)."""
+
+    def __init__(self, N, L, damping: float = 0.5, device="cuda", stream: torch.cuda.Stream | None = None,
+                 c_mode="paper", s_dtype="f32"):
+        import numpy as np
+        self.N = [int(x) for x in N]
+        self.L = [int(x) for x in L]
+        self.B = len(self.N)
+        self.device = torch.device(device)
+        o = options(c_mode=c_mode, s_dtype=s_dtype)
+        n_arr = np.ascontiguousarray(self.N, dtype=np.int64)
+        l_arr = np.ascontiguousarray(self.L, dtype=np.int32)
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            h = ctypes.c_void_p()
+            check(lib.hap_batch_create(self.B, n_arr.ctypes.data_as(ctypes.c_void_p), l_arr.ctypes.data_as(ctypes.c_void_p),
+                                       float(damping), ctypes.byref(o), ctypes.byref(h)), "hap_batch_create")
+            self._h = h
+            check(lib.hap_batch_set_stream(self._h, ctypes.c_void_p(self.stream.cuda_stream)), "hap_batch_set_stream")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.hap_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_preferences(self, prefs):
+        """One preference per (instance, level), instance-major."""
+        import numpy as np
+        p = np.ascontiguousarray(np.concatenate([np.broadcast_to(np.asarray(x, dtype=np.float32), (l,))
+                                                 for x, l in zip(prefs, self.L)]))
+        check(lib.hap_batch_set_preferences(self._h, p.ctypes.data_as(ctypes.c_void_p)), "hap_batch_set_preferences")
+
+    def set_similarity(self, b: int, S: torch.Tensor):
+        dt = {torch.float32: 0, torch.bfloat16: 1}[S.dtype]
+        check(lib.hap_batch_set_similarity(self._h, int(b), _ptr(S), S.stride(0), dt), "hap_batch_set_similarity")
+
+    def build_similarity(self, X: torch.Tensor, mode: str = "bf16_split"):
+        """X: (sum N, d) float32 CUDA tensor, instance-major rows."""
+        X = X.contiguous()
+        check(lib.hap_batch_build_similarity(self._h, _ptr(X), X.shape[1], SBUILD[mode]), "hap_batch_build_similarity")
+
+    def iterate(self, n: int = 1):
+        check(lib.hap_batch_iterate(self._h, int(n)), "hap_batch_iterate")
+
+    def tune(self) -> float:
+        ms = ctypes.c_double(0.0)
+        check(lib.hap_batch_tune(self._h, ctypes.byref(ms)), "hap_batch_tune")
+        return ms.value
+
+    def exemplars(self, out: torch.Tensor | None = None):
+        """List of int32 (L[b], N[b]) tensors (views of one flat buffer)."""
+        total = sum(n * l for n, l in zip(self.N, self.L))
+        if out is None:
+            out = torch.empty(total, dtype=torch.int32, device=self.device)
+        check(lib.hap_batch_exemplars(self._h, _ptr(out), 1 if out.device.type == "cpu" else 0), "hap_batch_exemplars")
+        res, q = [], 0
+        for n, l in zip(self.N, self.L):
+            res.append(out[q:q + n * l].view(l, n))
+            q += n * l
+        return res
+
+    def net_similarity(self):
+        import numpy as np
+        ns = np.zeros(sum(self.L), dtype=np.float64)
+        check(lib.hap_batch_net_similarity(self._h, ns.ctypes.data_as(ctypes.c_void_p)), "hap_batch_net_similarity")
+        out, q = [], 0
+        for l in self.L:
+            out.append(ns[q:q + l])
+            q += l
+        return out
+
+    def get_state(self, b: int):
+        n, l = self.N[b], self.L[b]
+        A = torch.empty((l, n, n), dtype=torch.float32, device=self.device)
+        R = torch.empty_like(A)
+        vecs = torch.empty((3, l, n), dtype=torch.float32, device=self.device)
+        it = ctypes.c_int64(0)
+        check(lib.hap_batch_get_state(self._h, int(b), _ptr(A), _ptr(R), _ptr(vecs), ctypes.byref(it)),
+              "hap_batch_get_state")
+        check(lib.hap_batch_sync(self._h), "hap_batch_sync")
+        return {"A": A, "R": R, "c": vecs[0], "tau": vecs[1], "phi": vecs[2], "t": it.value}
+
+    def query(self, key: int) -> int:
+        v = ctypes.c_int64(0)
+        check(lib.hap_batch_query(self._h, key, ctypes.byref(v)), "hap_batch_query")
+        return v.value
+
+    def sync(self):
+        check(lib.hap_batch_sync(self._h), "hap_batch_sync")

@@ -1,0 +1,98 @@
+"""Batched instances (one persistent launch per iteration) against the
+single-instance path and the FP64 reference."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import hap_oracle as H
+from paper_1403_7394_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+TOL = 1e-4
+
+
+def _instances(Ns, Ls, seed=0, d=2):
+    out = []
+    for q, (n, l) in enumerate(zip(Ns, Ls)):
+        X, _ = W.gmm_points(n, d, 5, sigma=0.6, seed=seed + q, means="uniform", mean_scale=10.0)
+        S32 = H.neg_sq_euclidean(X).astype(np.float32)
+        p = np.float32(H.median_preference(S32.astype(np.float64)))
+        prefs = np.array([p * (1.0 + 0.5 * k) for k in range(l)], dtype=np.float32)
+        out.append((X.astype(np.float32), S32, prefs))
+    return out
+
+
+def _np(x):
+    return x.cpu().numpy().astype(np.float64) if torch.is_tensor(x) else np.asarray(x, dtype=np.float64)
+
+
+def _errs(g, ref):
+    get = (lambda k: ref[k]) if isinstance(ref, dict) else (lambda k: getattr(ref, k))
+    return {k: H.message_rel_error(_np(g[k]), _np(get(k))) for k in ("A", "R", "c", "tau", "phi")}
+
+
+@pytest.mark.parametrize("c_mode", ["paper", "fixed"])
+def test_batch_matches_single_instances(c_mode, report):
+    from paper_1403_7394_gb300 import hap
+    Ns = [37, 200, 513, 1000, 2100, 4000, 256, 97]
+    Ls = [2, 3, 1, 4, 2, 3, 4, 1]
+    insts = _instances(Ns, Ls, seed=100)
+    bt = hap.HAPBatch(Ns, Ls, damping=0.5, device=DEV, c_mode=c_mode)
+    bt.set_preferences([x[2] for x in insts])
+    for b, (_, S32, _) in enumerate(insts):
+        bt.set_similarity(b, torch.from_numpy(S32).to(DEV))
+    T = 6  # iteration 1 direct, then graph replays
+    bt.iterate(T)
+    e_b = [x.cpu().numpy() for x in bt.exemplars()]
+    ns_b = bt.net_similarity()
+    worst = 0.0
+    for b, (_, S32, prefs) in enumerate(insts):
+        ctx = hap.HAP(Ns[b], Ls[b], prefs=prefs, damping=0.5, device=DEV, c_mode=c_mode)
+        ctx.set_similarity(torch.from_numpy(S32).to(DEV))
+        ctx.iterate(T)
+        errs = _errs(bt.get_state(b), ctx.get_state())
+        worst = max(worst, max(errs.values()))
+        assert all(e <= TOL for e in errs.values()), (b, errs)
+        np.testing.assert_array_equal(e_b[b], ctx.exemplars().cpu().numpy())
+        np.testing.assert_allclose(ns_b[b], ctx.net_similarity(), rtol=1e-9)
+        ctx.close()
+    report(worst=worst, launches=bt.query(7))
+    bt.close()
+
+
+def test_batch_against_reference_and_tuner():
+    from paper_1403_7394_gb300 import hap
+    Ns, Ls = [300, 64, 700], [3, 2, 2]
+    insts = _instances(Ns, Ls, seed=7)
+    bt = hap.HAPBatch(Ns, Ls, damping=0.6, device=DEV)
+    bt.set_preferences([x[2] for x in insts])
+    for b, (_, S32, _) in enumerate(insts):
+        bt.set_similarity(b, torch.from_numpy(S32).to(DEV))
+    ms = bt.tune()
+    assert ms > 0 and bt.query(8) in (1, 2, 3, 4, 6)
+    bt.iterate(4)
+    for b, (_, S32, prefs) in enumerate(insts):
+        ref = H.run(H.level_similarities(S32.astype(np.float64), prefs.astype(np.float64)), 4, 0.6, H.PAPER)
+        errs = _errs(bt.get_state(b), ref)
+        assert all(e <= TOL for e in errs.values()), (b, errs)
+    bt.close()
+
+
+def test_batch_build_similarity_tensor_cores():
+    from paper_1403_7394_gb300 import hap
+    Ns, Ls = [250, 1030, 64], [2, 3, 2]
+    insts = _instances(Ns, Ls, seed=3, d=32)
+    X = torch.from_numpy(np.concatenate([x[0] for x in insts])).to(DEV)
+    bt = hap.HAPBatch(Ns, Ls, damping=0.5, device=DEV)
+    bt.set_preferences([x[2] for x in insts])
+    bt.build_similarity(X, mode="bf16_split")
+    bt.iterate(3)
+    for b, (X32, _, prefs) in enumerate(insts):
+        ctx = hap.HAP(Ns[b], Ls[b], prefs=prefs, damping=0.5, device=DEV)
+        ctx.build_similarity(torch.from_numpy(X32).to(DEV), mode="bf16_split")
+        ctx.iterate(3)
+        errs = _errs(bt.get_state(b), ctx.get_state())
+        assert all(e <= TOL for e in errs.values()), (b, errs)
+        ctx.close()
+    bt.close()
