@@ -144,11 +144,32 @@ __global__ void __launch_bounds__(kBT, 1) rowpass_batched_kernel(const BatchArgs
 #pragma unroll
         for (int k = 0; k < kBK; ++k) srow[k] = make_float4(0.f, 0.f, 0.f, 0.f);
         float c_prev = 0.f;
+        // per-column b and per-row scalars of the next step, loaded ahead
+        float4 nb[kBK];
+        float npref = 0.f, nc = 0.f, ntp = 0.f;
+        auto prefetch = [&](int q) {
+            const int pm = q / L, pl = q % L;
+            const int prow = (itm.band + pm * in.G) * in.rps + r;
+            const bool prv = prow < N;
+            const int64_t pv = (int64_t)pl * ld;
+#pragma unroll
+            for (int k = 0; k < kBK; ++k)
+                nb[k] = (pending && ok[k] && prv) ? __ldg(reinterpret_cast<const float4*>(in.b + pv + col[k])) : f4_splat(0.f);
+            npref = prv ? __ldg(in.pref + pv + prow) : 0.f;
+            nc = (!p.update_c && prv) ? in.c[pv + prow] : 0.f;
+            ntp = (p.use_tau && pl > 0 && prv) ? __ldg(in.tpart + pv + prow) : 0.f;
+        };
+        if (itm.nsteps > 0) prefetch(0);
         for (int q = 0; q < itm.nsteps; ++q, ++step) {
             const int m = q / L, l = q % L;
             const int i0 = (itm.band + m * in.G) * in.rps;
             const int row = i0 + r;
             const bool rv = row < N;  // this group's row exists
+            float4 bcur[kBK];
+#pragma unroll
+            for (int k = 0; k < kBK; ++k) bcur[k] = nb[k];
+            const float pref_i = npref, c_fixed = nc, tpart_i = ntp;
+            if (q + 1 < itm.nsteps) prefetch(q + 1);
             const int st = step % kBStages;
             const unsigned char* base = sm + (size_t)st * STAGE;
             const float* sA = reinterpret_cast<const float*>(base) + (size_t)r * ld;
@@ -157,7 +178,6 @@ __global__ void __launch_bounds__(kBT, 1) rowpass_batched_kernel(const BatchArgs
             if (!bad) bad = !mbar_wait(bar0 + 8 * st, (uint32_t)(step / kBStages) & 1u, p.status);
             const int64_t voff = (int64_t)l * ld;
             const int64_t off = ((int64_t)l * N + row) * ld;
-            const float pref_i = rv ? in.pref[voff + row] : 0.f;
 
             float m1 = -kInf, m2 = -kInf, cm = -kInf;
             int k1 = 0x7fffffff;
@@ -173,9 +193,8 @@ __global__ void __launch_bounds__(kBT, 1) rowpass_batched_kernel(const BatchArgs
                     s4 = srow[k];
                 }
                 float4 an = a4;
-                float4 b4 = f4_splat(0.f);
+                const float4 b4 = bcur[k];
                 if (pending) {
-                    if (live) b4 = __ldg(reinterpret_cast<const float4*>(in.b + voff + col[k]));
                     an.x = damp(a4.x, avail_target(b4.x, r4.x, false), lam, oml);
                     an.y = damp(a4.y, avail_target(b4.y, r4.y, false), lam, oml);
                     an.z = damp(a4.z, avail_target(b4.z, r4.z, false), lam, oml);
@@ -211,8 +230,8 @@ __global__ void __launch_bounds__(kBT, 1) rowpass_batched_kernel(const BatchArgs
                 cm = fmaxf(cm, v.z);
             }
             // ---- inter-level messages (Eqs. 2.4-2.6) ---------------------------
-            const float cval = p.update_c ? cm : (rv ? in.c[voff + row] : 0.f);
-            const float tauv = (p.use_tau && l > 0 && rv) ? __fadd_rn(c_prev, in.tpart[voff + row]) : kInf;
+            const float cval = p.update_c ? cm : c_fixed;
+            const float tauv = (p.use_tau && l > 0 && rv) ? __fadd_rn(c_prev, tpart_i) : kInf;
             c_prev = cval;
             if (rv && t == 0 && !bad) {
                 if (p.update_c) in.c[voff + row] = cval;
