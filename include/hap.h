@@ -231,6 +231,88 @@ int hap_batch_tune(hap_batch* batch, double* best_ms);
 int hap_batch_query(hap_batch* batch, int key, int64_t* value);
 int hap_batch_sync(hap_batch* batch);
 
+/* ---- learned candidate proposal and sparse HAP ------------------------------
+ * Not in the paper (its method is dense, §2): each row keeps K candidate
+ * exemplars so that large N needs N*K messages instead of N^2.  Sparse HAP is
+ * exactly HAP on a similarity that is -inf outside the candidate graph.  The
+ * candidates come from an exact kNN pool, optionally re-ranked by a small MLP
+ * that scores how likely each point is an exemplar from its kNN distances.  */
+
+/* Exact M nearest neighbours of every point by squared Euclidean distance,
+ * itself excluded, ties to the lower index.  X device FP32 [N][d] (d <= 64);
+ * idx int32 / dist FP32 device [N][M] sorted ascending; 1 <= M <= 128, M < N.
+ * Asynchronous on `stream`. */
+int hap_knn(const float* X, int64_t N, int64_t d, int M, int32_t* idx, float* dist, void* stream);
+
+/* Features f_q(i) = log(dist[i][q]) - mean_i log(dist[i][F-1]), q < F <= 32,
+ * from hap_knn distances ([N][M] device) into feats device [N][F].  The
+ * subtracted mean is returned in *log_scale (host, may be NULL).
+ * Synchronising. */
+int hap_knn_features(const float* dist, int64_t N, int M, int F, float* feats, float* log_scale, void* stream);
+
+/* MLP proposal network: logit = W3 . relu(W2^T relu(W1^T f + b1) + b2) + b3,
+ * width 128, F inputs.  FP32 master parameters (flat: W1 [F][128], b1 [128],
+ * W2 [128][128], b2 [128], W3 [128], b3 [1]), BF16 copies of the weights used
+ * by forward and backward with FP32 accumulation.  theta0: host FP32 [P]. */
+typedef struct hap_mlp hap_mlp;
+int hap_mlp_create(int F, const float* theta0, hap_mlp** out);
+void hap_mlp_destroy(hap_mlp* mlp);
+int hap_mlp_set_stream(hap_mlp* mlp, void* stream);
+int hap_mlp_num_params(hap_mlp* mlp, int64_t* P);
+/* FP32 master parameters into host theta [P].  Synchronising. */
+int hap_mlp_get_params(hap_mlp* mlp, float* theta);
+/* logits device [n] from feats device [n][F].  Asynchronous. */
+int hap_mlp_forward(hap_mlp* mlp, const float* feats, int64_t n, float* logits);
+/* Gradients of mean_s w_s (softplus(z_s) - y_s z_s), w_s = pos_weight for
+ * y_s = 1 else 1, with respect to the FP32 parameters (host [P], may be
+ * NULL) and the loss (host, may be NULL).  labels device [n] in {0, 1}. */
+int hap_mlp_gradients(hap_mlp* mlp, const float* feats, const float* labels, int64_t n, float pos_weight,
+                      float* grads, float* loss);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on those gradients; the
+ * loss before the step goes to *loss (host, may be NULL). */
+int hap_mlp_train_step(hap_mlp* mlp, const float* feats, const float* labels, int64_t n, float pos_weight, float lr,
+                       float* loss);
+
+/* Candidates per row from a kNN pool ([N][M] device, M <= 128): the row
+ * itself, the K_near nearest, and the K - 1 - K_near pool members beyond
+ * those with the highest score (device [N], lower pool position on ties);
+ * score NULL: the K - 1 nearest.  cand device int32 [N][K], each row sorted
+ * by index; K <= 64, M >= K - 1.  Asynchronous. */
+int hap_select_candidates(const int32_t* pool, int64_t N, int M, const float* score, int K, int K_near,
+                          int32_t* cand, void* stream);
+
+/* Sparse HAP context: N points, L levels, K candidates per row (K <= 64),
+ * damping, c_mode (HAP_C_*), one preference per level (host [L], NULL = 0).
+ * Allocates its device memory; same equations and schedule as hap_iterate. */
+typedef struct hap_sparse hap_sparse;
+int hap_sparse_create(int64_t N, int L, int K, const float* prefs, float damping, int c_mode, hap_sparse** out);
+void hap_sparse_destroy(hap_sparse* sp);
+int hap_sparse_set_stream(hap_sparse* sp, void* stream);
+/* host prefs: [L] (per_point 0) or [L][N] (per_point 1). */
+int hap_sparse_set_preferences(hap_sparse* sp, const float* prefs, int per_point);
+/* Candidate graph (device int32 [N][K], every row sorted, containing the row
+ * itself; checked, HAP_EINVAL otherwise) and points (device FP32 [N][d]):
+ * s = -||x_i - x_j||^2 on the graph.  X is borrowed until the next call for
+ * hap_sparse_net_similarity.  Resets the messages.  Synchronising. */
+int hap_sparse_set_candidates(hap_sparse* sp, const int32_t* cand, const float* X, int64_t d);
+int hap_sparse_iterate(hap_sparse* sp, int n);
+/* Eq. 2.8 over the candidates: int32 [L][N] global exemplar indices. */
+int hap_sparse_exemplars(hap_sparse* sp, int32_t* e, int on_host);
+/* NS^l = sum_i -||x_i - x_{e_i}||^2 (preference for e_i = i) in FP64 from the
+ * points, host double [L].  Synchronising. */
+int hap_sparse_net_similarity(hap_sparse* sp, double* ns);
+/* alpha, rho device [L][N][K] (entry q of row i is candidate cand[i][q]);
+ * vecs device [3][L][N] (c, tau, phi).  Asynchronous. */
+int hap_sparse_get_state(hap_sparse* sp, float* A, float* R, float* vecs, int64_t* iter);
+int hap_sparse_query(hap_sparse* sp, int key, int64_t* value);
+
+/* Net similarity of any assignment from the points: NS^l = sum_i
+ * -||x_i - x_{e_i}||^2, preference pref[l][i] (device FP32 [L][N]) when
+ * e_i = i; X device [N][d], e device int32 [L][N]; ns host double [L].
+ * Synchronising. */
+int hap_net_similarity_points(const float* X, int64_t N, int64_t d, int L, const int32_t* e, const float* pref,
+                              double* ns, void* stream);
+
 /* Allocation-free iterations on caller-owned messages.  The paper has no
  * counterpart: this entry point exists for callers that cannot call
  * cudaMalloc - for example a plugin inside a host application that owns and

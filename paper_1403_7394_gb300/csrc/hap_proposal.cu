@@ -1,0 +1,629 @@
+// Learned candidate proposal: exact k nearest neighbours, kNN-distance
+// features, a 3-layer MLP (width 128, BF16 weights, FP32 accumulation) with
+// forward, backward and Adam kernels, and per-row candidate selection.
+//
+// None of this is in the paper (§2 is dense); it prunes each row of HAP to K
+// candidate exemplars so that large N needs N*K instead of N^2 messages.
+// Reductions are in fixed order (per-CTA partials summed in CTA order), so
+// training is bitwise reproducible.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <new>
+#include <vector>
+
+#include "hap.h"
+#include "hap_common.cuh"
+#include "hap_internal.h"
+
+namespace hap {
+namespace {
+
+// ---------------------------------------------------------------------------
+// exact kNN: one thread per query row, candidates streamed through shared
+// memory in tiles, a stable sorted top-M list per row in shared memory
+// ---------------------------------------------------------------------------
+constexpr int KNN_ROWS = 128;
+constexpr int KNN_TILE = 64;
+constexpr int KNN_MAXM = 128;
+
+template <int D>  // padded dimension, the query vector lives in registers
+__global__ void __launch_bounds__(KNN_ROWS) knn_kernel(const float* __restrict__ X, int N, int d, int M,
+                                                       int32_t* __restrict__ out_idx, float* __restrict__ out_dist) {
+    constexpr int dpad = D;
+    extern __shared__ __align__(16) float ksm[];
+    float* ct = ksm;                                      // [KNN_TILE][dpad]
+    float* tdist = ct + KNN_TILE * dpad;                  // [M][KNN_ROWS]
+    int* tidx = reinterpret_cast<int*>(tdist + M * KNN_ROWS);
+    const int t = threadIdx.x;
+    const int i = blockIdx.x * KNN_ROWS + t;
+    const bool valid = i < N;
+    float q[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) q[k] = (valid && k < d) ? X[(int64_t)i * d + k] : 0.f;
+    int cnt = 0;
+    float thr = kInf;
+    auto insert = [&](float dv, int j) {
+        int p = cnt < M ? cnt : M - 1;
+        if (cnt < M) ++cnt;
+        while (p > 0 && tdist[(p - 1) * KNN_ROWS + t] > dv) {
+            tdist[p * KNN_ROWS + t] = tdist[(p - 1) * KNN_ROWS + t];
+            tidx[p * KNN_ROWS + t] = tidx[(p - 1) * KNN_ROWS + t];
+            --p;
+        }
+        tdist[p * KNN_ROWS + t] = dv;
+        tidx[p * KNN_ROWS + t] = j;
+        thr = cnt == M ? tdist[(M - 1) * KNN_ROWS + t] : kInf;
+    };
+    for (int c0 = 0; c0 < N; c0 += KNN_TILE) {
+        __syncthreads();
+        for (int e = t; e < KNN_TILE * dpad; e += KNN_ROWS) {
+            const int r = e / dpad, k = e - r * dpad, j = c0 + r;
+            ct[e] = (j < N && k < d) ? X[(int64_t)j * d + k] : 0.f;
+        }
+        __syncthreads();
+        if (!valid) continue;
+        const int nc = min(KNN_TILE, N - c0);
+        for (int r = 0; r < nc; r += 4) {  // four candidates in flight
+            float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+            const float* c = ct + r * dpad;
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                const float x = q[k];
+                const float e0 = x - c[k], e1 = x - c[dpad + k], e2 = x - c[2 * dpad + k], e3 = x - c[3 * dpad + k];
+                a0 = fmaf(e0, e0, a0);
+                a1 = fmaf(e1, e1, a1);
+                a2 = fmaf(e2, e2, a2);
+                a3 = fmaf(e3, e3, a3);
+            }
+            const float dv[4] = {a0, a1, a2, a3};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int j = c0 + r + u;
+                if (r + u < nc && j != i && (cnt < M || dv[u] < thr)) insert(dv[u], j);
+            }
+        }
+    }
+    if (valid)
+        for (int m = 0; m < M; ++m) {
+            out_idx[(int64_t)i * M + m] = m < cnt ? tidx[m * KNN_ROWS + t] : -1;
+            out_dist[(int64_t)i * M + m] = m < cnt ? tdist[m * KNN_ROWS + t] : kInf;
+        }
+}
+
+// mean over rows of log(dist[i][F-1]) in FP64: per-block partials, fixed order
+__global__ void log_mean_partial_kernel(const float* __restrict__ dist, int N, int M, int col, double* __restrict__ part) {
+    __shared__ double red[256];
+    double acc = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x)
+        acc += log(fmax((double)dist[(int64_t)i * M + col], 1e-30));
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+__global__ void features_kernel(const float* __restrict__ dist, int N, int M, int F, float log_scale,
+                                float* __restrict__ feats) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)N * F) return;
+    const int64_t i = e / F;
+    const int q = (int)(e - i * F);
+    feats[e] = logf(fmaxf(dist[i * M + q], 1e-30f)) - log_scale;
+}
+
+// ---------------------------------------------------------------------------
+// MLP: logits = W3 . relu(W2^T relu(W1^T f + b1) + b2) + b3, width 128
+// ---------------------------------------------------------------------------
+constexpr int MH = 128;     // width
+constexpr int MS = 32;      // samples per tile
+constexpr int MAXF = 32;    // input features
+constexpr int W2LD = MH + 1;  // padded row stride of W2 in shared memory
+
+// offsets of the flat FP32 parameter vector
+struct MLPLayout {
+    int F, P, oW1, ob1, oW2, ob2, oW3, ob3;
+};
+__host__ __device__ inline MLPLayout mlp_layout(int F) {
+    MLPLayout y;
+    y.F = F;
+    y.oW1 = 0;
+    y.ob1 = y.oW1 + F * MH;
+    y.oW2 = y.ob1 + MH;
+    y.ob2 = y.oW2 + MH * MH;
+    y.oW3 = y.ob2 + MH;
+    y.ob3 = y.oW3 + MH;
+    y.P = y.ob3 + 1;
+    return y;
+}
+
+struct MLPSmem {
+    float* W2;   // [MH][W2LD]
+    float* W1;   // [MAXF][MH]
+    float* x;    // [MS][MAXF]
+    float* h1;   // [MS][MH]
+    float* red;  // [MS][4] per-warp partials
+    float* g;    // [MS]
+    float* lq;   // [MS] per-sample loss terms
+    float* d2;   // [MS][MH]
+    float* dW2;  // [MH][W2LD]
+};
+__device__ inline MLPSmem mlp_smem(float* base, bool train) {
+    MLPSmem m;
+    m.W2 = base;
+    m.W1 = m.W2 + MH * W2LD;
+    m.x = m.W1 + MAXF * MH;
+    m.h1 = m.x + MS * MAXF;
+    m.red = m.h1 + MS * MH;
+    m.g = m.red + MS * 4;
+    m.lq = m.g + MS;
+    m.d2 = m.lq + MS;
+    m.dW2 = train ? m.d2 + MS * MH : nullptr;
+    return m;
+}
+size_t mlp_smem_bytes(bool train) {
+    size_t f = (size_t)MH * W2LD + MAXF * MH + MS * MAXF + MS * MH + MS * 4 + 2 * MS + MS * MH;
+    if (train) f += (size_t)MH * W2LD;
+    return f * sizeof(float);
+}
+
+__device__ inline float bf(const __nv_bfloat16 v) { return __bfloat162float(v); }
+
+// Loads the BF16 weights as FP32 into shared memory (W1, W2).
+__device__ void mlp_load_weights(const MLPSmem& s, int F, const __nv_bfloat16* W1h, const __nv_bfloat16* W2h) {
+    for (int e = threadIdx.x; e < MH * MH; e += MH) s.W2[(e / MH) * W2LD + (e % MH)] = bf(W2h[e]);
+    for (int e = threadIdx.x; e < F * MH; e += MH) s.W1[e] = bf(W1h[e]);
+}
+
+// Forward of one tile for thread u: h1 (shared), h2 (registers), logits.
+__device__ void mlp_tile_forward(const MLPSmem& s, int F, int ns, const float* b1, const float* b2,
+                                 float w3u, float b3, float (&h2)[MS], float (&logit)[MS], bool (&pos1)[MS]) {
+    const int u = threadIdx.x, lane = u & 31, warp = u >> 5;
+    float a[MS];
+#pragma unroll
+    for (int q = 0; q < MS; ++q) a[q] = b1[u];
+    for (int f = 0; f < F; ++f) {
+        const float w = s.W1[f * MH + u];
+#pragma unroll
+        for (int q = 0; q < MS; ++q) a[q] = fmaf(s.x[q * MAXF + f], w, a[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < MS; ++q) {
+        pos1[q] = a[q] > 0.f;
+        s.h1[q * MH + u] = fmaxf(a[q], 0.f);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < MS; ++q) a[q] = b2[u];
+    for (int v = 0; v < MH; ++v) {
+        const float w = s.W2[v * W2LD + u];
+#pragma unroll
+        for (int q = 0; q < MS; ++q) a[q] = fmaf(s.h1[q * MH + v], w, a[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < MS; ++q) h2[q] = fmaxf(a[q], 0.f);
+    // logits: warp sums then the 4 warps in order
+#pragma unroll
+    for (int q = 0; q < MS; ++q) {
+        float c = h2[q] * w3u;
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+        if (lane == 0) s.red[q * 4 + warp] = c;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < MS; ++q)
+        logit[q] = b3 + ((s.red[q * 4 + 0] + s.red[q * 4 + 1]) + (s.red[q * 4 + 2] + s.red[q * 4 + 3]));
+    (void)ns;
+}
+
+__device__ void mlp_load_tile(const MLPSmem& s, const float* feats, int64_t n, int F, int64_t s0) {
+    for (int e = threadIdx.x; e < MS * MAXF; e += MH) {
+        const int q = e / MAXF, f = e - q * MAXF;
+        const int64_t r = s0 + q;
+        s.x[e] = (r < n && f < F) ? feats[r * F + f] : 0.f;
+    }
+}
+
+__global__ void __launch_bounds__(MH) mlp_forward_kernel(const float* __restrict__ feats, int64_t n, int F,
+                                                        const __nv_bfloat16* __restrict__ W1h, const float* __restrict__ b1,
+                                                        const __nv_bfloat16* __restrict__ W2h, const float* __restrict__ b2,
+                                                        const __nv_bfloat16* __restrict__ W3h, const float* __restrict__ b3,
+                                                        float* __restrict__ out) {
+    extern __shared__ __align__(16) float msm[];
+    const MLPSmem s = mlp_smem(msm, false);
+    mlp_load_weights(s, F, W1h, W2h);
+    const float w3u = bf(W3h[threadIdx.x]);
+    const float bb3 = b3[0];
+    for (int64_t s0 = (int64_t)blockIdx.x * MS; s0 < n; s0 += (int64_t)gridDim.x * MS) {
+        __syncthreads();
+        mlp_load_tile(s, feats, n, F, s0);
+        __syncthreads();
+        float h2[MS], logit[MS];
+        bool pos1[MS];
+        mlp_tile_forward(s, F, 0, b1, b2, w3u, bb3, h2, logit, pos1);
+        if (threadIdx.x < MS && s0 + threadIdx.x < n) {
+            float v = 0.f;
+#pragma unroll
+            for (int q = 0; q < MS; ++q)
+                if (q == (int)threadIdx.x) v = logit[q];
+            out[s0 + threadIdx.x] = v;
+        }
+    }
+}
+
+// Forward + backward over all samples; per-CTA gradient partials [P] and
+// loss partial, summed in CTA order by mlp_reduce_kernel.
+__global__ void __launch_bounds__(MH) mlp_grad_kernel(const float* __restrict__ feats, const float* __restrict__ labels,
+                                                     int64_t n, int F, float pos_weight,
+                                                     const __nv_bfloat16* __restrict__ W1h, const float* __restrict__ b1,
+                                                     const __nv_bfloat16* __restrict__ W2h, const float* __restrict__ b2,
+                                                     const __nv_bfloat16* __restrict__ W3h, const float* __restrict__ b3,
+                                                     float* __restrict__ gpart, float* __restrict__ lpart) {
+    extern __shared__ __align__(16) float msm[];
+    const MLPSmem s = mlp_smem(msm, true);
+    const MLPLayout y = mlp_layout(F);
+    const int u = threadIdx.x;
+    mlp_load_weights(s, F, W1h, W2h);
+    for (int e = u; e < MH * W2LD; e += MH) s.dW2[e] = 0.f;
+    const float w3u = bf(W3h[u]);
+    const float bb3 = b3[0];
+    float gW3 = 0.f, gb3 = 0.f, gb2 = 0.f, gb1 = 0.f, loss = 0.f;
+    float gW1[MAXF];
+#pragma unroll
+    for (int f = 0; f < MAXF; ++f) gW1[f] = 0.f;
+    const float inv_n = 1.0f / (float)n;
+    for (int64_t s0 = (int64_t)blockIdx.x * MS; s0 < n; s0 += (int64_t)gridDim.x * MS) {
+        __syncthreads();
+        mlp_load_tile(s, feats, n, F, s0);
+        __syncthreads();
+        float h2[MS], logit[MS];
+        bool pos1[MS];
+        mlp_tile_forward(s, F, 0, b1, b2, w3u, bb3, h2, logit, pos1);
+        // d loss / d logit for the tile's samples (thread q < MS)
+        if (u < MS) {
+            float z = 0.f;
+#pragma unroll
+            for (int q = 0; q < MS; ++q)
+                if (q == u) z = logit[q];
+            const int64_t r = s0 + u;
+            float gq = 0.f;
+            if (r < n) {
+                const float yv = labels[r];
+                const float w = yv > 0.5f ? pos_weight : 1.f;
+                const float sp = fmaxf(z, 0.f) + log1pf(expf(-fabsf(z)));  // softplus
+                s.lq[u] = w * (sp - yv * z);
+                gq = w * (1.f / (1.f + expf(-z)) - yv) * inv_n;
+            } else {
+                s.lq[u] = 0.f;
+            }
+            s.g[u] = gq;
+        }
+        __syncthreads();
+        if (u == 0)
+            for (int q = 0; q < MS; ++q) loss += s.lq[q];
+        // output layer and d2 = g W3 [z2 > 0]
+#pragma unroll
+        for (int q = 0; q < MS; ++q) {
+            const float gq = s.g[q];
+            gW3 = fmaf(gq, h2[q], gW3);
+            const float d = h2[q] > 0.f ? gq * w3u : 0.f;
+            s.d2[q * MH + u] = d;
+            gb2 += d;
+        }
+        if (u == 0)
+            for (int q = 0; q < MS; ++q) gb3 += s.g[q];
+        __syncthreads();
+        // dW2[v][u] += sum_q h1[q][v] d2[q][u]  (thread u owns column u)
+        for (int v = 0; v < MH; ++v) {
+            float acc = 0.f;
+#pragma unroll
+            for (int q = 0; q < MS; ++q) acc = fmaf(s.h1[q * MH + v], s.d2[q * MH + u], acc);
+            s.dW2[v * W2LD + u] += acc;
+        }
+        // d1[q][v] = (sum_u d2[q][u] W2[v][u]) [z1 > 0]   (thread v = u)
+        const int v = u;
+        float d1[MS];
+#pragma unroll
+        for (int q = 0; q < MS; ++q) d1[q] = 0.f;
+        for (int uu = 0; uu < MH; ++uu) {
+            const float w = s.W2[v * W2LD + uu];
+#pragma unroll
+            for (int q = 0; q < MS; ++q) d1[q] = fmaf(s.d2[q * MH + uu], w, d1[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < MS; ++q) {
+            const float dq = pos1[q] ? d1[q] : 0.f;
+            gb1 += dq;
+#pragma unroll
+            for (int f = 0; f < MAXF; ++f)
+                if (f < F) gW1[f] = fmaf(s.x[q * MAXF + f], dq, gW1[f]);
+        }
+    }
+    __syncthreads();
+    float* gp = gpart + (int64_t)blockIdx.x * y.P;
+#pragma unroll
+    for (int f = 0; f < MAXF; ++f)
+        if (f < F) gp[y.oW1 + f * MH + u] = gW1[f];
+    gp[y.ob1 + u] = gb1;
+    for (int vv = 0; vv < MH; ++vv) gp[y.oW2 + vv * MH + u] = s.dW2[vv * W2LD + u];
+    gp[y.ob2 + u] = gb2;
+    gp[y.oW3 + u] = gW3;
+    if (u == 0) {
+        gp[y.ob3] = gb3;
+        lpart[blockIdx.x] = loss;
+    }
+}
+
+__global__ void mlp_reduce_kernel(const float* __restrict__ gpart, const float* __restrict__ lpart, int ncta, int P,
+                                  int64_t n, float* __restrict__ grads, float* __restrict__ loss) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < P) {
+        float acc = 0.f;
+        for (int c = 0; c < ncta; ++c) acc += gpart[(int64_t)c * P + p];
+        grads[p] = acc;
+    }
+    if (p == 0) {
+        double l = 0.0;
+        for (int c = 0; c < ncta; ++c) l += lpart[c];
+        loss[0] = (float)(l / (double)n);
+    }
+}
+
+// Adam on the FP32 master parameters, then the BF16 weight copies.
+__global__ void adam_kernel(float* __restrict__ theta, float* __restrict__ m, float* __restrict__ v,
+                            const float* __restrict__ g, int P, float lr, float b1, float b2, float eps, float c1,
+                            float c2, int F, __nv_bfloat16* __restrict__ W1h, __nv_bfloat16* __restrict__ W2h,
+                            __nv_bfloat16* __restrict__ W3h) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    const float gp = g[p];
+    const float mp = b1 * m[p] + (1.f - b1) * gp;
+    const float vp = b2 * v[p] + (1.f - b2) * gp * gp;
+    m[p] = mp;
+    v[p] = vp;
+    const float th = theta[p] - lr * (mp / c1) / (sqrtf(vp / c2) + eps);
+    theta[p] = th;
+    const MLPLayout y = mlp_layout(F);
+    if (p < y.ob1) W1h[p - y.oW1] = __float2bfloat16_rn(th);
+    else if (p >= y.oW2 && p < y.ob2) W2h[p - y.oW2] = __float2bfloat16_rn(th);
+    else if (p >= y.oW3 && p < y.ob3) W3h[p - y.oW3] = __float2bfloat16_rn(th);
+}
+
+__global__ void refresh_bf16_kernel(const float* __restrict__ theta, int P, int F, __nv_bfloat16* __restrict__ W1h,
+                                    __nv_bfloat16* __restrict__ W2h, __nv_bfloat16* __restrict__ W3h) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    const MLPLayout y = mlp_layout(F);
+    const float th = theta[p];
+    if (p < y.ob1) W1h[p - y.oW1] = __float2bfloat16_rn(th);
+    else if (p >= y.oW2 && p < y.ob2) W2h[p - y.oW2] = __float2bfloat16_rn(th);
+    else if (p >= y.oW3 && p < y.ob3) W3h[p - y.oW3] = __float2bfloat16_rn(th);
+}
+
+// ---------------------------------------------------------------------------
+// candidate selection: self + K_near nearest + highest-scoring pool members
+// ---------------------------------------------------------------------------
+__global__ void select_candidates_kernel(const int32_t* __restrict__ pool, int N, int M, const float* __restrict__ score,
+                                         int K, int K_near, int32_t* __restrict__ cand) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    int sel[64];
+    int ns = 0;
+    sel[ns++] = i;
+    const int32_t* pi = pool + (int64_t)i * M;
+    if (!score) {
+        for (int q = 0; q < K - 1; ++q) sel[ns++] = pi[q];
+    } else {
+        for (int q = 0; q < K_near; ++q) sel[ns++] = pi[q];
+        uint32_t used[4] = {0u, 0u, 0u, 0u};  // pool positions already taken (M <= 128)
+        for (int r = 0; r < K - 1 - K_near; ++r) {
+            int best = -1;
+            float bs = -kInf;
+            for (int q = K_near; q < M; ++q) {
+                if (used[q >> 5] & (1u << (q & 31))) continue;
+                const float sv = score[pi[q]];
+                if (best < 0 || sv > bs) { bs = sv; best = q; }
+            }
+            used[best >> 5] |= 1u << (best & 31);
+            sel[ns++] = pi[best];
+        }
+    }
+    for (int a = 1; a < K; ++a) {  // sort by index
+        const int v = sel[a];
+        int b = a - 1;
+        while (b >= 0 && sel[b] > v) { sel[b + 1] = sel[b]; --b; }
+        sel[b + 1] = v;
+    }
+    for (int q = 0; q < K; ++q) cand[(int64_t)i * K + q] = sel[q];
+}
+
+}  // namespace
+}  // namespace hap
+
+using namespace hap;
+
+#define PCU(x)                          \
+    do {                                \
+        if ((x) != cudaSuccess) {       \
+            cudaGetLastError();         \
+            return HAP_ECUDA;           \
+        }                               \
+    } while (0)
+
+struct hap_mlp {
+    int F = 0;
+    MLPLayout y{};
+    float* theta = nullptr;  // FP32 master parameters [P]
+    float* m = nullptr;
+    float* v = nullptr;
+    float* grads = nullptr;
+    float* loss = nullptr;
+    __nv_bfloat16* W1h = nullptr;
+    __nv_bfloat16* W2h = nullptr;
+    __nv_bfloat16* W3h = nullptr;
+    float* gpart = nullptr;
+    float* lpart = nullptr;
+    int ncta = 0;
+    int64_t step = 0;
+    cudaStream_t stream = nullptr;
+};
+
+extern "C" {
+
+int hap_knn(const float* X, int64_t N, int64_t d, int M, int32_t* idx, float* dist, void* stream) {
+    if (!X || !idx || !dist || N < 2 || d < 1 || d > 64 || M < 1 || M > KNN_MAXM || M >= N) return HAP_EINVAL;
+    const int D = d <= 4 ? 4 : d <= 8 ? 8 : d <= 16 ? 16 : d <= 32 ? 32 : 64;
+    const size_t smem = ((size_t)KNN_TILE * D + (size_t)M * KNN_ROWS * 2) * 4;
+    const unsigned grid = (unsigned)((N + KNN_ROWS - 1) / KNN_ROWS);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+#define HAP_KNN_CASE(DD)                                                                                \
+    if (D == DD) {                                                                                      \
+        PCU(cudaFuncSetAttribute(knn_kernel<DD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
+        knn_kernel<DD><<<grid, KNN_ROWS, smem, st>>>(X, (int)N, (int)d, M, idx, dist);                 \
+    }
+    HAP_KNN_CASE(4) HAP_KNN_CASE(8) HAP_KNN_CASE(16) HAP_KNN_CASE(32) HAP_KNN_CASE(64)
+#undef HAP_KNN_CASE
+    PCU(cudaGetLastError());
+    return HAP_OK;
+}
+
+int hap_knn_features(const float* dist, int64_t N, int M, int F, float* feats, float* log_scale_out, void* stream) {
+    if (!dist || !feats || N < 1 || F < 1 || F > M || F > MAXF) return HAP_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int nb = 64;
+    std::vector<double> part(nb);
+    double* dpart = nullptr;
+    PCU(cudaMallocAsync(&dpart, nb * sizeof(double), st));
+    log_mean_partial_kernel<<<nb, 256, 0, st>>>(dist, (int)N, M, F - 1, dpart);
+    PCU(cudaGetLastError());
+    PCU(cudaMemcpyAsync(part.data(), dpart, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+    PCU(cudaFreeAsync(dpart, st));
+    PCU(cudaStreamSynchronize(st));
+    double tot = 0.0;
+    for (double x : part) tot += x;
+    const float ls = (float)(tot / (double)N);
+    if (log_scale_out) *log_scale_out = ls;
+    const int64_t n = N * F;
+    features_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(dist, (int)N, M, F, ls, feats);
+    PCU(cudaGetLastError());
+    return HAP_OK;
+}
+
+int hap_mlp_create(int F, const float* theta0, hap_mlp** out) {
+    if (!out || F < 1 || F > MAXF || !theta0) return HAP_EINVAL;
+    hap_mlp* h = new (std::nothrow) hap_mlp();
+    if (!h) return HAP_ENOMEM;
+    h->F = F;
+    h->y = mlp_layout(F);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    h->ncta = sms;
+    const size_t P = h->y.P;
+    bool ok = cudaMalloc(&h->theta, P * 4) == cudaSuccess && cudaMalloc(&h->m, P * 4) == cudaSuccess &&
+              cudaMalloc(&h->v, P * 4) == cudaSuccess && cudaMalloc(&h->grads, P * 4) == cudaSuccess &&
+              cudaMalloc(&h->loss, 16) == cudaSuccess && cudaMalloc(&h->W1h, (size_t)F * MH * 2) == cudaSuccess &&
+              cudaMalloc(&h->W2h, (size_t)MH * MH * 2) == cudaSuccess && cudaMalloc(&h->W3h, MH * 2) == cudaSuccess &&
+              cudaMalloc(&h->gpart, (size_t)h->ncta * P * 4) == cudaSuccess &&
+              cudaMalloc(&h->lpart, (size_t)h->ncta * 4) == cudaSuccess;
+    if (!ok) { cudaGetLastError(); hap_mlp_destroy(h); return HAP_ENOMEM; }
+    cudaMemcpy(h->theta, theta0, P * 4, cudaMemcpyHostToDevice);
+    cudaMemset(h->m, 0, P * 4);
+    cudaMemset(h->v, 0, P * 4);
+    const size_t fsm = mlp_smem_bytes(false), tsm = mlp_smem_bytes(true);
+    if (cudaFuncSetAttribute(mlp_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm) != cudaSuccess ||
+        cudaFuncSetAttribute(mlp_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm) != cudaSuccess) {
+        cudaGetLastError();
+        hap_mlp_destroy(h);
+        return HAP_ECUDA;
+    }
+    refresh_bf16_kernel<<<(unsigned)((P + 255) / 256), 256>>>(h->theta, (int)P, F, h->W1h, h->W2h, h->W3h);
+    if (cudaDeviceSynchronize() != cudaSuccess) { cudaGetLastError(); hap_mlp_destroy(h); return HAP_ECUDA; }
+    *out = h;
+    return HAP_OK;
+}
+
+void hap_mlp_destroy(hap_mlp* h) {
+    if (!h) return;
+    cudaFree(h->theta); cudaFree(h->m); cudaFree(h->v); cudaFree(h->grads); cudaFree(h->loss);
+    cudaFree(h->W1h); cudaFree(h->W2h); cudaFree(h->W3h); cudaFree(h->gpart); cudaFree(h->lpart);
+    delete h;
+}
+
+int hap_mlp_set_stream(hap_mlp* h, void* stream) {
+    if (!h) return HAP_EINVAL;
+    h->stream = static_cast<cudaStream_t>(stream);
+    return HAP_OK;
+}
+
+int hap_mlp_num_params(hap_mlp* h, int64_t* P) {
+    if (!h || !P) return HAP_EINVAL;
+    *P = h->y.P;
+    return HAP_OK;
+}
+
+int hap_mlp_get_params(hap_mlp* h, float* theta_host) {
+    if (!h || !theta_host) return HAP_EINVAL;
+    PCU(cudaMemcpyAsync(theta_host, h->theta, (size_t)h->y.P * 4, cudaMemcpyDeviceToHost, h->stream));
+    PCU(cudaStreamSynchronize(h->stream));
+    return HAP_OK;
+}
+
+int hap_mlp_forward(hap_mlp* h, const float* feats, int64_t n, float* logits) {
+    if (!h || !feats || !logits || n < 1) return HAP_EINVAL;
+    const MLPLayout& y = h->y;
+    const int grid = (int)std::min<int64_t>((n + MS - 1) / MS, (int64_t)h->ncta * 4);
+    mlp_forward_kernel<<<grid, MH, mlp_smem_bytes(false), h->stream>>>(feats, n, h->F, h->W1h, h->theta + y.ob1, h->W2h,
+                                                                       h->theta + y.ob2, h->W3h, h->theta + y.ob3, logits);
+    PCU(cudaGetLastError());
+    return HAP_OK;
+}
+
+int hap_mlp_gradients(hap_mlp* h, const float* feats, const float* labels, int64_t n, float pos_weight,
+                      float* grads_host, float* loss_host) {
+    if (!h || !feats || !labels || n < 1) return HAP_EINVAL;
+    const MLPLayout& y = h->y;
+    mlp_grad_kernel<<<h->ncta, MH, mlp_smem_bytes(true), h->stream>>>(feats, labels, n, h->F, pos_weight, h->W1h,
+                                                                     h->theta + y.ob1, h->W2h, h->theta + y.ob2, h->W3h,
+                                                                     h->theta + y.ob3, h->gpart, h->lpart);
+    PCU(cudaGetLastError());
+    mlp_reduce_kernel<<<(unsigned)((y.P + 255) / 256), 256, 0, h->stream>>>(h->gpart, h->lpart, h->ncta, y.P, n,
+                                                                           h->grads, h->loss);
+    PCU(cudaGetLastError());
+    if (grads_host) PCU(cudaMemcpyAsync(grads_host, h->grads, (size_t)y.P * 4, cudaMemcpyDeviceToHost, h->stream));
+    if (loss_host) PCU(cudaMemcpyAsync(loss_host, h->loss, 4, cudaMemcpyDeviceToHost, h->stream));
+    if (grads_host || loss_host) PCU(cudaStreamSynchronize(h->stream));
+    return HAP_OK;
+}
+
+int hap_mlp_train_step(hap_mlp* h, const float* feats, const float* labels, int64_t n, float pos_weight, float lr,
+                       float* loss_host) {
+    int rc = hap_mlp_gradients(h, feats, labels, n, pos_weight, nullptr, nullptr);
+    if (rc) return rc;
+    h->step += 1;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.f - powf(b1, (float)h->step), c2 = 1.f - powf(b2, (float)h->step);
+    adam_kernel<<<(unsigned)((h->y.P + 255) / 256), 256, 0, h->stream>>>(h->theta, h->m, h->v, h->grads, h->y.P, lr, b1,
+                                                                        b2, 1e-8f, c1, c2, h->F, h->W1h, h->W2h, h->W3h);
+    PCU(cudaGetLastError());
+    if (loss_host) {
+        PCU(cudaMemcpyAsync(loss_host, h->loss, 4, cudaMemcpyDeviceToHost, h->stream));
+        PCU(cudaStreamSynchronize(h->stream));
+    }
+    return HAP_OK;
+}
+
+int hap_select_candidates(const int32_t* pool, int64_t N, int M, const float* score, int K, int K_near, int32_t* cand,
+                          void* stream) {
+    if (!pool || !cand || N < 2 || K < 2 || K > 64 || M < K - 1 || M > KNN_MAXM || K_near < 0 || K_near > K - 1)
+        return HAP_EINVAL;
+    select_candidates_kernel<<<(unsigned)((N + 127) / 128), 128, 0, static_cast<cudaStream_t>(stream)>>>(
+        pool, (int)N, M, score, K, K_near, cand);
+    PCU(cudaGetLastError());
+    return HAP_OK;
+}
+
+}  // extern "C"

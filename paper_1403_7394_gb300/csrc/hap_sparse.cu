@@ -1,0 +1,447 @@
+// Sparse HAP: the messages of §2 (Eqs. 2.1-2.6 with damping, §3 schedule)
+// kept only on a candidate graph with K entries per row (row i's candidate
+// exemplars, including i itself, sorted by index).  It is exactly HAP on a
+// similarity that is -inf outside the graph: such pairs never win a row
+// maximum and add max(0, rho) = 0 to every column sum.
+//
+// Layout: cand [N][K] int32, s [N][K] FP32 (= -||x_i - x_cand||^2, the
+// preference on the self entry), alpha and rho [L][N][K].  Row pass: one warp
+// per row walks the L levels (alpha kept one step behind exactly as in the
+// dense row pass).  Column statistics read rho through a CSC map (for every
+// column j the entries (k, q) with cand[k][q] = j, in entry order), so every
+// sum has a fixed order.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "hap.h"
+#include "hap_common.cuh"
+#include "hap_internal.h"
+
+namespace hap {
+namespace {
+
+constexpr int SP_MAXK = 64;
+
+struct SparseArgs {
+    const int32_t* cand;
+    const float* s;
+    float* A;
+    float* R;
+    const float* pref;
+    float* c;
+    float* tau;
+    float* phi;
+    const float* tpart;
+    const float* b;
+    float* rdiag;
+    unsigned* status;
+    int N, L, K;
+    float lam, oml;
+    int pending, update_c, use_tau;
+};
+
+// one warp per row, all levels of the row in order; lane holds entries
+// q = lane and q = lane + 32
+__global__ void __launch_bounds__(256) sparse_rowpass_kernel(const SparseArgs p) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int K = p.K, L = p.L, N = p.N;
+    const bool pending = p.pending != 0;
+    for (int64_t i = wid; i < N; i += nw) {
+        int jq[2];
+        float sq[2];
+        bool has[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int q = lane + 32 * h;
+            has[h] = q < K;
+            jq[h] = has[h] ? p.cand[i * K + q] : 0x7fffffff;
+            sq[h] = has[h] ? p.s[i * K + q] : 0.f;
+        }
+        float c_prev = 0.f;
+        for (int l = 0; l < L; ++l) {
+            const int64_t base = ((int64_t)l * N + i) * K;
+            const int64_t voff = (int64_t)l * N;
+            float a[2], r[2], x[2];
+            float m1 = -kInf, m2 = -kInf, cm = -kInf;
+            int k1 = 0x7fffffff;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int q = lane + 32 * h;
+                if (!has[h]) { a[h] = -kInf; r[h] = 0.f; x[h] = -kInf; continue; }
+                const bool diag = jq[h] == (int)i;
+                const float sv = diag ? p.pref[voff + i] : sq[h];
+                x[h] = sv;
+                a[h] = p.A[base + q];
+                r[h] = p.R[base + q];
+                if (pending) {
+                    a[h] = damp(a[h], avail_target(p.b[voff + jq[h]], r[h], diag), p.lam, p.oml);
+                    p.A[base + q] = a[h];
+                }
+                top2_push(__fadd_rn(a[h], sv), jq[h], m1, k1, m2);
+                cm = fmaxf(cm, __fadd_rn(a[h], r[h]));
+            }
+            warp_top2(m1, k1, m2, cm);
+            const float cval = p.update_c ? cm : p.c[voff + i];
+            const float tauv = (p.use_tau && l > 0) ? __fadd_rn(c_prev, p.tpart[voff + i]) : kInf;
+            c_prev = cval;
+            if (lane == 0) {
+                if (p.update_c) p.c[voff + i] = cval;
+                p.tau[voff + i] = tauv;
+                if (l > 0) p.phi[voff - N + i] = m1;
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                if (!has[h]) continue;
+                const int q = lane + 32 * h;
+                const float mx = jq[h] == k1 ? m2 : m1;
+                const float rn = damp(r[h], __fadd_rn(x[h], fminf(tauv, -mx)), p.lam, p.oml);
+                p.R[base + q] = rn;
+                if (jq[h] == (int)i) p.rdiag[voff + i] = rn;
+            }
+        }
+    }
+}
+
+// P_j = sum over the column's entries (rows k != j, entry order) of max(0, rho)
+__global__ void sparse_colstats_kernel(const float* __restrict__ R, const int64_t* __restrict__ cptr,
+                                       const int32_t* __restrict__ cent, int N, int L, int K,
+                                       const float* __restrict__ c, const float* __restrict__ phi,
+                                       const float* __restrict__ rdiag, float* __restrict__ b, float* __restrict__ tpart) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)L * N) return;
+    const int l = (int)(idx / N);
+    const int64_t j = idx - (int64_t)l * N;
+    const float* Rl = R + (int64_t)l * N * K;
+    float P = 0.f;
+    for (int64_t e = cptr[j]; e < cptr[j + 1]; ++e) {
+        const int32_t ent = cent[e];
+        if (ent / K != j) P = __fadd_rn(P, fmaxf(Rl[ent], 0.f));
+    }
+    const float rd = rdiag[idx];
+    b[idx] = __fadd_rn(__fadd_rn(__fadd_rn(c[idx], phi[idx]), rd), P);
+    if (l + 1 < L) tpart[idx + N] = __fadd_rn(rd, P);
+}
+
+// s_iq = -||x_i - x_cand||^2 (FP32, direct differences); one warp per row
+__global__ void sparse_similarity_kernel(const float* __restrict__ X, int64_t d, const int32_t* __restrict__ cand,
+                                         int N, int K, float* __restrict__ s) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)N * K) return;
+    const int64_t i = e / K;
+    const int64_t j = cand[e];
+    float acc = 0.f;
+    for (int64_t k = 0; k < d; ++k) {
+        const float df = X[i * d + k] - X[j * d + k];
+        acc = fmaf(df, df, acc);
+    }
+    s[e] = -acc;
+}
+
+__global__ void sparse_exemplars_kernel(const int32_t* __restrict__ cand, const float* __restrict__ A,
+                                        const float* __restrict__ R, const float* __restrict__ b, int N, int L, int K,
+                                        int pending, float lam, float oml, int32_t* __restrict__ e,
+                                        float* __restrict__ A_out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (w >= (int64_t)L * N) return;
+    const int l = (int)(w / N);
+    const int64_t i = w - (int64_t)l * N;
+    float best = -kInf;
+    int bj = 0x7fffffff;
+    for (int q = lane; q < K; q += 32) {
+        const int64_t at = w * K + q;
+        const int j = cand[i * K + q];
+        const float r = R[at];
+        float a = A[at];
+        if (pending) a = damp(a, avail_target(b[(int64_t)l * N + j], r, j == i), lam, oml);
+        if (A_out) A_out[at] = a;
+        const float v = __fadd_rn(a, r);
+        if (v > best || (v == best && j < bj)) { best = v; bj = j; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const float ov = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
+        if (ov > best || (ov == best && oj < bj)) { best = ov; bj = oj; }
+    }
+    if (e && lane == 0) e[w] = bj;
+}
+
+// NS^l = sum_i s(i, e_i) with s = -||x_i - x_e||^2 in FP64 from the points
+// (preference on self-assignments); one CTA per level, fixed-order tree
+__global__ void netsim_points_kernel(const float* __restrict__ X, int64_t d, const int32_t* __restrict__ e,
+                                     const float* __restrict__ pref, int N, double* __restrict__ ns) {
+    __shared__ double part[256];
+    const int l = blockIdx.x;
+    double acc = 0.0;
+    for (int64_t i = threadIdx.x; i < N; i += blockDim.x) {
+        const int64_t j = e[(int64_t)l * N + i];
+        if (j == i) { acc += (double)pref[(int64_t)l * N + i]; continue; }
+        double s = 0.0;
+        for (int64_t k = 0; k < d; ++k) {
+            const double df = (double)X[i * d + k] - (double)X[j * d + k];
+            s += df * df;
+        }
+        acc -= s;
+    }
+    part[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) part[threadIdx.x] += part[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) ns[l] = part[0];
+}
+
+}  // namespace
+}  // namespace hap
+
+using namespace hap;
+
+#define SCU(x)                          \
+    do {                                \
+        if ((x) != cudaSuccess) {       \
+            cudaGetLastError();         \
+            return HAP_ECUDA;           \
+        }                               \
+    } while (0)
+
+struct hap_sparse {
+    int N = 0, L = 0, K = 0;
+    float lam = 0.5f;
+    int c_mode = HAP_C_PAPER;
+    cudaStream_t stream = nullptr;
+    int32_t* cand = nullptr;
+    float* s = nullptr;
+    float *A = nullptr, *R = nullptr;
+    float *pref = nullptr, *c = nullptr, *c0 = nullptr, *tau = nullptr, *phi = nullptr, *tpart = nullptr, *b = nullptr,
+          *rdiag = nullptr;
+    int64_t* cptr = nullptr;
+    int32_t* cent = nullptr;
+    int32_t* e = nullptr;
+    double* ns = nullptr;
+    unsigned* status = nullptr;
+    const float* X = nullptr;  // points of the last hap_sparse_set_candidates (borrowed for NS)
+    int64_t d = 0;
+    int64_t iter = 0;
+    bool pending = false;
+    int64_t launches = 0;
+};
+
+namespace {
+
+int sparse_reset(hap_sparse* h) {
+    const size_t mat = (size_t)h->L * h->N * h->K * 4, vec = (size_t)h->L * h->N * 4;
+    SCU(cudaMemsetAsync(h->A, 0, mat, h->stream));
+    SCU(cudaMemsetAsync(h->R, 0, mat, h->stream));
+    SCU(cudaMemcpyAsync(h->c, h->c0, vec, cudaMemcpyDeviceToDevice, h->stream));
+    SCU(cudaMemsetAsync(h->phi, 0, vec, h->stream));
+    SCU(cudaMemsetAsync(h->tpart, 0, vec, h->stream));
+    SCU(cudaMemsetAsync(h->b, 0, vec, h->stream));
+    SCU(cudaMemsetAsync(h->rdiag, 0, vec, h->stream));
+    std::vector<float> inf((size_t)h->L * h->N, __builtin_inff());
+    SCU(cudaMemcpyAsync(h->tau, inf.data(), vec, cudaMemcpyHostToDevice, h->stream));
+    SCU(cudaStreamSynchronize(h->stream));
+    h->iter = 0;
+    h->pending = false;
+    return HAP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hap_sparse_create(int64_t N, int L, int K, const float* prefs, float damping, int c_mode, hap_sparse** out) {
+    if (!out || N < 2 || L < 1 || L > 16 || K < 2 || K > SP_MAXK || K > N || !(damping > 0.f && damping < 1.f) ||
+        (c_mode != HAP_C_PAPER && c_mode != HAP_C_FIXED) || N * K >= (int64_t)1 << 31)
+        return HAP_EINVAL;
+    hap_sparse* h = new (std::nothrow) hap_sparse();
+    if (!h) return HAP_ENOMEM;
+    h->N = (int)N;
+    h->L = L;
+    h->K = K;
+    h->lam = damping;
+    h->c_mode = c_mode;
+    const size_t nk = (size_t)N * K, mat = nk * L * 4, vec = (size_t)L * N * 4;
+    bool ok = cudaMalloc(&h->cand, nk * 4) == cudaSuccess && cudaMalloc(&h->s, nk * 4) == cudaSuccess &&
+              cudaMalloc(&h->A, mat) == cudaSuccess && cudaMalloc(&h->R, mat) == cudaSuccess &&
+              cudaMalloc(&h->pref, vec) == cudaSuccess && cudaMalloc(&h->c, vec) == cudaSuccess &&
+              cudaMalloc(&h->c0, vec) == cudaSuccess && cudaMalloc(&h->tau, vec) == cudaSuccess &&
+              cudaMalloc(&h->phi, vec) == cudaSuccess && cudaMalloc(&h->tpart, vec) == cudaSuccess &&
+              cudaMalloc(&h->b, vec) == cudaSuccess && cudaMalloc(&h->rdiag, vec) == cudaSuccess &&
+              cudaMalloc(&h->cptr, (N + 1) * 8) == cudaSuccess && cudaMalloc(&h->cent, nk * 4) == cudaSuccess &&
+              cudaMalloc(&h->e, (size_t)L * N * 4) == cudaSuccess && cudaMalloc(&h->ns, (size_t)L * 8) == cudaSuccess &&
+              cudaMalloc(&h->status, 16) == cudaSuccess;
+    if (!ok) { cudaGetLastError(); hap_sparse_destroy(h); return HAP_ENOMEM; }
+    cudaMemset(h->c0, 0, vec);
+    cudaMemset(h->status, 0, 16);
+    std::vector<float> pv((size_t)L * N, 0.f);
+    if (prefs)
+        for (int l = 0; l < L; ++l)
+            for (int64_t i = 0; i < N; ++i) pv[(size_t)l * N + i] = prefs[l];
+    cudaMemcpy(h->pref, pv.data(), vec, cudaMemcpyHostToDevice);
+    int rc = sparse_reset(h);
+    if (rc) { hap_sparse_destroy(h); return rc; }
+    *out = h;
+    return HAP_OK;
+}
+
+void hap_sparse_destroy(hap_sparse* h) {
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    cudaFree(h->cand); cudaFree(h->s); cudaFree(h->A); cudaFree(h->R); cudaFree(h->pref); cudaFree(h->c);
+    cudaFree(h->c0); cudaFree(h->tau); cudaFree(h->phi); cudaFree(h->tpart); cudaFree(h->b); cudaFree(h->rdiag);
+    cudaFree(h->cptr); cudaFree(h->cent); cudaFree(h->e); cudaFree(h->ns); cudaFree(h->status);
+    delete h;
+}
+
+int hap_sparse_set_stream(hap_sparse* h, void* stream) {
+    if (!h) return HAP_EINVAL;
+    h->stream = static_cast<cudaStream_t>(stream);
+    return HAP_OK;
+}
+
+int hap_sparse_set_preferences(hap_sparse* h, const float* prefs, int per_point) {
+    if (!h || !prefs) return HAP_EINVAL;
+    std::vector<float> pv((size_t)h->L * h->N);
+    for (int l = 0; l < h->L; ++l)
+        for (int i = 0; i < h->N; ++i) pv[(size_t)l * h->N + i] = per_point ? prefs[(size_t)l * h->N + i] : prefs[l];
+    SCU(cudaMemcpyAsync(h->pref, pv.data(), pv.size() * 4, cudaMemcpyHostToDevice, h->stream));
+    SCU(cudaStreamSynchronize(h->stream));
+    return HAP_OK;
+}
+
+int hap_sparse_set_candidates(hap_sparse* h, const int32_t* cand, const float* X, int64_t d) {
+    if (!h || !cand || !X || d < 1) return HAP_EINVAL;
+    const int64_t N = h->N, K = h->K, nk = N * K;
+    // candidate rows must contain the row itself, sorted, in range (host check)
+    std::vector<int32_t> hc(nk);
+    SCU(cudaMemcpyAsync(hc.data(), cand, nk * 4, cudaMemcpyDeviceToHost, h->stream));
+    SCU(cudaStreamSynchronize(h->stream));
+    std::vector<int64_t> cnt(N + 1, 0);
+    for (int64_t i = 0; i < N; ++i) {
+        bool self = false;
+        for (int64_t q = 0; q < K; ++q) {
+            const int32_t j = hc[i * K + q];
+            if (j < 0 || j >= N || (q > 0 && j <= hc[i * K + q - 1])) return HAP_EINVAL;
+            self |= j == i;
+            cnt[j + 1] += 1;
+        }
+        if (!self) return HAP_EINVAL;
+    }
+    for (int64_t j = 0; j < N; ++j) cnt[j + 1] += cnt[j];
+    std::vector<int32_t> ent(nk);
+    std::vector<int64_t> pos(cnt.begin(), cnt.end() - 1);
+    for (int64_t e = 0; e < nk; ++e) ent[pos[hc[e]]++] = (int32_t)e;  // entry order within each column
+    SCU(cudaMemcpyAsync(h->cand, hc.data(), nk * 4, cudaMemcpyHostToDevice, h->stream));
+    SCU(cudaMemcpyAsync(h->cptr, cnt.data(), (N + 1) * 8, cudaMemcpyHostToDevice, h->stream));
+    SCU(cudaMemcpyAsync(h->cent, ent.data(), nk * 4, cudaMemcpyHostToDevice, h->stream));
+    sparse_similarity_kernel<<<(unsigned)((nk + 255) / 256), 256, 0, h->stream>>>(X, d, h->cand, (int)N, (int)K, h->s);
+    SCU(cudaGetLastError());
+    h->launches += 1;
+    h->X = X;
+    h->d = d;
+    return sparse_reset(h);
+}
+
+int hap_sparse_iterate(hap_sparse* h, int n) {
+    if (!h || n < 0) return HAP_EINVAL;
+    SparseArgs a;
+    a.cand = h->cand; a.s = h->s; a.A = h->A; a.R = h->R; a.pref = h->pref; a.c = h->c; a.tau = h->tau;
+    a.phi = h->phi; a.tpart = h->tpart; a.b = h->b; a.rdiag = h->rdiag; a.status = h->status;
+    a.N = h->N; a.L = h->L; a.K = h->K; a.lam = h->lam; a.oml = 1.0f - h->lam;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t warps = std::min<int64_t>(h->N, (int64_t)sms * 64);
+    const unsigned grid = (unsigned)((warps * 32 + 255) / 256);
+    for (int it = 0; it < n; ++it) {
+        const int64_t t = h->iter + 1;
+        a.pending = h->pending ? 1 : 0;
+        a.update_c = (h->c_mode == HAP_C_PAPER && t >= 2) ? 1 : 0;
+        a.use_tau = t >= 2 ? 1 : 0;
+        sparse_rowpass_kernel<<<grid, 256, 0, h->stream>>>(a);
+        SCU(cudaGetLastError());
+        const int64_t tot = (int64_t)h->L * h->N;
+        sparse_colstats_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, h->stream>>>(
+            h->R, h->cptr, h->cent, h->N, h->L, h->K, h->c, h->phi, h->rdiag, h->b, h->tpart);
+        SCU(cudaGetLastError());
+        h->launches += 2;
+        h->pending = true;
+        h->iter = t;
+    }
+    return HAP_OK;
+}
+
+int hap_sparse_exemplars(hap_sparse* h, int32_t* e, int on_host) {
+    if (!h || !e || (on_host != 0 && on_host != 1)) return HAP_EINVAL;
+    const int64_t rows = (int64_t)h->L * h->N;
+    sparse_exemplars_kernel<<<(unsigned)((rows * 32 + 255) / 256), 256, 0, h->stream>>>(
+        h->cand, h->A, h->R, h->b, h->N, h->L, h->K, h->pending, h->lam, 1.0f - h->lam, h->e, nullptr);
+    SCU(cudaGetLastError());
+    h->launches += 1;
+    SCU(cudaMemcpyAsync(e, h->e, rows * 4, on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, h->stream));
+    if (on_host) SCU(cudaStreamSynchronize(h->stream));
+    return HAP_OK;
+}
+
+int hap_net_similarity_points(const float* X, int64_t N, int64_t d, int L, const int32_t* e, const float* pref,
+                              double* ns_host, void* stream) {
+    if (!X || !e || !pref || !ns_host || N < 1 || L < 1) return HAP_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    double* dns = nullptr;
+    SCU(cudaMallocAsync(&dns, (size_t)L * 8, st));
+    netsim_points_kernel<<<L, 256, 0, st>>>(X, d, e, pref, (int)N, dns);
+    SCU(cudaGetLastError());
+    SCU(cudaMemcpyAsync(ns_host, dns, (size_t)L * 8, cudaMemcpyDeviceToHost, st));
+    SCU(cudaFreeAsync(dns, st));
+    SCU(cudaStreamSynchronize(st));
+    return HAP_OK;
+}
+
+int hap_sparse_net_similarity(hap_sparse* h, double* ns) {
+    if (!h || !ns || !h->X) return HAP_EINVAL;
+    const int64_t rows = (int64_t)h->L * h->N;
+    sparse_exemplars_kernel<<<(unsigned)((rows * 32 + 255) / 256), 256, 0, h->stream>>>(
+        h->cand, h->A, h->R, h->b, h->N, h->L, h->K, h->pending, h->lam, 1.0f - h->lam, h->e, nullptr);
+    SCU(cudaGetLastError());
+    netsim_points_kernel<<<h->L, 256, 0, h->stream>>>(h->X, h->d, h->e, h->pref, h->N, h->ns);
+    SCU(cudaGetLastError());
+    h->launches += 2;
+    SCU(cudaMemcpyAsync(ns, h->ns, (size_t)h->L * 8, cudaMemcpyDeviceToHost, h->stream));
+    SCU(cudaStreamSynchronize(h->stream));
+    return HAP_OK;
+}
+
+int hap_sparse_get_state(hap_sparse* h, float* A, float* R, float* vecs, int64_t* iter) {
+    if (!h) return HAP_EINVAL;
+    const int64_t rows = (int64_t)h->L * h->N, mat = rows * h->K;
+    if (A) {
+        sparse_exemplars_kernel<<<(unsigned)((rows * 32 + 255) / 256), 256, 0, h->stream>>>(
+            h->cand, h->A, h->R, h->b, h->N, h->L, h->K, h->pending, h->lam, 1.0f - h->lam, nullptr, A);
+        SCU(cudaGetLastError());
+        h->launches += 1;
+    }
+    if (R) SCU(cudaMemcpyAsync(R, h->R, mat * 4, cudaMemcpyDeviceToDevice, h->stream));
+    if (vecs) {
+        const float* src[3] = {h->c, h->tau, h->phi};
+        for (int q = 0; q < 3; ++q)
+            SCU(cudaMemcpyAsync(vecs + (size_t)q * rows, src[q], rows * 4, cudaMemcpyDeviceToDevice, h->stream));
+    }
+    if (iter) *iter = h->iter;
+    return HAP_OK;
+}
+
+int hap_sparse_query(hap_sparse* h, int key, int64_t* value) {
+    if (!h || !value) return HAP_EINVAL;
+    if (key == HAP_Q_ITER) { *value = h->iter; return HAP_OK; }
+    if (key == HAP_Q_LAUNCHES) { *value = h->launches; return HAP_OK; }
+    return HAP_EINVAL;
+}
+
+}  // extern "C"

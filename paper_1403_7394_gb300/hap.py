@@ -69,6 +69,28 @@ def _load():
         "hap_batch_tune": (i32, [vp, ctypes.POINTER(ctypes.c_double)]),
         "hap_batch_query": (i32, [vp, i32, ctypes.POINTER(i64)]),
         "hap_batch_sync": (i32, [vp]),
+        "hap_knn": (i32, [vp, i64, i64, i32, vp, vp, vp]),
+        "hap_knn_features": (i32, [vp, i64, i32, i32, vp, ctypes.POINTER(f32), vp]),
+        "hap_mlp_create": (i32, [i32, vp, ctypes.POINTER(vp)]),
+        "hap_mlp_destroy": (None, [vp]),
+        "hap_mlp_set_stream": (i32, [vp, vp]),
+        "hap_mlp_num_params": (i32, [vp, ctypes.POINTER(i64)]),
+        "hap_mlp_get_params": (i32, [vp, vp]),
+        "hap_mlp_forward": (i32, [vp, vp, i64, vp]),
+        "hap_mlp_gradients": (i32, [vp, vp, vp, i64, f32, vp, vp]),
+        "hap_mlp_train_step": (i32, [vp, vp, vp, i64, f32, f32, vp]),
+        "hap_select_candidates": (i32, [vp, i64, i32, vp, i32, i32, vp, vp]),
+        "hap_sparse_create": (i32, [i64, i32, i32, vp, f32, i32, ctypes.POINTER(vp)]),
+        "hap_sparse_destroy": (None, [vp]),
+        "hap_sparse_set_stream": (i32, [vp, vp]),
+        "hap_sparse_set_preferences": (i32, [vp, vp, i32]),
+        "hap_sparse_set_candidates": (i32, [vp, vp, vp, i64]),
+        "hap_sparse_iterate": (i32, [vp, i32]),
+        "hap_sparse_exemplars": (i32, [vp, vp, i32]),
+        "hap_sparse_net_similarity": (i32, [vp, vp]),
+        "hap_sparse_get_state": (i32, [vp, vp, vp, vp, ctypes.POINTER(i64)]),
+        "hap_sparse_query": (i32, [vp, i32, ctypes.POINTER(i64)]),
+        "hap_net_similarity_points": (i32, [vp, i64, i64, i32, vp, vp, vp, vp]),
         "hap_noalloc_scratch_bytes": (ctypes.c_size_t, []),
     }
     for name, (res, args) in sigs.items():
@@ -382,3 +404,182 @@ class HAPBatch:
 
     def sync(self):
         check(lib.hap_batch_sync(self._h), "hap_batch_sync")
+
+
+# ---- learned candidate proposal and sparse HAP -------------------------------
+def _stream_ptr(device, stream=None):
+    st = stream if stream is not None else torch.cuda.current_stream(device)
+    return ctypes.c_void_p(st.cuda_stream)
+
+
+def knn(X: torch.Tensor, M: int, stream=None):
+    """Exact M nearest neighbours (squared Euclidean, self excluded):
+    (idx int32 (N, M), dist float32 (N, M)) on X's device."""
+    X = X.contiguous()
+    N, d = X.shape
+    idx = torch.empty((N, M), dtype=torch.int32, device=X.device)
+    dist = torch.empty((N, M), dtype=torch.float32, device=X.device)
+    check(lib.hap_knn(_ptr(X), N, d, int(M), _ptr(idx), _ptr(dist), _stream_ptr(X.device, stream)), "hap_knn")
+    return idx, dist
+
+
+def knn_features(dist: torch.Tensor, F: int, stream=None):
+    """(feats (N, F), log_scale) with feats = log(dist[:, :F]) - mean log(dist[:, F-1])."""
+    N, M = dist.shape
+    feats = torch.empty((N, F), dtype=torch.float32, device=dist.device)
+    ls = ctypes.c_float(0.0)
+    check(lib.hap_knn_features(_ptr(dist.contiguous()), N, M, int(F), _ptr(feats), ctypes.byref(ls),
+                               _stream_ptr(dist.device, stream)), "hap_knn_features")
+    return feats, ls.value
+
+
+def mlp_init_params(F: int, seed: int = 0, width: int = 128):
+    """Flat FP32 initial parameters: uniform(+-1/sqrt(fan_in)) weights, zero biases."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    a1, a2 = 1.0 / np.sqrt(F), 1.0 / np.sqrt(width)
+    parts = [rng.uniform(-a1, a1, F * width), np.zeros(width), rng.uniform(-a2, a2, width * width),
+             np.zeros(width), rng.uniform(-a2, a2, width), np.zeros(1)]
+    return np.concatenate(parts).astype(np.float32)
+
+
+class MLP:
+    """The proposal network (hap_mlp_*): width 128, BF16 weights, FP32 accumulation."""
+
+    def __init__(self, F: int, theta0=None, seed: int = 0, device="cuda", stream=None):
+        import numpy as np
+        self.F = int(F)
+        self.device = torch.device(device)
+        th = mlp_init_params(F, seed) if theta0 is None else np.ascontiguousarray(np.asarray(theta0, dtype=np.float32))
+        with torch.cuda.device(self.device):
+            h = ctypes.c_void_p()
+            check(lib.hap_mlp_create(self.F, th.ctypes.data_as(ctypes.c_void_p), ctypes.byref(h)), "hap_mlp_create")
+            self._h = h
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            check(lib.hap_mlp_set_stream(self._h, ctypes.c_void_p(self.stream.cuda_stream)), "hap_mlp_set_stream")
+        P = ctypes.c_int64(0)
+        check(lib.hap_mlp_num_params(self._h, ctypes.byref(P)), "hap_mlp_num_params")
+        self.P = P.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.hap_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self):
+        import numpy as np
+        th = np.empty(self.P, dtype=np.float32)
+        check(lib.hap_mlp_get_params(self._h, th.ctypes.data_as(ctypes.c_void_p)), "hap_mlp_get_params")
+        return th
+
+    def forward(self, feats: torch.Tensor) -> torch.Tensor:
+        feats = feats.contiguous()
+        out = torch.empty(feats.shape[0], dtype=torch.float32, device=self.device)
+        check(lib.hap_mlp_forward(self._h, _ptr(feats), feats.shape[0], _ptr(out)), "hap_mlp_forward")
+        return out
+
+    def gradients(self, feats: torch.Tensor, labels: torch.Tensor, pos_weight: float):
+        import numpy as np
+        g = np.empty(self.P, dtype=np.float32)
+        loss = ctypes.c_float(0.0)
+        check(lib.hap_mlp_gradients(self._h, _ptr(feats.contiguous()), _ptr(labels.contiguous()), feats.shape[0],
+                                    float(pos_weight), g.ctypes.data_as(ctypes.c_void_p), ctypes.byref(loss)),
+              "hap_mlp_gradients")
+        return g, loss.value
+
+    def train_step(self, feats: torch.Tensor, labels: torch.Tensor, pos_weight: float, lr: float, want_loss=False):
+        loss = ctypes.c_float(0.0)
+        check(lib.hap_mlp_train_step(self._h, _ptr(feats), _ptr(labels), feats.shape[0], float(pos_weight), float(lr),
+                                     ctypes.byref(loss) if want_loss else None), "hap_mlp_train_step")
+        return loss.value if want_loss else None
+
+
+def select_candidates(pool: torch.Tensor, K: int, K_near: int, score: torch.Tensor | None = None, stream=None):
+    N, M = pool.shape
+    cand = torch.empty((N, K), dtype=torch.int32, device=pool.device)
+    check(lib.hap_select_candidates(_ptr(pool.contiguous()), N, M, _ptr(score) if score is not None else None, int(K),
+                                    int(K_near), _ptr(cand), _stream_ptr(pool.device, stream)), "hap_select_candidates")
+    return cand
+
+
+def net_similarity_points(X: torch.Tensor, e: torch.Tensor, pref: torch.Tensor, stream=None):
+    """FP64 NS per level of assignment e (L, N) from the points X (N, d), pref (L, N)."""
+    import numpy as np
+    L, N = e.shape
+    ns = np.zeros(L, dtype=np.float64)
+    check(lib.hap_net_similarity_points(_ptr(X.contiguous()), N, X.shape[1], L, _ptr(e.contiguous()),
+                                        _ptr(pref.contiguous()), ns.ctypes.data_as(ctypes.c_void_p),
+                                        _stream_ptr(X.device, stream)), "hap_net_similarity_points")
+    return ns
+
+
+class HAPSparse:
+    """Sparse HAP over a K-candidate graph (hap_sparse_*)."""
+
+    def __init__(self, N: int, L: int, K: int, prefs=None, damping: float = 0.5, c_mode="paper", device="cuda",
+                 stream=None):
+        import numpy as np
+        self.N, self.L, self.K = int(N), int(L), int(K)
+        self.device = torch.device(device)
+        with torch.cuda.device(self.device):
+            h = ctypes.c_void_p()
+            check(lib.hap_sparse_create(self.N, self.L, self.K, None, float(damping), C_MODES[c_mode], ctypes.byref(h)),
+                  "hap_sparse_create")
+            self._h = h
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            check(lib.hap_sparse_set_stream(self._h, ctypes.c_void_p(self.stream.cuda_stream)), "hap_sparse_set_stream")
+        if prefs is not None:
+            self.set_preferences(prefs)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.hap_sparse_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_preferences(self, prefs):
+        import numpy as np
+        p = np.ascontiguousarray(np.asarray(prefs, dtype=np.float32))
+        per_point = 1 if p.ndim == 2 else 0
+        check(lib.hap_sparse_set_preferences(self._h, p.ctypes.data_as(ctypes.c_void_p), per_point),
+              "hap_sparse_set_preferences")
+
+    def set_candidates(self, cand: torch.Tensor, X: torch.Tensor):
+        self._X = X.contiguous()
+        check(lib.hap_sparse_set_candidates(self._h, _ptr(cand.contiguous()), _ptr(self._X), self._X.shape[1]),
+              "hap_sparse_set_candidates")
+
+    def iterate(self, n: int = 1):
+        check(lib.hap_sparse_iterate(self._h, int(n)), "hap_sparse_iterate")
+
+    def exemplars(self, out: torch.Tensor | None = None):
+        if out is None:
+            out = torch.empty((self.L, self.N), dtype=torch.int32, device=self.device)
+        check(lib.hap_sparse_exemplars(self._h, _ptr(out), 1 if out.device.type == "cpu" else 0), "hap_sparse_exemplars")
+        return out
+
+    def net_similarity(self):
+        import numpy as np
+        ns = np.zeros(self.L, dtype=np.float64)
+        check(lib.hap_sparse_net_similarity(self._h, ns.ctypes.data_as(ctypes.c_void_p)), "hap_sparse_net_similarity")
+        return ns
+
+    def get_state(self):
+        A = torch.empty((self.L, self.N, self.K), dtype=torch.float32, device=self.device)
+        R = torch.empty_like(A)
+        vecs = torch.empty((3, self.L, self.N), dtype=torch.float32, device=self.device)
+        it = ctypes.c_int64(0)
+        check(lib.hap_sparse_get_state(self._h, _ptr(A), _ptr(R), _ptr(vecs), ctypes.byref(it)), "hap_sparse_get_state")
+        self.stream.synchronize()
+        return {"A": A, "R": R, "c": vecs[0], "tau": vecs[1], "phi": vecs[2], "t": it.value}
