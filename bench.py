@@ -39,9 +39,9 @@ BATCHED = {"c3": (256, 32, 200, "256 instances, N uniform in [200, 4000], L unif
                                "(5-50 components), S built BF16 hi/lo split, one persistent launch per iteration "
                                "in a CUDA graph, 200 iterations")}
 LEARNED = {"c4": (262144, 32, 3, 64, 400,
-                  "N=262144 d=32 1024-component GMM, L=3, K=64 candidates per row from a 128-neighbour pool re-ranked "
-                  "by the MLP proposal (trained on dense HAP labels of two N=8192 instances), sparse HAP 400 "
-                  "iterations, c fixed, lambda 0.9")}
+                  "N=262144 d=32 1024-component GMM, L=3, K=64 candidates per row: itself, its 32 nearest "
+                  "neighbours and its nearest hubs (the N/64 points the MLP proposal scores highest; trained on "
+                  "dense HAP labels of two N=8192 instances), sparse HAP 400 iterations, c fixed, lambda 0.9")}
 CPU_SAMPLE_N = 4096
 
 
@@ -443,7 +443,7 @@ def run_learned(args, world, rank, local):
     N, d, L, K, T, desc = LEARNED[args.workload]
     if args.iters:
         T = args.iters
-    lam, M, F = 0.9, 128, 16
+    lam, M, F = 0.9, 32, 16
 
     def instance(n, seed):
         X, lab = W.gmm_points(n, d, max(1, n // 256), sigma=1.0, seed=seed, means="normal", mean_scale=2.0)
@@ -484,13 +484,15 @@ def run_learned(args, world, rank, local):
 
     def sparse_solve(Xt, prefs, score, k_near, iters):
         n = Xt.shape[0]
-        pool, dist_ = hap.knn(Xt, M)
         if score == "mlp":
+            pool, dist_ = hap.knn(Xt, M)
             f, _ = hap.knn_features(dist_, F)
-            score_t = mlp.forward(f)
+            hubs = hap.top_scores(mlp.forward(f), n // 64)
+            hubnn, _ = hap.knn_subset(Xt, hubs, K)
+            cand = hap.select_hub_candidates(pool, hubnn, K, k_near)
         else:
-            score_t = None
-        cand = hap.select_candidates(pool, K, k_near, score_t)
+            pool, _ = hap.knn(Xt, K - 1)
+            cand = hap.select_candidates(pool, K, K - 1, None)
         sp = hap.HAPSparse(n, L, K, prefs=prefs, damping=lam, c_mode="fixed", device=dev)
         sp.set_candidates(cand, Xt)
         sp.iterate(iters)
@@ -509,7 +511,7 @@ def run_learned(args, world, rank, local):
         ns_d = hap.net_similarity_points(Xjt, e_d, ptj)
         ed = e_d.cpu().numpy()
         judge = {"n": args.judge_n, "dense_exemplars_level1": int(len(np.unique(ed[0])))}
-        for name, sc, kn in (("learned", "mlp", K // 2), ("knn", None, K - 1)):
+        for name, sc, kn in (("learned", "mlp", M), ("knn", None, K - 1)):
             e_s, ns_s = sparse_solve(Xjt, pj, sc, kn, T)
             es = e_s.cpu().numpy()
             judge[name] = {"ns_gap_level1": float((ns_d[0] - ns_s[0]) / abs(ns_d[0])),
@@ -526,7 +528,7 @@ def run_learned(args, world, rank, local):
     Xt = torch.from_numpy(X32).to(dev)
     stream = torch.cuda.current_stream(dev)
     for _ in range(args.warmup):
-        sparse_solve(Xt, prefs, "mlp", K // 2, T)
+        sparse_solve(Xt, prefs, "mlp", M, T)
     torch.cuda.synchronize()
     props = torch.cuda.get_device_properties(dev)
     gpu_id = str(getattr(props, "uuid", local))
@@ -536,14 +538,15 @@ def run_learned(args, world, rank, local):
     with ClockSampler(gpu_id) as clk:
         ev0.record(stream)
         for _ in range(args.steps):
-            e, ns = sparse_solve(Xt, prefs, "mlp", K // 2, T)
+            e, ns = sparse_solve(Xt, prefs, "mlp", M, T)
         ev1.record(stream)
         torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1)
     # the sparse iterations alone
     pool, dist_ = hap.knn(Xt, M)
     f, _ = hap.knn_features(dist_, F)
-    cand = hap.select_candidates(pool, K, K // 2, mlp.forward(f))
+    hubnn, _ = hap.knn_subset(Xt, hap.top_scores(mlp.forward(f), N // 64), K)
+    cand = hap.select_hub_candidates(pool, hubnn, K, M)
     sp = hap.HAPSparse(N, L, K, prefs=prefs, damping=lam, c_mode="fixed", device=dev)
     sp.set_candidates(cand, Xt)
     sp.iterate(2)

@@ -244,6 +244,23 @@ int hap_batch_sync(hap_batch* batch);
  * Asynchronous on `stream`. */
 int hap_knn(const float* X, int64_t N, int64_t d, int M, int32_t* idx, float* dist, void* stream);
 
+/* M nearest members of a subset for every point: candidates are the points
+ * subset[0..Ns) (device int32 global indices), a point never takes itself;
+ * idx holds global indices.  Uses a temporary device buffer of Ns*d floats
+ * (stream-ordered allocation).  Otherwise as hap_knn. */
+int hap_knn_subset(const float* X, int64_t N, int64_t d, const int32_t* subset, int64_t Ns, int M, int32_t* idx,
+                   float* dist, void* stream);
+
+/* Indices of the H highest scores (device [N]), lower index first on ties,
+ * ordered by decreasing score, into hubs device int32 [H].  Asynchronous. */
+int hap_top_scores(const float* score, int64_t N, int64_t H, int32_t* hubs, void* stream);
+
+/* Candidates per row: the row itself, its K_near nearest (pool [N][Mp]),
+ * then its nearest hubs (hubnn [N][Mh], global indices) not already taken,
+ * then further pool entries; sorted by index, K <= 64.  Asynchronous. */
+int hap_select_hub_candidates(const int32_t* pool, int64_t N, int Mp, const int32_t* hubnn, int Mh, int K, int K_near,
+                              int32_t* cand, void* stream);
+
 /* Features f_q(i) = log(dist[i][q]) - mean_i log(dist[i][F-1]), q < F <= 32,
  * from hap_knn distances ([N][M] device) into feats device [N][F].  The
  * subtracted mean is returned in *log_scale (host, may be NULL).

@@ -109,6 +109,46 @@ def select_candidates(pool_idx, K, K_near, score=None):
     return out
 
 
+def knn_subset(X, subset, k):
+    """The k nearest members of ``subset`` for every point (global indices),
+    a point never taking itself; ties to the lower global index."""
+    X = np.asarray(X, dtype=np.float64)
+    subset = np.asarray(subset)
+    n = X.shape[0]
+    idx = np.empty((n, k), dtype=np.int32)
+    dist = np.empty((n, k))
+    for i in range(n):
+        d = ((X[subset] - X[i]) ** 2).sum(axis=1)
+        d[subset == i] = np.inf
+        order = np.lexsort((subset, d))[:k]
+        idx[i] = subset[order]
+        dist[i] = d[order]
+    return idx, dist
+
+
+def top_scores(score, H):
+    """Indices of the H highest scores, lower index first on ties."""
+    score = np.asarray(score, dtype=np.float64)
+    return np.lexsort((np.arange(score.size), -score))[:H].astype(np.int32)
+
+
+def select_hub_candidates(pool, hubnn, K, K_near):
+    """Candidates of row i: i, its K_near nearest, its nearest hubs not yet
+    taken, then further pool entries, up to K; sorted by index."""
+    n = pool.shape[0]
+    out = np.empty((n, K), dtype=np.int32)
+    for i in range(n):
+        sel = [i]
+        for src in (pool[i, :K_near], hubnn[i], pool[i, K_near:]):
+            for v in src:
+                if len(sel) == K:
+                    break
+                if v >= 0 and v not in sel:
+                    sel.append(int(v))
+        out[i] = np.sort(np.array(sel, dtype=np.int32))
+    return out
+
+
 def masked_similarity(S, cand):
     """S with -inf outside the candidate graph (each row keeps its candidate
     columns, including the diagonal)."""

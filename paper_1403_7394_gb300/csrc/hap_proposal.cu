@@ -28,19 +28,21 @@ constexpr int KNN_TILE = 64;
 constexpr int KNN_MAXM = 128;
 
 template <int D>  // padded dimension, the query vector lives in registers
-__global__ void __launch_bounds__(KNN_ROWS) knn_kernel(const float* __restrict__ X, int N, int d, int M,
+__global__ void __launch_bounds__(KNN_ROWS) knn_kernel(const float* __restrict__ Q, int Nq, const float* __restrict__ C,
+                                                       const int32_t* __restrict__ cid, int Nc, int d, int M,
                                                        int32_t* __restrict__ out_idx, float* __restrict__ out_dist) {
-    constexpr int dpad = D;
+    // queries are points 0..Nq-1; candidate j has global id cid[j] (j if cid
+    // is NULL); a query never takes itself
     extern __shared__ __align__(16) float ksm[];
-    float* ct = ksm;                                      // [KNN_TILE][dpad]
-    float* tdist = ct + KNN_TILE * dpad;                  // [M][KNN_ROWS]
+    float* ct = ksm;                                      // [KNN_TILE][D]
+    float* tdist = ct + KNN_TILE * D;                     // [M][KNN_ROWS]
     int* tidx = reinterpret_cast<int*>(tdist + M * KNN_ROWS);
     const int t = threadIdx.x;
     const int i = blockIdx.x * KNN_ROWS + t;
-    const bool valid = i < N;
+    const bool valid = i < Nq;
     float q[D];
 #pragma unroll
-    for (int k = 0; k < D; ++k) q[k] = (valid && k < d) ? X[(int64_t)i * d + k] : 0.f;
+    for (int k = 0; k < D; ++k) q[k] = (valid && k < d) ? Q[(int64_t)i * d + k] : 0.f;
     int cnt = 0;
     float thr = kInf;
     auto insert = [&](float dv, int j) {
@@ -55,32 +57,38 @@ __global__ void __launch_bounds__(KNN_ROWS) knn_kernel(const float* __restrict__
         tidx[p * KNN_ROWS + t] = j;
         thr = cnt == M ? tdist[(M - 1) * KNN_ROWS + t] : kInf;
     };
-    for (int c0 = 0; c0 < N; c0 += KNN_TILE) {
+    for (int c0 = 0; c0 < Nc; c0 += KNN_TILE) {
         __syncthreads();
-        for (int e = t; e < KNN_TILE * dpad; e += KNN_ROWS) {
-            const int r = e / dpad, k = e - r * dpad, j = c0 + r;
-            ct[e] = (j < N && k < d) ? X[(int64_t)j * d + k] : 0.f;
+        for (int e = t; e < KNN_TILE * D; e += KNN_ROWS) {
+            const int r = e / D, k = e - r * D, j = c0 + r;
+            ct[e] = (j < Nc && k < d) ? C[(int64_t)j * d + k] : 0.f;
         }
         __syncthreads();
         if (!valid) continue;
-        const int nc = min(KNN_TILE, N - c0);
-        for (int r = 0; r < nc; r += 4) {  // four candidates in flight
+        const int nc = min(KNN_TILE, Nc - c0);
+        for (int r = 0; r < nc; r += 4) {  // four candidates in flight, 4 dimensions per load
             float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-            const float* c = ct + r * dpad;
+            const float4* c = reinterpret_cast<const float4*>(ct + r * D);
 #pragma unroll
-            for (int k = 0; k < D; ++k) {
-                const float x = q[k];
-                const float e0 = x - c[k], e1 = x - c[dpad + k], e2 = x - c[2 * dpad + k], e3 = x - c[3 * dpad + k];
-                a0 = fmaf(e0, e0, a0);
-                a1 = fmaf(e1, e1, a1);
-                a2 = fmaf(e2, e2, a2);
-                a3 = fmaf(e3, e3, a3);
+            for (int k4 = 0; k4 < D / 4; ++k4) {
+                const float4 v0 = c[k4], v1 = c[D / 4 + k4], v2 = c[2 * (D / 4) + k4], v3 = c[3 * (D / 4) + k4];
+                const float x0 = q[4 * k4], x1 = q[4 * k4 + 1], x2 = q[4 * k4 + 2], x3 = q[4 * k4 + 3];
+                float e;
+                e = x0 - v0.x; a0 = fmaf(e, e, a0); e = x1 - v0.y; a0 = fmaf(e, e, a0);
+                e = x2 - v0.z; a0 = fmaf(e, e, a0); e = x3 - v0.w; a0 = fmaf(e, e, a0);
+                e = x0 - v1.x; a1 = fmaf(e, e, a1); e = x1 - v1.y; a1 = fmaf(e, e, a1);
+                e = x2 - v1.z; a1 = fmaf(e, e, a1); e = x3 - v1.w; a1 = fmaf(e, e, a1);
+                e = x0 - v2.x; a2 = fmaf(e, e, a2); e = x1 - v2.y; a2 = fmaf(e, e, a2);
+                e = x2 - v2.z; a2 = fmaf(e, e, a2); e = x3 - v2.w; a2 = fmaf(e, e, a2);
+                e = x0 - v3.x; a3 = fmaf(e, e, a3); e = x1 - v3.y; a3 = fmaf(e, e, a3);
+                e = x2 - v3.z; a3 = fmaf(e, e, a3); e = x3 - v3.w; a3 = fmaf(e, e, a3);
             }
             const float dv[4] = {a0, a1, a2, a3};
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                const int j = c0 + r + u;
-                if (r + u < nc && j != i && (cnt < M || dv[u] < thr)) insert(dv[u], j);
+                if (r + u >= nc) continue;
+                const int j = cid ? cid[c0 + r + u] : c0 + r + u;
+                if (j != i && (cnt < M || dv[u] < thr)) insert(dv[u], j);
             }
         }
     }
@@ -89,6 +97,72 @@ __global__ void __launch_bounds__(KNN_ROWS) knn_kernel(const float* __restrict__
             out_idx[(int64_t)i * M + m] = m < cnt ? tidx[m * KNN_ROWS + t] : -1;
             out_dist[(int64_t)i * M + m] = m < cnt ? tdist[m * KNN_ROWS + t] : kInf;
         }
+}
+
+__global__ void gather_rows_kernel(const float* __restrict__ X, int64_t d, const int32_t* __restrict__ rows,
+                                   float* __restrict__ out) {
+    const int64_t r = blockIdx.x;
+    const int64_t src = rows[r];
+    for (int64_t k = threadIdx.x; k < d; k += blockDim.x) out[r * d + k] = X[src * d + k];
+}
+
+// ---------------------------------------------------------------------------
+// top-H scores (hubs): bitonic sort of (descending score, ascending index)
+// keys packed in 64 bits, padded to a power of two with keys that sort last
+// ---------------------------------------------------------------------------
+__global__ void hub_keys_kernel(const float* __restrict__ score, int N, int n2, uint64_t* __restrict__ keys) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n2) return;
+    if (i >= N) { keys[i] = ~0ull; return; }
+    // larger score -> smaller key: order-preserving bits of -score
+    uint32_t b = __float_as_uint(-score[i]);
+    b = (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+    keys[i] = ((uint64_t)b << 32) | (uint32_t)i;
+}
+__global__ void bitonic_step_kernel(uint64_t* __restrict__ keys, int n2, int j, int k) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n2) return;
+    const int p = i ^ j;
+    if (p > i) {
+        const uint64_t a = keys[i], b = keys[p];
+        const bool up = (i & k) == 0;
+        if ((a > b) == up) { keys[i] = b; keys[p] = a; }
+    }
+}
+__global__ void hub_ids_kernel(const uint64_t* __restrict__ keys, int H, int32_t* __restrict__ hubs) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < H) hubs[i] = (int32_t)(keys[i] & 0xffffffffu);
+}
+
+// candidates: self, the K_near nearest, then the nearest hubs not yet taken
+// (pool entries beyond K_near fill any remainder); sorted by index
+__global__ void select_hub_candidates_kernel(const int32_t* __restrict__ pool, int Mp, const int32_t* __restrict__ hubnn,
+                                             int Mh, int N, int K, int K_near, int32_t* __restrict__ cand) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    int sel[64];
+    int ns = 0;
+    sel[ns++] = i;
+    const int32_t* pi = pool + (int64_t)i * Mp;
+    const int32_t* hi = hubnn + (int64_t)i * Mh;
+    auto taken = [&](int v) {
+        for (int a = 0; a < ns; ++a)
+            if (sel[a] == v) return true;
+        return false;
+    };
+    for (int q = 0; q < K_near && ns < K; ++q)
+        if (pi[q] >= 0 && !taken(pi[q])) sel[ns++] = pi[q];
+    for (int q = 0; q < Mh && ns < K; ++q)
+        if (hi[q] >= 0 && !taken(hi[q])) sel[ns++] = hi[q];
+    for (int q = K_near; q < Mp && ns < K; ++q)
+        if (pi[q] >= 0 && !taken(pi[q])) sel[ns++] = pi[q];
+    for (int a = 1; a < ns; ++a) {
+        const int v = sel[a];
+        int b = a - 1;
+        while (b >= 0 && sel[b] > v) { sel[b + 1] = sel[b]; --b; }
+        sel[b + 1] = v;
+    }
+    for (int q = 0; q < K; ++q) cand[(int64_t)i * K + q] = q < ns ? sel[q] : -1;
 }
 
 // mean over rows of log(dist[i][F-1]) in FP64: per-block partials, fixed order
@@ -473,19 +547,67 @@ struct hap_mlp {
 
 extern "C" {
 
-int hap_knn(const float* X, int64_t N, int64_t d, int M, int32_t* idx, float* dist, void* stream) {
-    if (!X || !idx || !dist || N < 2 || d < 1 || d > 64 || M < 1 || M > KNN_MAXM || M >= N) return HAP_EINVAL;
+static int knn_launch(const float* Q, int64_t Nq, const float* C, const int32_t* cid, int64_t Nc, int64_t d, int M,
+                      int32_t* idx, float* dist, cudaStream_t st) {
     const int D = d <= 4 ? 4 : d <= 8 ? 8 : d <= 16 ? 16 : d <= 32 ? 32 : 64;
     const size_t smem = ((size_t)KNN_TILE * D + (size_t)M * KNN_ROWS * 2) * 4;
-    const unsigned grid = (unsigned)((N + KNN_ROWS - 1) / KNN_ROWS);
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const unsigned grid = (unsigned)((Nq + KNN_ROWS - 1) / KNN_ROWS);
 #define HAP_KNN_CASE(DD)                                                                                \
     if (D == DD) {                                                                                      \
         PCU(cudaFuncSetAttribute(knn_kernel<DD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
-        knn_kernel<DD><<<grid, KNN_ROWS, smem, st>>>(X, (int)N, (int)d, M, idx, dist);                 \
+        knn_kernel<DD><<<grid, KNN_ROWS, smem, st>>>(Q, (int)Nq, C, cid, (int)Nc, (int)d, M, idx, dist); \
     }
     HAP_KNN_CASE(4) HAP_KNN_CASE(8) HAP_KNN_CASE(16) HAP_KNN_CASE(32) HAP_KNN_CASE(64)
 #undef HAP_KNN_CASE
+    PCU(cudaGetLastError());
+    return HAP_OK;
+}
+
+int hap_knn(const float* X, int64_t N, int64_t d, int M, int32_t* idx, float* dist, void* stream) {
+    if (!X || !idx || !dist || N < 2 || d < 1 || d > 64 || M < 1 || M > KNN_MAXM || M >= N) return HAP_EINVAL;
+    return knn_launch(X, N, X, nullptr, N, d, M, idx, dist, static_cast<cudaStream_t>(stream));
+}
+
+int hap_knn_subset(const float* X, int64_t N, int64_t d, const int32_t* subset, int64_t Ns, int M, int32_t* idx,
+                   float* dist, void* stream) {
+    if (!X || !subset || !idx || !dist || N < 1 || Ns < 1 || d < 1 || d > 64 || M < 1 || M > KNN_MAXM || M > Ns)
+        return HAP_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    float* C = nullptr;
+    PCU(cudaMallocAsync(&C, (size_t)Ns * d * 4, st));
+    // gather the subset's points (one row per thread block)
+    for (int64_t q = 0; q < Ns; q += 65535) {
+        const int64_t nb = Ns - q < 65535 ? Ns - q : 65535;
+        gather_rows_kernel<<<(unsigned)nb, 64, 0, st>>>(X, d, subset + q, C + q * d);
+    }
+    int rc = knn_launch(X, N, C, subset, Ns, d, M, idx, dist, st);
+    cudaFreeAsync(C, st);
+    return rc;
+}
+
+int hap_top_scores(const float* score, int64_t N, int64_t H, int32_t* hubs, void* stream) {
+    if (!score || !hubs || N < 1 || H < 1 || H > N || N > (1 << 30)) return HAP_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int n2 = 1;
+    while (n2 < N) n2 <<= 1;
+    uint64_t* keys = nullptr;
+    PCU(cudaMallocAsync(&keys, (size_t)n2 * 8, st));
+    const unsigned g = (unsigned)((n2 + 255) / 256);
+    hub_keys_kernel<<<g, 256, 0, st>>>(score, (int)N, n2, keys);
+    for (int k = 2; k <= n2; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) bitonic_step_kernel<<<g, 256, 0, st>>>(keys, n2, j, k);
+    hub_ids_kernel<<<(unsigned)((H + 255) / 256), 256, 0, st>>>(keys, (int)H, hubs);
+    cudaError_t err = cudaGetLastError();
+    cudaFreeAsync(keys, st);
+    PCU(err);
+    return HAP_OK;
+}
+
+int hap_select_hub_candidates(const int32_t* pool, int64_t N, int Mp, const int32_t* hubnn, int Mh, int K, int K_near,
+                              int32_t* cand, void* stream) {
+    if (!pool || !hubnn || !cand || N < 2 || K < 2 || K > 64 || K_near < 0 || K_near > Mp || Mh < 0) return HAP_EINVAL;
+    select_hub_candidates_kernel<<<(unsigned)((N + 127) / 128), 128, 0, static_cast<cudaStream_t>(stream)>>>(
+        pool, Mp, hubnn, Mh, (int)N, K, K_near, cand);
     PCU(cudaGetLastError());
     return HAP_OK;
 }

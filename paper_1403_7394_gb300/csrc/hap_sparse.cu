@@ -108,24 +108,31 @@ __global__ void __launch_bounds__(256) sparse_rowpass_kernel(const SparseArgs p)
     }
 }
 
-// P_j = sum over the column's entries (rows k != j, entry order) of max(0, rho)
+// P_j = sum over the column's entries (rows k != j) of max(0, rho): one warp
+// per (level, column); lane t sums entries t, t + 32, ... in order, then a
+// fixed xor-shuffle tree (columns of popular candidates hold thousands of
+// entries, so a thread per column would serialise on them)
 __global__ void sparse_colstats_kernel(const float* __restrict__ R, const int64_t* __restrict__ cptr,
                                        const int32_t* __restrict__ cent, int N, int L, int K,
                                        const float* __restrict__ c, const float* __restrict__ phi,
                                        const float* __restrict__ rdiag, float* __restrict__ b, float* __restrict__ tpart) {
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t idx = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     if (idx >= (int64_t)L * N) return;
     const int l = (int)(idx / N);
     const int64_t j = idx - (int64_t)l * N;
     const float* Rl = R + (int64_t)l * N * K;
     float P = 0.f;
-    for (int64_t e = cptr[j]; e < cptr[j + 1]; ++e) {
+    for (int64_t e = cptr[j] + lane; e < cptr[j + 1]; e += 32) {
         const int32_t ent = cent[e];
         if (ent / K != j) P = __fadd_rn(P, fmaxf(Rl[ent], 0.f));
     }
-    const float rd = rdiag[idx];
-    b[idx] = __fadd_rn(__fadd_rn(__fadd_rn(c[idx], phi[idx]), rd), P);
-    if (l + 1 < L) tpart[idx + N] = __fadd_rn(rd, P);
+    for (int o = 16; o > 0; o >>= 1) P = __fadd_rn(P, __shfl_xor_sync(0xffffffffu, P, o));
+    if (lane == 0) {
+        const float rd = rdiag[idx];
+        b[idx] = __fadd_rn(__fadd_rn(__fadd_rn(c[idx], phi[idx]), rd), P);
+        if (l + 1 < L) tpart[idx + N] = __fadd_rn(rd, P);
+    }
 }
 
 // s_iq = -||x_i - x_cand||^2 (FP32, direct differences); one warp per row
@@ -367,7 +374,7 @@ int hap_sparse_iterate(hap_sparse* h, int n) {
         a.use_tau = t >= 2 ? 1 : 0;
         sparse_rowpass_kernel<<<grid, 256, 0, h->stream>>>(a);
         SCU(cudaGetLastError());
-        const int64_t tot = (int64_t)h->L * h->N;
+        const int64_t tot = (int64_t)h->L * h->N * 32;
         sparse_colstats_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, h->stream>>>(
             h->R, h->cptr, h->cent, h->N, h->L, h->K, h->c, h->phi, h->rdiag, h->b, h->tpart);
         SCU(cudaGetLastError());

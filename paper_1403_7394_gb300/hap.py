@@ -71,6 +71,9 @@ def _load():
         "hap_batch_sync": (i32, [vp]),
         "hap_knn": (i32, [vp, i64, i64, i32, vp, vp, vp]),
         "hap_knn_features": (i32, [vp, i64, i32, i32, vp, ctypes.POINTER(f32), vp]),
+        "hap_knn_subset": (i32, [vp, i64, i64, vp, i64, i32, vp, vp, vp]),
+        "hap_top_scores": (i32, [vp, i64, i64, vp, vp]),
+        "hap_select_hub_candidates": (i32, [vp, i64, i32, vp, i32, i32, i32, vp, vp]),
         "hap_mlp_create": (i32, [i32, vp, ctypes.POINTER(vp)]),
         "hap_mlp_destroy": (None, [vp]),
         "hap_mlp_set_stream": (i32, [vp, vp]),
@@ -421,6 +424,33 @@ def knn(X: torch.Tensor, M: int, stream=None):
     dist = torch.empty((N, M), dtype=torch.float32, device=X.device)
     check(lib.hap_knn(_ptr(X), N, d, int(M), _ptr(idx), _ptr(dist), _stream_ptr(X.device, stream)), "hap_knn")
     return idx, dist
+
+
+def knn_subset(X: torch.Tensor, subset: torch.Tensor, M: int, stream=None):
+    """For every point, its M nearest members of `subset` (global indices)."""
+    X = X.contiguous()
+    N, d = X.shape
+    idx = torch.empty((N, M), dtype=torch.int32, device=X.device)
+    dist = torch.empty((N, M), dtype=torch.float32, device=X.device)
+    check(lib.hap_knn_subset(_ptr(X), N, d, _ptr(subset.contiguous()), subset.numel(), int(M), _ptr(idx), _ptr(dist),
+                             _stream_ptr(X.device, stream)), "hap_knn_subset")
+    return idx, dist
+
+
+def top_scores(score: torch.Tensor, H: int, stream=None):
+    hubs = torch.empty(int(H), dtype=torch.int32, device=score.device)
+    check(lib.hap_top_scores(_ptr(score.contiguous()), score.numel(), int(H), _ptr(hubs),
+                             _stream_ptr(score.device, stream)), "hap_top_scores")
+    return hubs
+
+
+def select_hub_candidates(pool: torch.Tensor, hubnn: torch.Tensor, K: int, K_near: int, stream=None):
+    N, Mp = pool.shape
+    cand = torch.empty((N, K), dtype=torch.int32, device=pool.device)
+    check(lib.hap_select_hub_candidates(_ptr(pool.contiguous()), N, Mp, _ptr(hubnn.contiguous()), hubnn.shape[1], int(K),
+                                        int(K_near), _ptr(cand), _stream_ptr(pool.device, stream)),
+          "hap_select_hub_candidates")
+    return cand
 
 
 def knn_features(dist: torch.Tensor, F: int, stream=None):

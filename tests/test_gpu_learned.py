@@ -2,8 +2,10 @@
 
 The network is trained on the GPU (hand-written forward/backward/Adam
 kernels) on exemplar labels from dense HAP runs of two training instances,
-then prunes a third instance to K = 16 candidates per row; sparse HAP on the
-learned candidates is compared with sparse HAP on the 15 nearest neighbours,
+then scores the points of a third instance; the N/64 highest-scoring points
+become hubs, and every row keeps itself, its 8 nearest neighbours and its
+nearest hubs (K = 16 candidates).  Sparse HAP on these learned candidates is
+compared with sparse HAP on the 15 nearest neighbours,
 both judged against dense HAP on the same instance (ARI of the level-1
 assignments and net-similarity gap, NS from the points in FP64).
 
@@ -68,12 +70,17 @@ def test_learned_candidates_beat_nearest_neighbours(report):
     Xt = torch.from_numpy(X32).to(DEV)
     pref_t = torch.from_numpy(np.repeat(prefs[:, None], N, axis=1)).to(DEV)
     ns_dense = hap.net_similarity_points(Xt, torch.from_numpy(e_dense).to(DEV), pref_t)
-    pool, dist = hap.knn(Xt, 128)
+    pool, dist = hap.knn(Xt, 32)
     f, _ = hap.knn_features(dist, 16)
     score = mlp.forward(f)
+    hubs = hap.top_scores(score, N // 64)
+    hubnn, _ = hap.knn_subset(Xt, hubs, K)
     res = {}
-    for name, sc, k_near in (("knn", None, K - 1), ("learned", score, K // 2)):
-        cand = hap.select_candidates(pool, K, k_near, sc)
+    for name in ("knn", "learned"):
+        if name == "knn":
+            cand = hap.select_candidates(pool, K, K - 1, None)
+        else:
+            cand = hap.select_hub_candidates(pool, hubnn, K, K // 2)
         sp = hap.HAPSparse(N, L, K, prefs=prefs, damping=LAM, c_mode="fixed", device=DEV)
         sp.set_candidates(cand, Xt)
         sp.iterate(T)
@@ -84,5 +91,5 @@ def test_learned_candidates_beat_nearest_neighbours(report):
                      "gap": float((ns_dense[0] - ns[0]) / abs(ns_dense[0])), "n_exemplars": int(len(np.unique(e[0])))}
     report(loss=[l0, l1], dense_exemplars=int(len(np.unique(e_dense[0]))), **res)
     assert l1 < l0
-    assert res["learned"]["ari"] >= res["knn"]["ari"] + 0.2
-    assert res["learned"]["gap"] < res["knn"]["gap"]
+    assert res["learned"]["ari"] >= res["knn"]["ari"] + 0.3
+    assert res["learned"]["gap"] < 0.25 * res["knn"]["gap"]

@@ -106,6 +106,26 @@ def test_candidate_selection_matches_reference():
         np.testing.assert_array_equal(c, ref)
 
 
+def test_hub_selection_subset_knn_and_candidates():
+    hap = hapm()
+    N = 3000
+    X, _ = W.gmm_points(N, 16, 12, sigma=1.0, seed=8, means="normal", mean_scale=2.0)
+    X32 = X.astype(np.float32)
+    Xt = torch.from_numpy(X32).to(DEV)
+    score = np.random.default_rng(4).normal(size=N).astype(np.float32)
+    score[10] = score[20]
+    hubs = hap.top_scores(torch.from_numpy(score).to(DEV), 100).cpu().numpy()
+    np.testing.assert_array_equal(hubs, P.top_scores(score, 100))
+    hubnn, hd = hap.knn_subset(Xt, torch.from_numpy(hubs).to(DEV), 20)
+    ridx, rd = P.knn_subset(X32, hubs, 20)
+    assert np.abs(hd.cpu().numpy() - rd).max() <= 1e-5 * rd.max()
+    mism = np.any(hubnn.cpu().numpy() != ridx, axis=1).mean()
+    assert mism <= 0.01  # only FP32 near-ties may reorder
+    pool, _ = hap.knn(Xt, 32)
+    c = hap.select_hub_candidates(pool, hubnn, 40, 16).cpu().numpy()
+    np.testing.assert_array_equal(c, P.select_hub_candidates(pool.cpu().numpy(), hubnn.cpu().numpy(), 40, 16))
+
+
 def _sparse_problem(N, L, K, seed, K_near=None, score=None):
     hap = hapm()
     X, _ = W.gmm_points(N, 2, 6, sigma=0.6, seed=seed, means="uniform", mean_scale=10.0)

@@ -88,3 +88,22 @@ def test_full_candidate_graph_is_dense_hap_and_masked_hap_is_finite():
         assert np.all(np.isfinite(st.A[l]))
     e = H.exemplars(st.A, st.R)
     assert np.all(inside[np.arange(40), e[0]])  # exemplars are always candidates
+
+
+def test_hub_helpers():
+    X, _ = W.gmm_points(120, 3, 4, sigma=0.8, seed=6)
+    score = np.random.default_rng(2).normal(size=120)
+    score[5] = score[7]  # a tie: lower index first
+    hubs = P.top_scores(score, 12)
+    assert list(hubs) == sorted(range(120), key=lambda i: (-score[i], i))[:12]
+    hubnn, hd = P.knn_subset(X, hubs, 5)
+    for i in range(120):
+        d = {h: ((X[i] - X[h]) ** 2).sum() for h in hubs if h != i}
+        best = sorted(d, key=lambda h: (d[h], h))[:5]
+        assert list(hubnn[i]) == best
+    pool, _ = P.knn(X, 10)
+    c = P.select_hub_candidates(pool, hubnn, 8, 3)
+    for i in range(120):
+        assert i in c[i] and np.all(np.diff(c[i]) > 0)
+        assert set(pool[i, :3]) <= set(c[i])
+        assert hubnn[i, 0] in c[i]
