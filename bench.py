@@ -56,10 +56,12 @@ def parse():
     ap.add_argument("--sbuild", default="bf16_split", choices=["bf16_split", "bf16", "f32"])
     ap.add_argument("--s-dtype", default="f32", choices=["f32", "bf16"])
     ap.add_argument("--iters", type=int, default=0, help="override the iteration count")
+    ap.add_argument("--n", type=int, default=0, help="first n points only (a smaller case for profiling)")
     ap.add_argument("--cpu-baseline", type=int, default=1)
     ap.add_argument("--e2e-steps", type=int, default=2)
     for k in ("block_threads", "cluster_size", "grid_clusters", "elems_per_thread"):
         ap.add_argument("--" + k.replace("_", "-"), type=int, default=0)
+    ap.add_argument("--col-sums", default="auto", choices=["auto", "smem", "tmem"])
     return ap.parse_args()
 
 
@@ -207,7 +209,12 @@ def main():
     if args.iters:
         T = args.iters
     X, prefs = make_inputs(args.workload, seed=rank)
-    shape_opts = {k: getattr(args, k) for k in ("block_threads", "cluster_size", "grid_clusters", "elems_per_thread")}
+    if args.n:
+        N = min(N, args.n)
+        X = np.ascontiguousarray(X[:N])
+        desc = f"first {N} points of: {desc}"
+    shape_opts = {k: getattr(args, k) for k in ("block_threads", "cluster_size", "grid_clusters", "elems_per_thread",
+                                                 "col_sums")}
     ctx = hap.HAP(N, L, prefs=prefs, damping=0.5, device=dev, s_dtype=args.s_dtype, profile=True, **shape_opts)
     stream = ctx.stream
     Xd = torch.from_numpy(X).to(dev)
@@ -281,7 +288,7 @@ def main():
     bytes_per_launch = float(N) * N * (16 * L + s_bytes)
     avg_rp_s = (rp_ms / rp_n) / 1e3 if rp_n else float("nan")
     achieved = bytes_per_launch / avg_rp_s / 1e9
-    traffic = ncu_traffic(args.workload, args.s_dtype)
+    traffic = ncu_traffic(args.workload, args.s_dtype) if N == WORKLOADS[args.workload][0] else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "peak_source": peak_src,
             "kernel": "rowpass_kernel", "launches_timed": rp_n, "avg_launch_ms": avg_rp_s * 1e3,
@@ -602,9 +609,12 @@ def ncu_traffic(workload: str, s_dtype: str):
 
 
 def kernel_hash() -> str:
+    """Digest of the row-pass sources (kernel and the device helpers it uses)."""
     import hashlib
-    p = os.path.join(ROOT, "paper_1403_7394_gb300", "csrc", "hap_rowpass.cu")
-    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for f in ("hap_rowpass.cu", "hap_common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1403_7394_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
 
 
 if __name__ == "__main__":

@@ -74,6 +74,19 @@ extern "C" {
 #define HAP_Q_ELEMS_PER_THREAD 6 /* columns per thread of the row pass     */
 #define HAP_Q_LAUNCHES      7 /* kernels this context has launched so far      */
 #define HAP_Q_BATCH_ITEMS_PER_CTA 8 /* batch scheduling granularity (tuned)      */
+#define HAP_Q_COL_SUMS      9 /* where the row pass keeps its column sums (HAP_COLSUM_*) */
+#define HAP_Q_STAGES       10 /* TMA ring stages of the row pass                */
+
+/* Where each row-pass thread keeps the running column sums of max(0, rho) of
+ * its columns (Eqs. 2.2-2.4) while its cluster walks its rows.  Both give the
+ * same bits for the same grid; they differ in how long a row fits on chip. */
+#define HAP_COLSUM_AUTO 0 /* the variant whose clusters cover more SMs, then
+                             fewer CTAs per cluster, then TMEM; shared memory
+                             when an explicit launch shape is given            */
+#define HAP_COLSUM_SMEM 1 /* shared memory: 4, 8 or 16 columns per thread      */
+#define HAP_COLSUM_TMEM 2 /* tensor memory (TMEM): 8 or 16 columns per thread,
+                             up to 512 threads; frees shared memory for the TMA
+                             ring, so a cluster holds twice as long a row      */
 
 typedef struct hap_options {
     int c_mode;        /* HAP_C_PAPER (default) or HAP_C_FIXED                         */
@@ -87,6 +100,7 @@ typedef struct hap_options {
     int grid_clusters; /* 0 = automatic (all co-resident clusters)                     */
     int elems_per_thread; /* 0 = automatic (8); 4, 8 or 16 columns per thread          */
     int profile;       /* 1: time every row-pass launch with CUDA events               */
+    int col_sums;      /* HAP_COLSUM_AUTO (default), HAP_COLSUM_SMEM or HAP_COLSUM_TMEM */
 } hap_options;
 
 typedef struct hap_ctx hap_ctx;

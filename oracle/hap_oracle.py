@@ -138,6 +138,16 @@ def positive_column_sums(R_l) -> np.ndarray:
     return Rp.sum(axis=0)
 
 
+def row_block_column_sums(R_rows, rows) -> np.ndarray:
+    """The part of P_j (positive_column_sums) contributed by the whole rows
+    ``rows`` of one level: sum over k in rows, k != j, of max(0, rho_kj).
+    Summing it over a partition of the rows gives P_j."""
+    rows = np.asarray(rows)
+    Rp = np.maximum(R_rows, 0.0)
+    Rp[np.arange(rows.size), rows] = 0.0
+    return Rp.sum(axis=0)
+
+
 def availability_update(A_rows, R_rows, rows, c_l, phi_l, R_diag, P, lam):
     """Eqs. 2.2 and 2.3 with damping, for the rows ``rows`` of one level.
 
@@ -273,9 +283,7 @@ def step_sharded(S, st: HAPState, rows, lam: float, c_mode: str, allreduce,
     if carry is None:  # column statistics of the current rho (Eqs. 2.2-2.4 sums)
         part = np.zeros((2, L, n))
         for l in range(L):
-            Rp = np.maximum(R[l][rows], 0.0)
-            Rp[np.arange(rows.size), rows] = 0.0
-            part[0, l] = Rp.sum(axis=0)
+            part[0, l] = row_block_column_sums(R[l][rows], rows)
             part[1, l, rows] = R[l][rows, rows]
         part = allreduce(part)
         carry = {"P": part[0], "Rdiag": part[1]}
@@ -295,9 +303,7 @@ def step_sharded(S, st: HAPState, rows, lam: float, c_mode: str, allreduce,
     # the one exchange: column sums of the new rho, and the owned c, phi, rho_jj
     part = np.zeros((4, L, n))
     for l in range(L):
-        Rp = np.maximum(R_new[l][rows], 0.0)
-        Rp[np.arange(rows.size), rows] = 0.0
-        part[0, l] = Rp.sum(axis=0)
+        part[0, l] = row_block_column_sums(R_new[l][rows], rows)
         part[1, l, rows] = R_new[l][rows, rows]
         part[2, l, rows] = c[l, rows]
         part[3, l, rows] = phi[l, rows]

@@ -5,6 +5,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 #include <vector>
 
@@ -65,42 +66,88 @@ int64_t padded_ld(int64_t N) { return (N + 31) / 32 * 32; }
 // Row-pass launch shape: one cluster holds a whole row (C CTAs x T threads x
 // 4K columns >= ld), the fewest CTAs per cluster whose shared memory fits;
 // then as many clusters as can be resident at once (persistent grid).
+// The fewest CTAs per cluster (1, 2, 4, 8, 16) whose T threads x 4K columns
+// cover the row and whose shared memory fits, for one column-sum variant.
+int shape_for(int64_t ld, int L, const hap_options& o, int tm, int K, int smem_limit, LaunchShape* out) {
+    const int64_t q4 = ld / 4;  // float4 columns
+    const int maxT = tm ? 512 : (K == 1 ? 1024 : K == 2 ? 512 : 256);
+    const int s_bf16 = o.s_dtype == HAP_S_BF16;
+    const int sizes[5] = {1, 2, 4, 8, 16};
+    for (int c : sizes) {
+        if (o.cluster_size && c != o.cluster_size) continue;
+        int T = o.block_threads;
+        const int quantum = tm ? 128 : 32;  // TMEM: whole lane quarters per warp group
+        if (T == 0) {
+            const int64_t per = (q4 + (int64_t)c * K - 1) / ((int64_t)c * K);
+            T = (int)((per + quantum - 1) / quantum * quantum);
+            if (T < quantum) T = quantum;
+            if (T > maxT) continue;
+        } else if (T < quantum || T > maxT || T % quantum) {
+            return HAP_EINVAL;
+        }
+        if ((int64_t)c * T * K * 4 < ld) continue;
+        LaunchShape sh{T, c, K, 0, tm, tm ? 4 : 0};
+        if (tm && rowpass_smem_bytes(sh, L, s_bf16) > (size_t)smem_limit) sh.nst = 2;
+        if (rowpass_smem_bytes(sh, L, s_bf16) > (size_t)smem_limit) continue;
+        if (tm && rowpass_tmem_columns(sh, L) > 512) return HAP_EUNSUPPORTED;
+        *out = sh;
+        return HAP_OK;
+    }
+    return HAP_EUNSUPPORTED;
+}
+
 int choose_shape(int64_t N, int L, const hap_options& o, LaunchShape* out) {
     const int64_t ld = padded_ld(N);
-    const int64_t q4 = ld / 4;  // float4 columns
-    // 8 columns per thread by default: enough work per step to amortise the
-    // per-row reduction, few enough registers for 512-thread CTAs.
-    const int K = o.elems_per_thread ? o.elems_per_thread / 4 : 2;
-    if (K != 1 && K != 2 && K != 4) return HAP_EINVAL;
-    if (o.elems_per_thread && o.elems_per_thread != 4 * K) return HAP_EINVAL;
-    const int maxT = K == 1 ? 1024 : K == 2 ? 512 : 256;
+    if (o.cluster_size < 0 || o.cluster_size > 16) return HAP_EINVAL;
+    if (o.col_sums < HAP_COLSUM_AUTO || o.col_sums > HAP_COLSUM_TMEM) return HAP_EINVAL;
     int dev = 0, smem_limit = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&smem_limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
         cudaGetLastError();
         return HAP_ECUDA;
     }
-    const int s_elem = o.s_dtype == HAP_S_BF16 ? 2 : 4;
-    const int sizes[5] = {1, 2, 4, 8, 16};
-    for (int c : sizes) {
-        if (o.cluster_size && c != o.cluster_size) continue;
-        if (o.cluster_size < 0 || o.cluster_size > 16) return HAP_EINVAL;
-        int T = o.block_threads;
-        if (T == 0) {
-            const int64_t per = (q4 + (int64_t)c * K - 1) / ((int64_t)c * K);
-            T = (int)((per + 31) / 32 * 32);
-            if (T < 32) T = 32;
-            if (T > maxT) continue;
-        } else if (T < 32 || T > maxT || T % 32) {
-            return HAP_EINVAL;
-        }
-        if ((int64_t)c * T * K * 4 < ld) continue;
-        LaunchShape sh{T, c, K, 0};
-        if (rowpass_smem_bytes(sh, L, s_elem == 2) > (size_t)smem_limit) continue;
-        *out = sh;
+    const bool explicit_shape = o.elems_per_thread || o.block_threads || o.cluster_size;
+    const int mode = o.col_sums != HAP_COLSUM_AUTO ? o.col_sums : explicit_shape ? HAP_COLSUM_SMEM : HAP_COLSUM_AUTO;
+    // 8 columns per thread by default with shared-memory sums (enough work per
+    // step to amortise the per-row reduction, few enough registers for
+    // 512-thread CTAs); 16 with TMEM sums (twice the row per cluster).
+    auto K_of = [&](int tm, int* K) {
+        *K = o.elems_per_thread ? o.elems_per_thread / 4 : (tm ? 4 : 2);
+        if (o.elems_per_thread && o.elems_per_thread != 4 * *K) return HAP_EINVAL;
+        if (tm ? (*K != 2 && *K != 4) : (*K != 1 && *K != 2 && *K != 4)) return HAP_EINVAL;
         return HAP_OK;
+    };
+    if (mode != HAP_COLSUM_AUTO) {
+        const int tm = mode == HAP_COLSUM_TMEM;
+        int K = 0, rc = K_of(tm, &K);
+        if (rc) return rc;
+        return shape_for(ld, L, o, tm, K, smem_limit, out);
     }
-    return HAP_EUNSUPPORTED;
+    // automatic: the variant whose co-resident clusters cover more SMs (a row
+    // too long for a cluster of 2 or 4 in one variant may fit in the other);
+    // on a tie the one with fewer CTAs per cluster (a cheaper row exchange),
+    // then TMEM sums (16 columns per thread; measured faster on GB300)
+    LaunchShape best{};
+    int64_t best_ctas = -1;
+    for (int tm = 1; tm >= 0; --tm) {
+        int K = 0;
+        if (K_of(tm, &K)) continue;
+        LaunchShape sh{};
+        if (shape_for(ld, L, o, tm, K, smem_limit, &sh) != HAP_OK) continue;
+        int maxc = 0;
+        if (rowpass_max_clusters(sh, L, o.s_dtype == HAP_S_BF16, &maxc) != cudaSuccess) {
+            cudaGetLastError();
+            return HAP_ECUDA;
+        }
+        const int64_t ctas = (int64_t)std::min<int64_t>(maxc, (N + 3) / 4) * sh.C;
+        if (ctas > best_ctas || (ctas == best_ctas && sh.C < best.C)) {
+            best = sh;
+            best_ctas = ctas;
+        }
+    }
+    if (best_ctas <= 0) return HAP_EUNSUPPORTED;
+    *out = best;
+    return HAP_OK;
 }
 
 int finish_shape(int64_t N, int L, const hap_options& o, LaunchShape* sh) {
@@ -523,6 +570,8 @@ int hap_query(hap_ctx* h, int key, int64_t* value) {
         case HAP_Q_ITER: *value = h->iter; return HAP_OK;
         case HAP_Q_ELEMS_PER_THREAD: *value = 4 * h->sh.K; return HAP_OK;
         case HAP_Q_LAUNCHES: *value = h->launches; return HAP_OK;
+        case HAP_Q_COL_SUMS: *value = h->sh.tm ? HAP_COLSUM_TMEM : HAP_COLSUM_SMEM; return HAP_OK;
+        case HAP_Q_STAGES: *value = h->sh.tm ? h->sh.nst : 3; return HAP_OK;
         default: return HAP_EINVAL;
     }
 }

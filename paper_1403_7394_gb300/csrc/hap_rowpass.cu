@@ -5,7 +5,9 @@
 //
 //   row pass, per row i, levels l = 0..L-1 in order, by one thread-block
 //   cluster that holds the whole row on chip (each CTA a contiguous slice of
-//   columns, each thread 4*K columns):
+//   columns, each thread 4*K columns; every thread keeps the column sums of
+//   its columns for all levels, in shared memory or, in the TMEM variant, in
+//   tensor memory so that shared memory holds only the TMA ring):
 //     1. alpha_{t-1} = damp(alpha_{t-2}, Eqs. 2.2/2.3 from b_{t-1}, rho_{t-1})
 //        is applied on the fly and written back (availability is kept one
 //        step behind so that A is read and written once per iteration);
@@ -28,18 +30,29 @@
 
 namespace hap {
 
-constexpr int kStages = 3;  // row slices in flight per CTA (TMA ring depth)
+constexpr int kStages = 3;  // TMA ring depth of the shared-memory-sums variant
 
-// Shared memory of one row-pass CTA: kStages x {A, R, S slices} | per-thread
-// column sums [L][K][T] float4 | exchange slots [2][C][32] float4 | mbarriers.
-__host__ __device__ inline size_t rowpass_smem_layout(int T, int K, int C, int L, int s_elem, size_t* stage_bytes,
-                                                      size_t* a_bytes) {
+// Shared memory of one row-pass CTA: nst x {A, R, S slices} | per-thread
+// column sums [L][K][T] float4 (not in the TMEM variant) | exchange slots
+// [2][C][32] float4 | mbarriers full[nst], xfull[2] | TMEM address slot.
+__host__ __device__ inline size_t rowpass_smem_layout(int T, int K, int C, int L, int s_elem, int nst, bool tm,
+                                                      size_t* stage_bytes, size_t* a_bytes) {
     const size_t W = (size_t)4 * K * T;
     const size_t a = (W * 4 + 127) / 128 * 128;
     const size_t sb = (W * s_elem + 127) / 128 * 128;
     if (stage_bytes) *stage_bytes = 2 * a + sb;
     if (a_bytes) *a_bytes = a;
-    return kStages * (2 * a + sb) + (size_t)L * W * 4 + (size_t)2 * C * 32 * 16 + (kStages + 2) * 8;
+    return nst * (2 * a + sb) + (tm ? 0 : (size_t)L * W * 4) + (size_t)2 * C * 32 * 16 + (nst + 2) * 8 + 8;
+}
+
+// TMEM columns of the TMEM variant: the warps sharing a lane quarter (T/128
+// of them) each hold L x 4K consecutive columns; allocation is a power of two
+// of at least 32 columns.
+__host__ __device__ inline int rowpass_tmem_cols(int T, int K, int L) {
+    const int need = (T / 128) * L * 4 * K;
+    int n = 32;
+    while (n < need) n *= 2;
+    return n;
 }
 
 template <typename ST>
@@ -51,8 +64,9 @@ HAP_DEV float4 load_s_smem<__nv_bfloat16>(const __nv_bfloat16* p) {
     return SVec<__nv_bfloat16>::to_f4(*reinterpret_cast<const uint2*>(p));
 }
 
-template <typename ST, int K, int MAXT>
+template <typename ST, int K, int MAXT, int NST, bool TM>
 __global__ void __launch_bounds__(MAXT, 1) rowpass_kernel(const RowPassArgs p) {
+    static_assert(!TM || K == 2 || K == 4, "TMEM column sums use 8 or 16 columns per thread");
     extern __shared__ __align__(128) unsigned char sm[];
     const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = T >> 5;
     const unsigned C = cluster_nctarank(), rank = cluster_ctarank();
@@ -67,11 +81,16 @@ __global__ void __launch_bounds__(MAXT, 1) rowpass_kernel(const RowPassArgs p) {
 
     // ---- shared memory carve-up ------------------------------------------------
     size_t stage_bytes, a_bytes;
-    rowpass_smem_layout(T, K, (int)C, L, (int)sizeof(ST), &stage_bytes, &a_bytes);
-    float4* acc = reinterpret_cast<float4*>(sm + kStages * stage_bytes);  // [L][K][T]
-    float4* xbuf = acc + (size_t)L * K * T;                             // [2][C][32]
-    const uint32_t bar0 = smem_addr(xbuf + 2 * C * 32);                 // full[kStages], xfull[2]
+    rowpass_smem_layout(T, K, (int)C, L, (int)sizeof(ST), NST, TM, &stage_bytes, &a_bytes);
+    float4* acc = reinterpret_cast<float4*>(sm + NST * stage_bytes);    // [L][K][T] (shared-memory sums)
+    float4* xbuf = acc + (TM ? 0 : (size_t)L * K * T);                  // [2][C][32]
+    const uint32_t bar0 = smem_addr(xbuf + 2 * C * 32);                 // full[NST], xfull[2]
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(xbuf + 2 * C * 32) + 2 * (NST + 2);
     const uint32_t sm0 = smem_addr(sm);
+    // TMEM variant: this thread's sums of level l live in lane 32*(warp%4)+lane,
+    // columns tacc + l*4K .. +4K-1.
+    const int tcols = TM ? rowpass_tmem_cols(T, K, L) : 0;
+    uint32_t tacc = 0;
 
     // ---- columns of this thread: slice of CTA `rank`, 4 consecutive per group
     const int W = 4 * K * T;
@@ -84,20 +103,31 @@ __global__ void __launch_bounds__(MAXT, 1) rowpass_kernel(const RowPassArgs p) {
         col[k] = slice0 + 4 * (k * T + tid);
         ok[k] = col[k] < (int)ld;
     }
-    for (int q = tid; q < L * K * T; q += T) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (!TM)
+        for (int q = tid; q < L * K * T; q += T) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (TM && warp == 0) tmem_alloc(smem_addr(tslot), (uint32_t)tcols);
     if (tid == 0) {
-        for (int q = 0; q < kStages + 2; ++q) mbar_init(bar0 + 8 * q, 1);
+        for (int q = 0; q < NST + 2; ++q) mbar_init(bar0 + 8 * q, 1);
         fence_mbarrier_init();
     }
+    if (TM) tc_fence_before();
     if (C > 1) cluster_barrier(); else __syncthreads();
+    if (TM) {
+        tc_fence_after();
+        tacc = *tslot + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((warp >> 2) * L * 4 * K);
+        float z[4 * K];
+#pragma unroll
+        for (int q = 0; q < 4 * K; ++q) z[q] = 0.f;
+        for (int ll = 0; ll < L; ++ll) tmem_store<4 * K>(tacc + (uint32_t)(ll * 4 * K), z);
+    }
 
     const int my_rows = N > (int)g ? (N - 1 - (int)g) / (int)G + 1 : 0;
     const int nsteps = my_rows * L;
 
     // One elected thread streams the A, R (and, when needed, S) row slices of
-    // step q into ring stage q % kStages.
+    // step q into ring stage q % NST.
     auto issue = [&](int q) {
-        const int row = (int)g + (q / L) * (int)G, l = q % L, st = q % kStages;
+        const int row = (int)g + (q / L) * (int)G, l = q % L, st = q % NST;
         const bool load_s = s_each_level || l == 0;
         const uint32_t bar = bar0 + 8 * st;
         const uint32_t dst = sm0 + (uint32_t)(st * stage_bytes);
@@ -113,7 +143,7 @@ __global__ void __launch_bounds__(MAXT, 1) rowpass_kernel(const RowPassArgs p) {
         }
     };
     if (tid == 0)
-        for (int q = 0; q < min(kStages, nsteps); ++q) issue(q);
+        for (int q = 0; q < min(NST, nsteps); ++q) issue(q);
 
     float4 srow[K];
 #pragma unroll
@@ -138,12 +168,12 @@ __global__ void __launch_bounds__(MAXT, 1) rowpass_kernel(const RowPassArgs p) {
     if (nsteps > 0) prefetch(row, 0);
 
     for (int s = 0; s < nsteps; ++s) {
-        const int st = s % kStages;
+        const int st = s % NST;
         const unsigned char* base = sm + (size_t)st * stage_bytes;
         const float* sA = reinterpret_cast<const float*>(base);
         const float* sR = reinterpret_cast<const float*>(base + a_bytes);
         const ST* sS = reinterpret_cast<const ST*>(base + 2 * a_bytes);
-        if (!bad) bad = !mbar_wait(bar0 + 8 * st, (uint32_t)(s / kStages) & 1u, p.status);
+        if (!bad) bad = !mbar_wait(bar0 + 8 * st, (uint32_t)(s / NST) & 1u, p.status);
 
         const bool new_s = s_each_level || l == 0;
         const int64_t voff = (int64_t)l * ld;
@@ -200,7 +230,7 @@ __global__ void __launch_bounds__(MAXT, 1) rowpass_kernel(const RowPassArgs p) {
         // summary sent to every CTA's shared memory (st.async + mbarrier) ------
         warp_top2(m1, k1, m2, cm);
         const int par = s & 1;
-        const uint32_t xbar = bar0 + 8 * (kStages + par);
+        const uint32_t xbar = bar0 + 8 * (NST + par);
         if (lane == 0) {
             const float4 v = make_float4(m1, m2, cm, __int_as_float(k1));
             const uint32_t slot = smem_addr(xbuf + (par * C + rank) * 32 + warp);
@@ -219,7 +249,7 @@ __global__ void __launch_bounds__(MAXT, 1) rowpass_kernel(const RowPassArgs p) {
         }
         warp_top2(m1, k1, m2, cm);
         // every warp of this CTA has read stage st: refill it
-        if (tid == 0 && s + kStages < nsteps) issue(s + kStages);
+        if (tid == 0 && s + NST < nsteps) issue(s + NST);
 
         // ---- inter-level messages of (i, l): Eqs. 2.4-2.6 --------------------
         const float cval = p.update_c ? cm : c_fixed;
@@ -232,6 +262,7 @@ __global__ void __launch_bounds__(MAXT, 1) rowpass_kernel(const RowPassArgs p) {
         }
 
         // ---- pass 2: responsibilities (Eq. 2.1) and column sums -----------------
+        float addv[TM ? 4 * K : 1];
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             const int dk = k1 - col[k];
@@ -248,22 +279,55 @@ __global__ void __launch_bounds__(MAXT, 1) rowpass_kernel(const RowPassArgs p) {
                 if (!bad) p.rdiag[voff + row] = f4_get(rn, dd);
             }
             if (ok[k] && !bad) st_stream(p.R + off + col[k], rn);
-            float4& a = acc[(l * K + k) * T + tid];
-            a.x = __fadd_rn(a.x, add.x);
-            a.y = __fadd_rn(a.y, add.y);
-            a.z = __fadd_rn(a.z, add.z);
-            a.w = __fadd_rn(a.w, add.w);
+            if constexpr (TM) {
+                addv[4 * k + 0] = add.x;
+                addv[4 * k + 1] = add.y;
+                addv[4 * k + 2] = add.z;
+                addv[4 * k + 3] = add.w;
+            } else {
+                float4& a = acc[(l * K + k) * T + tid];
+                a.x = __fadd_rn(a.x, add.x);
+                a.y = __fadd_rn(a.y, add.y);
+                a.z = __fadd_rn(a.z, add.z);
+                a.w = __fadd_rn(a.w, add.w);
+            }
+        }
+        if constexpr (TM) {
+            __syncwarp();  // tcgen05.ld / st are warp-collective
+            float cur[4 * K];
+            const uint32_t ta = tacc + (uint32_t)(l * 4 * K);
+            tmem_load<4 * K>(ta, cur);
+#pragma unroll
+            for (int q = 0; q < 4 * K; ++q) cur[q] = __fadd_rn(cur[q], addv[q]);
+            tmem_store<4 * K>(ta, cur);
         }
         if (++l == L) { l = 0; row += (int)G; }
     }
 
     // ---- per-cluster column partials ------------------------------------------
     for (int ll = 0; ll < L; ++ll) {
+        if constexpr (TM) {
+            float cur[4 * K];
+            __syncwarp();
+            tmem_load<4 * K>(tacc + (uint32_t)(ll * 4 * K), cur);
 #pragma unroll
-        for (int k = 0; k < K; ++k)
-            if (ok[k])
-                *reinterpret_cast<float4*>(p.partials + ((int64_t)g * L + ll) * ld + col[k]) =
-                    acc[(ll * K + k) * T + tid];
+            for (int k = 0; k < K; ++k)
+                if (ok[k])
+                    *reinterpret_cast<float4*>(p.partials + ((int64_t)g * L + ll) * ld + col[k]) =
+                        make_float4(cur[4 * k], cur[4 * k + 1], cur[4 * k + 2], cur[4 * k + 3]);
+        } else {
+#pragma unroll
+            for (int k = 0; k < K; ++k)
+                if (ok[k])
+                    *reinterpret_cast<float4*>(p.partials + ((int64_t)g * L + ll) * ld + col[k]) =
+                        acc[(ll * K + k) * T + tid];
+        }
+    }
+    if constexpr (TM) {
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (warp == 0) tmem_dealloc(*tslot, (uint32_t)tcols);
     }
     // No CTA may leave while a peer can still write into its shared memory.
     if (C > 1) cluster_barrier();
@@ -322,34 +386,9 @@ __global__ void prepare_from_R_kernel(const float* __restrict__ R, int G, int L,
 }
 
 // ---------------------------------------------------------------------------
-template <typename ST, int K, int MAXT>
-static cudaError_t launch_one(const RowPassArgs& a, const LaunchShape& sh, cudaStream_t st) {
-    auto kern = rowpass_kernel<ST, K, MAXT>;
-    const size_t smem = rowpass_smem_bytes(sh, a.L, sizeof(ST) == 2);
-    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (err != cudaSuccess) return err;
-    if (sh.C > 8) {
-        err = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        if (err != cudaSuccess) return err;
-    }
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(sh.G * sh.C), 1, 1);
-    cfg.blockDim = dim3((unsigned)sh.T, 1, 1);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = (unsigned)sh.C;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kern, a);
-}
-
-template <typename ST, int K, int MAXT>
-static cudaError_t max_clusters_one(const LaunchShape& sh, int L, int* out) {
-    auto kern = rowpass_kernel<ST, K, MAXT>;
+template <typename ST, int K, int MAXT, int NST, bool TM>
+static cudaError_t cluster_config(const LaunchShape& sh, int L, cudaLaunchConfig_t* cfg, cudaLaunchAttribute* attr) {
+    auto kern = rowpass_kernel<ST, K, MAXT, NST, TM>;
     const size_t smem = rowpass_smem_bytes(sh, L, sizeof(ST) == 2);
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
@@ -357,23 +396,51 @@ static cudaError_t max_clusters_one(const LaunchShape& sh, int L, int* out) {
         err = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         if (err != cudaSuccess) return err;
     }
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)sh.C, 1, 1);
-    cfg.blockDim = dim3((unsigned)sh.T, 1, 1);
-    cfg.dynamicSmemBytes = smem;
-    cudaLaunchAttribute attr[1];
+    cfg->blockDim = dim3((unsigned)sh.T, 1, 1);
+    cfg->dynamicSmemBytes = smem;
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = (unsigned)sh.C;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaOccupancyMaxActiveClusters(out, kern, &cfg);
+    cfg->attrs = attr;
+    cfg->numAttrs = 1;
+    return cudaSuccess;
 }
 
-size_t rowpass_smem_bytes(const LaunchShape& sh, int L, int s_bf16) {
-    return rowpass_smem_layout(sh.T, sh.K, sh.C, L, s_bf16 ? 2 : 4, nullptr, nullptr);
+template <typename ST, int K, int MAXT, int NST, bool TM>
+static cudaError_t launch_one(const RowPassArgs& a, const LaunchShape& sh, cudaStream_t st) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    cudaError_t err = cluster_config<ST, K, MAXT, NST, TM>(sh, a.L, &cfg, attr);
+    if (err != cudaSuccess) return err;
+    cfg.gridDim = dim3((unsigned)(sh.G * sh.C), 1, 1);
+    cfg.stream = st;
+    return cudaLaunchKernelEx(&cfg, rowpass_kernel<ST, K, MAXT, NST, TM>, a);
 }
+
+template <typename ST, int K, int MAXT, int NST, bool TM>
+static cudaError_t max_clusters_one(const LaunchShape& sh, int L, int* out) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    cudaError_t err = cluster_config<ST, K, MAXT, NST, TM>(sh, L, &cfg, attr);
+    if (err != cudaSuccess) return err;
+    cfg.gridDim = dim3((unsigned)sh.C, 1, 1);
+    return cudaOccupancyMaxActiveClusters(out, rowpass_kernel<ST, K, MAXT, NST, TM>, &cfg);
+}
+
+// The TMEM variant asks for more than half of an SM's 228 KB of shared memory
+// so that at most one of its CTAs is resident per SM: its TMEM allocation
+// (at most 512 columns) then never waits for another row-pass CTA, which
+// could itself be waiting for a cluster peer blocked in allocation.
+constexpr size_t kTmemMinSmem = 116 * 1024;
+
+size_t rowpass_smem_bytes(const LaunchShape& sh, int L, int s_bf16) {
+    const int nst = sh.tm ? sh.nst : kStages;
+    const size_t bytes = rowpass_smem_layout(sh.T, sh.K, sh.C, L, s_bf16 ? 2 : 4, nst, sh.tm != 0, nullptr, nullptr);
+    return sh.tm && bytes < kTmemMinSmem ? kTmemMinSmem : bytes;
+}
+
+int rowpass_tmem_columns(const LaunchShape& sh, int L) { return sh.tm ? rowpass_tmem_cols(sh.T, sh.K, L) : 0; }
 
 cudaError_t launch_fill_alpha_padding(float* A, int64_t rows, int64_t N, int64_t ld, cudaStream_t st) {
     if (ld == N) return cudaSuccess;
@@ -382,17 +449,27 @@ cudaError_t launch_fill_alpha_padding(float* A, int64_t rows, int64_t N, int64_t
     return cudaGetLastError();
 }
 
+// Instantiated shapes: shared-memory sums with 4, 8 or 16 columns per thread
+// and a 3-stage ring; TMEM sums with 8 or 16 columns per thread and a 2- or
+// 4-stage ring.
+#define HAP_ROWPASS_DISPATCH_ST(ST, FN, ...)                                        \
+    do {                                                                            \
+        if (!sh.tm) {                                                               \
+            if (sh.K == 1) return FN<ST, 1, 1024, kStages, false>(__VA_ARGS__);     \
+            if (sh.K == 2) return FN<ST, 2, 512, kStages, false>(__VA_ARGS__);      \
+            if (sh.K == 4) return FN<ST, 4, 256, kStages, false>(__VA_ARGS__);      \
+        } else if (sh.nst == 2) {                                                   \
+            if (sh.K == 2) return FN<ST, 2, 512, 2, true>(__VA_ARGS__);             \
+            if (sh.K == 4) return FN<ST, 4, 512, 2, true>(__VA_ARGS__);             \
+        } else if (sh.nst == 4) {                                                   \
+            if (sh.K == 2) return FN<ST, 2, 512, 4, true>(__VA_ARGS__);             \
+            if (sh.K == 4) return FN<ST, 4, 512, 4, true>(__VA_ARGS__);             \
+        }                                                                           \
+    } while (0)
 #define HAP_ROWPASS_DISPATCH(FN, ...)                                               \
     do {                                                                            \
-        if (s_bf16) {                                                               \
-            if (sh.K == 1) return FN<__nv_bfloat16, 1, 1024>(__VA_ARGS__);          \
-            if (sh.K == 2) return FN<__nv_bfloat16, 2, 512>(__VA_ARGS__);           \
-            if (sh.K == 4) return FN<__nv_bfloat16, 4, 256>(__VA_ARGS__);           \
-        } else {                                                                    \
-            if (sh.K == 1) return FN<float, 1, 1024>(__VA_ARGS__);                  \
-            if (sh.K == 2) return FN<float, 2, 512>(__VA_ARGS__);                   \
-            if (sh.K == 4) return FN<float, 4, 256>(__VA_ARGS__);                   \
-        }                                                                           \
+        if (s_bf16) HAP_ROWPASS_DISPATCH_ST(__nv_bfloat16, FN, __VA_ARGS__);        \
+        else HAP_ROWPASS_DISPATCH_ST(float, FN, __VA_ARGS__);                       \
         return cudaErrorInvalidValue;                                               \
     } while (0)
 

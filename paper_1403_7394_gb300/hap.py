@@ -21,13 +21,15 @@ S_DTYPES = {"f32": 0, "bf16": 1}
 SBUILD = {"f32": 0, "bf16": 1, "bf16_split": 2}
 Q_BLOCK_THREADS, Q_CLUSTER_SIZE, Q_GRID_CLUSTERS, Q_LD, Q_ITER, Q_ELEMS_PER_THREAD, Q_LAUNCHES = 1, 2, 3, 4, 5, 6, 7
 Q_BATCH_ITEMS_PER_CTA = 8
+Q_COL_SUMS, Q_STAGES = 9, 10
+COL_SUMS = {"auto": 0, "smem": 1, "tmem": 2}
 
 
 class HapOptions(ctypes.Structure):
     _fields_ = [("c_mode", ctypes.c_int), ("schedule", ctypes.c_int), ("s_dtype", ctypes.c_int),
                 ("s_per_level", ctypes.c_int), ("block_threads", ctypes.c_int),
                 ("cluster_size", ctypes.c_int), ("grid_clusters", ctypes.c_int),
-                ("elems_per_thread", ctypes.c_int), ("profile", ctypes.c_int)]
+                ("elems_per_thread", ctypes.c_int), ("profile", ctypes.c_int), ("col_sums", ctypes.c_int)]
 
 
 def _load():
@@ -122,7 +124,7 @@ def _ptr(t: torch.Tensor | None):
 
 
 def options(c_mode="paper", s_dtype="f32", s_per_level=False, block_threads=0, cluster_size=0,
-            grid_clusters=0, elems_per_thread=0, profile=False) -> HapOptions:
+            grid_clusters=0, elems_per_thread=0, profile=False, col_sums="auto") -> HapOptions:
     o = HapOptions()
     lib.hap_default_options(ctypes.byref(o))
     o.c_mode = C_MODES[c_mode]
@@ -133,6 +135,7 @@ def options(c_mode="paper", s_dtype="f32", s_per_level=False, block_threads=0, c
     o.grid_clusters = int(grid_clusters)
     o.elems_per_thread = int(elems_per_thread)
     o.profile = int(bool(profile))
+    o.col_sums = COL_SUMS[col_sums]
     return o
 
 
@@ -274,7 +277,8 @@ class HAP:
     def shape(self):
         return {"block_threads": self.query(Q_BLOCK_THREADS), "cluster_size": self.query(Q_CLUSTER_SIZE),
                 "grid_clusters": self.query(Q_GRID_CLUSTERS), "ld": self.query(Q_LD),
-                "elems_per_thread": self.query(Q_ELEMS_PER_THREAD)}
+                "elems_per_thread": self.query(Q_ELEMS_PER_THREAD),
+                "col_sums": {1: "smem", 2: "tmem"}[self.query(Q_COL_SUMS)], "stages": self.query(Q_STAGES)}
 
     @property
     def launches(self) -> int:

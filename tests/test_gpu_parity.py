@@ -79,6 +79,13 @@ SHAPES = [
     (4099, 2, {}),
     (3000, 1, {"cluster_size": 16, "block_threads": 64}),
     (1500, 4, {"grid_clusters": 7}),
+    # column sums in tensor memory: 8 or 16 columns per thread, 2- or 4-stage ring
+    (37, 3, {"col_sums": "tmem"}),
+    (500, 2, {"col_sums": "tmem", "elems_per_thread": 8}),
+    (2051, 3, {"col_sums": "tmem"}),
+    (4099, 2, {"col_sums": "tmem", "cluster_size": 2}),
+    (3000, 4, {"col_sums": "tmem", "cluster_size": 4, "elems_per_thread": 8}),
+    (1500, 5, {"col_sums": "tmem", "block_threads": 384, "grid_clusters": 5}),
 ]
 
 
@@ -323,63 +330,122 @@ def test_error_codes():
 
 
 # ----------------------------------------------------------------- full size
+def sampled_step_errors(ctx, prefs, lam, n_rows=48, chunk=2048, seed=2):
+    """One iteration of a large context from its own current state, checked
+    against the reference's equations: c, tau and phi on every row (from the
+    GPU's state, streamed to the host in row blocks), rho and alpha on
+    n_rows sampled rows per level (alpha from the column statistics of the
+    GPU's new rho)."""
+    N, L = ctx.N, ctx.L
+    rows = np.sort(np.random.default_rng(seed).choice(N, n_rows, replace=False))
+    rows_t = torch.from_numpy(rows).to(DEV)
+    host = lambda t: t.cpu().numpy().astype(np.float64)
+    S = ctx.get_similarity(0)
+    g0 = ctx.get_state()
+    c = np.empty((L, N))
+    phi = np.zeros((L, N))
+    P0 = np.zeros((L, N))
+    Rd0 = np.empty((L, N))
+    for l in range(L):
+        for r0 in range(0, N, chunk):
+            blk = np.arange(r0, min(N, r0 + chunk))
+            A = host(g0["A"][l, r0:r0 + blk.size])
+            R = host(g0["R"][l, r0:r0 + blk.size])
+            c[l, blk] = H.cluster_preference_update(A[None], R[None])[0]       # Eq. 2.6
+            P0[l] += H.row_block_column_sums(R, blk)
+            if l >= 1:                                                       # Eq. 2.5
+                Sb = host(S[r0:r0 + blk.size])
+                Sb[np.arange(blk.size), blk] = prefs[l]
+                phi[l - 1, blk] = H.phi_update(np.stack([A, A]), np.stack([Sb, Sb]))[0]
+        Rd0[l] = host(torch.diagonal(g0["R"][l]))
+    tau = np.full((L, N), np.inf)
+    for l in range(1, L):                                                    # Eq. 2.4
+        tau[l] = c[l - 1] + Rd0[l - 1] + P0[l - 1]
+    A0r = host(g0["A"][:, rows_t])
+    R0r = host(g0["R"][:, rows_t])
+    Sr = host(S[rows_t])
+    del g0, S
+    ctx.iterate(1)
+    g1 = ctx.get_state()
+    errs = {}
+    for fld, ref in (("c", c), ("tau", tau), ("phi", phi)):
+        errs[fld] = H.message_rel_error(host(g1[fld]), ref)
+    eR, eA = 0.0, 0.0
+    for l in range(L):
+        P1 = np.zeros(N)
+        for r0 in range(0, N, chunk):
+            blk = np.arange(r0, min(N, r0 + chunk))
+            P1 += H.row_block_column_sums(host(g1["R"][l, r0:r0 + blk.size]), blk)
+        Rd1 = host(torch.diagonal(g1["R"][l]))
+        Sl = Sr.copy()
+        Sl[np.arange(rows.size), rows] = prefs[l]
+        Rn = H.responsibility_update(Sl, A0r[l], R0r[l], tau[l][rows], lam)   # Eq. 2.1
+        R1r = host(g1["R"][l][rows_t])
+        eR = max(eR, H.message_rel_error(R1r, Rn))
+        An = H.availability_update(A0r[l], R1r, rows, c[l], phi[l], Rd1, P1, lam)  # Eqs. 2.2, 2.3
+        eA = max(eA, H.message_rel_error(host(g1["A"][l][rows_t]), An))
+    errs["R"], errs["A"] = eR, eA
+    return errs
+
+
+def median_pref(X32, seed=1):
+    N = X32.shape[0]
+    i, j = W.sample_pairs(N, 1 << 16, seed=seed)
+    diff = X32[i].astype(np.float64) - X32[j].astype(np.float64)
+    return np.float32(np.median(-np.einsum("kd,kd->k", diff, diff)))
+
+
 def test_full_size_teacher_forced_sampled_rows(report):
     """The benchmark workload (N = 8192 points in 64-D, L = 4, S from the
-    tensor-core BF16-split build) in the benchmark's default launch shape: one
-    iteration from the GPU's own state at t = 5, checked on 48 sampled rows
-    per level against the reference's equations (c, tau, phi, rho on whole
-    rows; alpha from the column statistics of the GPU's new rho)."""
+    tensor-core BF16-split build) in the benchmark's default launch shape (one
+    CTA per row, column sums in TMEM): one iteration from the GPU's own state
+    at t = 5."""
     hap = hap_mod()
-    N, d, L, lam = 8192, 64, 4, 0.5
-    X, _ = W.config1(seed=0)
-    X32 = X.astype(np.float32)
-    i, j = W.sample_pairs(N, 1 << 16, seed=1)
-    diff = X32[i].astype(np.float64) - X32[j].astype(np.float64)
-    pref = np.float32(np.median(-np.einsum("kd,kd->k", diff, diff)))
-    prefs = np.full(L, pref, dtype=np.float32)
+    N, L, lam = 8192, 4, 0.5
+    X32 = W.config1(seed=0)[0].astype(np.float32)
+    prefs = np.full(L, median_pref(X32), dtype=np.float32)
     ctx = hap.HAP(N, L, prefs=prefs, damping=lam, device=DEV)
     ctx.build_similarity(torch.from_numpy(X32).to(DEV), mode="bf16_split")
     ctx.iterate(5)
-    g0 = ctx.get_state()
-    S32 = ctx.get_similarity(0).cpu().numpy()
-    ctx.iterate(1)
-    g1 = ctx.get_state()
-    rows = np.sort(np.random.default_rng(2).choice(N, 48, replace=False))
-    A0 = g0["A"].cpu().numpy()
-    R0 = g0["R"].cpu().numpy()
-    R1 = g1["R"].cpu().numpy()
-    c0 = g0["c"].cpu().numpy().astype(np.float64)
-    S = S32.astype(np.float64)
-    # inter-level vectors of iteration 6 from the GPU's state after 5 (Eqs. 2.4-2.6)
-    c = np.stack([H.cluster_preference_update(A0[l:l + 1].astype(np.float64), R0[l:l + 1].astype(np.float64))[0]
-                  for l in range(L)])
-    Rdiag0 = np.stack([np.diagonal(R0[l]).astype(np.float64) for l in range(L)])
-    P0 = np.stack([H.positive_column_sums(R0[l].astype(np.float64)) for l in range(L)])
-    tau = np.full((L, N), np.inf)
-    for l in range(1, L):
-        tau[l] = c[l - 1] + Rdiag0[l - 1] + P0[l - 1]
-    phi = np.zeros((L, N))
-    for l in range(L - 1):
-        Sl = S.copy()
-        np.fill_diagonal(Sl, prefs[l + 1])
-        phi[l] = np.max(A0[l + 1].astype(np.float64) + Sl, axis=1)
-    errs = {}
-    for fld, ref in (("c", c), ("tau", tau), ("phi", phi)):
-        errs[fld] = H.message_rel_error(g1[fld].cpu().numpy().astype(np.float64), ref)
-    eR, eA = 0.0, 0.0
-    for l in range(L):
-        Sl = S[rows].copy()
-        Sl[np.arange(len(rows)), rows] = prefs[l]
-        Rn = H.responsibility_update(Sl, A0[l][rows].astype(np.float64), R0[l][rows].astype(np.float64),
-                                     tau[l][rows], lam)
-        eR = max(eR, H.message_rel_error(R1[l][rows].astype(np.float64), Rn))
-        # alpha of iteration 6 for the sampled rows, from the column statistics
-        # of the GPU's rho_6 (teacher forcing through the column sums)
-        R1l = R1[l].astype(np.float64)
-        An = H.availability_update(A0[l][rows].astype(np.float64), R1l[rows], rows, c[l], phi[l],
-                                   np.diagonal(R1l).copy(), H.positive_column_sums(R1l), lam)
-        eA = max(eA, H.message_rel_error(g1["A"][l][rows].cpu().numpy().astype(np.float64), An))
-    errs["R"], errs["A"] = eR, eA
+    errs = sampled_step_errors(ctx, prefs, lam)
     report(shape=ctx.shape, errs=errs)
     assert all(e <= TOL for e in errs.values()), errs
-    assert ctx.shape["elems_per_thread"] == 8 and ctx.shape["cluster_size"] == 2
+    assert ctx.shape["col_sums"] == "tmem" and ctx.shape["cluster_size"] == 1
+
+
+@pytest.mark.parametrize("s_dtype", ["bf16", "f32"])
+def test_large_dense_teacher_forced_sampled_rows(s_dtype, report):
+    """The large dense workload (N = 32768 texture patches in 192-D, L = 3,
+    S from the BF16-split tensor-core build, stored in BF16 or FP32) in its
+    automatic launch shape (column sums in TMEM, clusters of 4 CTAs holding a
+    row): one iteration from the GPU's own state at t = 3."""
+    hap = hap_mod()
+    N, L, lam = 32768, 3, 0.5
+    X32 = W.config2(seed=0)[0].astype(np.float32)
+    prefs = np.full(L, median_pref(X32), dtype=np.float32)
+    ctx = hap.HAP(N, L, prefs=prefs, damping=lam, device=DEV, s_dtype=s_dtype)
+    ctx.build_similarity(torch.from_numpy(X32).to(DEV), mode="bf16_split")
+    ctx.iterate(3)
+    errs = sampled_step_errors(ctx, prefs, lam, n_rows=24, chunk=1024)
+    report(shape=ctx.shape, errs=errs)
+    assert all(e <= TOL for e in errs.values()), errs
+    assert ctx.shape["col_sums"] == "tmem" and ctx.shape["cluster_size"] == 4
+    ctx.close()
+
+
+def test_tmem_and_shared_memory_sums_agree_bitwise():
+    """The two column-sum variants run the same arithmetic in the same order
+    for the same grid, so five iterations give identical bits."""
+    N, L, lam = 3001, 3, 0.5
+    S32, prefs, _ = problem(N, L, seed=11)
+    out = []
+    for opt in ({"col_sums": "smem", "elems_per_thread": 8}, {"col_sums": "tmem", "elems_per_thread": 16},
+                {"col_sums": "tmem", "elems_per_thread": 8, "cluster_size": 2}):
+        ctx = make_ctx(N, L, prefs, lam, S32, grid_clusters=24, **opt)
+        ctx.iterate(5)
+        out.append((ctx.shape, ctx.get_state()))
+        ctx.close()
+    assert out[0][0]["col_sums"] == "smem" and out[1][0]["col_sums"] == "tmem"
+    for shape, g in out[1:]:
+        for f in ("A", "R", "c", "tau", "phi"):
+            assert torch.equal(out[0][1][f], g[f]), (shape, f)

@@ -286,3 +286,17 @@ def test_message_rel_error():
     y = x.copy()
     y[0, 0] = 5.0
     assert H.message_rel_error(y, x) == float("inf")
+
+
+def test_row_block_column_sums_partition():
+    """Column sums over a partition of the rows add up to P_j of the whole
+    matrix, and a hand-checked 3 x 3 case (negative entries and the diagonal
+    drop out)."""
+    R = np.array([[5.0, -1.0, 2.0], [3.0, 7.0, -4.0], [0.5, 1.5, 9.0]])
+    assert np.array_equal(H.positive_column_sums(R), [3.5, 1.5, 2.0])
+    assert np.array_equal(H.row_block_column_sums(R[1:], np.array([1, 2])), [3.5, 1.5, 0.0])
+    rng = np.random.default_rng(4)
+    R = rng.normal(size=(37, 37))
+    parts = [np.arange(0, 10), np.arange(10, 11), np.arange(11, 37)]
+    total = sum(H.row_block_column_sums(R[b], b) for b in parts)
+    assert np.allclose(total, H.positive_column_sums(R), rtol=0, atol=1e-12)
