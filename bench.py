@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--s-dtype", default="f32", choices=["f32", "bf16"])
     ap.add_argument("--iters", type=int, default=0, help="override the iteration count")
     ap.add_argument("--n", type=int, default=0, help="first n points only (a smaller case for profiling)")
+    ap.add_argument("--instances", type=int, default=0, help="first B instances only (batched; for profiling)")
     ap.add_argument("--cpu-baseline", type=int, default=1)
     ap.add_argument("--e2e-steps", type=int, default=2)
     for k in ("block_threads", "cluster_size", "grid_clusters", "elems_per_thread"):
@@ -333,6 +334,10 @@ def run_batched(args, world, rank, local):
     if args.iters:
         T = args.iters
     insts = W.batch_instances(B, d=d, seed=rank)
+    if args.instances:
+        B = min(B, args.instances)
+        insts = insts[:B]
+        desc = f"first {B} of: {desc}"
     Ns = [x["X"].shape[0] for x in insts]
     Ls = [x["L"] for x in insts]
     prefs = []

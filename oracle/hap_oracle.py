@@ -49,6 +49,20 @@ notes of the repository):
       identical to flat affinity propagation.
   R9  Net similarity, not defined in the paper, is NS^l = sum_i s^l_{i, e_i^l}
       with s^l_ii the preference of level l.
+  R10 Eq. 2.7 (optional level-wise similarity update; its index j is both
+      free and bound as printed) is read element-wise:
+      s^{l+1}_ij = s^l_ij + kappa (alpha^l_ij + rho^l_ij) for i != j, the
+      diagonal of level l+1 staying its preference.  kappa = 0 (default)
+      leaves every level's S as given.  Jacobi: built from the
+      start-of-iteration messages; Gauss-Seidel: from level l's messages just
+      updated.  NS (R9) keeps using the given S.
+  R11 Level schedule "gauss_seidel" (Algorithm 1's sequential level loop):
+      for l = 1..L in order, rho^l (Eq. 2.1 with the tau^l that level l-1
+      sent in this iteration, +inf at l = 1), then alpha^l (Eqs. 2.2-2.3 with
+      c^l and phi^l as they stand), then the messages level l sends: c^l
+      (Eq. 2.6, c_mode "paper"), tau^{l+1} (Eq. 2.4) and phi^{l-1} (Eq. 2.5)
+      from the new alpha^l and rho^l.  Algorithm 1 has no first-iteration
+      exception, so c and tau are updated from t = 1; phi starts at 0.
 """
 from __future__ import annotations
 
@@ -58,6 +72,8 @@ import numpy as np
 
 PAPER = "paper"
 FIXED = "fixed"
+JACOBI = "jacobi"
+GAUSS_SEIDEL = "gauss_seidel"
 
 
 # ---------------------------------------------------------------------------
@@ -218,14 +234,33 @@ def init_state(L: int, N: int, c0=None) -> HAPState:
                     tau=np.full((L, N), np.inf), phi=np.zeros((L, N)), t=0)
 
 
-def step(S, st: HAPState, lam: float, c_mode: str = PAPER) -> HAPState:
+def similarity_level_update(S_l, A_l, R_l, pref_next, kappa):
+    """Eq. 2.7 (reading R10): the level-(l+1) similarity from level l,
+    s_ij + kappa (alpha_ij + rho_ij) off the diagonal, pref_next on it."""
+    out = S_l + kappa * (A_l + R_l)
+    idx = np.arange(S_l.shape[0])
+    out[idx, idx] = pref_next
+    return out
+
+
+def step(S, st: HAPState, lam: float, c_mode: str = PAPER, schedule: str = JACOBI,
+         kappa: float = 0.0) -> HAPState:
     """One HAP iteration (number st.t + 1) on the (L, N, N) similarity tensor S.
 
     Order (readings R4-R6): inter-level quantities from the start-of-iteration
     state, then rho at every level (Eq. 2.1), then alpha at every level from
-    the new rho (Eqs. 2.2-2.3)."""
+    the new rho (Eqs. 2.2-2.3).  schedule="gauss_seidel" runs Algorithm 1's
+    level loop instead (R11); kappa > 0 applies Eq. 2.7 (R10)."""
+    if schedule == GAUSS_SEIDEL:
+        return step_gauss_seidel(S, st, lam, c_mode, kappa)
+    if schedule != JACOBI:
+        raise ValueError(f"unknown schedule {schedule!r}")
     S = np.asarray(S, dtype=np.float64)
     L, n, _ = S.shape
+    if kappa:
+        S = S.copy()
+        for l in range(L - 1):                                 # Eq. 2.7
+            S[l + 1] = similarity_level_update(S[l], st.A[l], st.R[l], np.diagonal(S[l + 1]), kappa)
     t = st.t + 1
     c = st.c.copy()
     if t >= 2:
@@ -249,14 +284,41 @@ def step(S, st: HAPState, lam: float, c_mode: str = PAPER) -> HAPState:
     return HAPState(A=A_new, R=R_new, c=c, tau=tau, phi=phi, t=t)
 
 
+def step_gauss_seidel(S, st: HAPState, lam: float, c_mode: str = PAPER, kappa: float = 0.0) -> HAPState:
+    """One iteration of Algorithm 1's sequential level loop (reading R11):
+    level by level, rho^l, then alpha^l, then the messages level l sends
+    (c^l, tau^{l+1}, phi^{l-1}) and, with kappa > 0, the level-(l+1)
+    similarity (Eq. 2.7)."""
+    S = np.array(S, dtype=np.float64)
+    L, n, _ = S.shape
+    A, R, c, phi = st.A.copy(), st.R.copy(), st.c.copy(), st.phi.copy()
+    tau = np.full((L, n), np.inf)
+    rows = np.arange(n)
+    for l in range(L):
+        R[l] = responsibility_update(S[l], A[l], R[l], tau[l], lam)                  # Eq. 2.1
+        P = positive_column_sums(R[l])
+        Rd = np.diagonal(R[l]).copy()
+        A[l] = availability_update(A[l], R[l], rows, c[l], phi[l], Rd, P, lam)        # Eqs. 2.2, 2.3
+        if c_mode == PAPER:
+            c[l] = cluster_preference_update(A[l][None], R[l][None])[0]               # Eq. 2.6
+        if l + 1 < L:
+            tau[l + 1] = c[l] + Rd + P                                               # Eq. 2.4
+            if kappa:
+                S[l + 1] = similarity_level_update(S[l], A[l], R[l], np.diagonal(S[l + 1]), kappa)  # Eq. 2.7
+        if l >= 1:
+            phi[l - 1] = phi_update(np.stack([A[l], A[l]]), np.stack([S[l], S[l]]))[0]  # Eq. 2.5
+    return HAPState(A=A, R=R, c=c, tau=tau, phi=phi, t=st.t + 1)
+
+
 def run(S, iterations: int, lam: float, c_mode: str = PAPER, c0=None,
-        state: HAPState | None = None, callback=None) -> HAPState:
+        state: HAPState | None = None, callback=None, schedule: str = JACOBI,
+        kappa: float = 0.0) -> HAPState:
     """Algorithm 1's iteration loop for a fixed number of iterations."""
     S = np.asarray(S, dtype=np.float64)
     L, n, _ = S.shape
     st = init_state(L, n, c0) if state is None else state
     for _ in range(iterations):
-        st = step(S, st, lam, c_mode)
+        st = step(S, st, lam, c_mode, schedule, kappa)
         if callback is not None:
             callback(st)
     return st
@@ -368,6 +430,19 @@ def adjusted_rand_index(a, b) -> float:
     if max_index == expected:
         return 1.0
     return float((sum_ij - expected) / (max_index - expected))
+
+
+def purity(labels, truth) -> float:
+    """Purity, the extrinsic cluster-quality measure of §4: the fraction of
+    points that carry the most frequent true class of their cluster,
+    (1/N) sum over clusters of max over classes |cluster and class|."""
+    labels = np.asarray(labels).ravel()
+    truth = np.asarray(truth).ravel()
+    total = 0
+    for k in np.unique(labels):
+        _, counts = np.unique(truth[labels == k], return_counts=True)
+        total += int(counts.max())
+    return total / labels.size
 
 
 def message_rel_error(x_test, x_ref) -> float:

@@ -341,20 +341,40 @@ __global__ void fill_alpha_padding_kernel(float* A, int64_t rows, int64_t N, int
     for (int64_t j = N + threadIdx.x; j < ld; j += blockDim.x) A[r * ld + j] = -kInf;
 }
 
-// P_j as the fixed-order sum of the cluster partials; b and tau's column part.
-__global__ void colstats_kernel(const float* __restrict__ partials, int G, int L, int64_t N, int64_t ld,
-                                const float* __restrict__ c, const float* __restrict__ phi,
-                                const float* __restrict__ rdiag, float* __restrict__ b,
-                                float* __restrict__ tpart) {
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (int64_t)L * N) return;
-    const int l = (int)(idx / N);
-    const int64_t j = idx - (int64_t)l * N;
-    const float* pp = partials + (int64_t)l * ld + j;
-    const int64_t gstride = (int64_t)L * ld;
-    float P = 0.f;
-#pragma unroll 8
-    for (int q = 0; q < G; ++q) P = __fadd_rn(P, pp[q * gstride]);
+// Fixed summation order of P_j over the G cluster partials: kChunks
+// contiguous ranges of clusters [q_lo(w), q_lo(w+1)), each summed in cluster
+// order, then the range sums folded in range order.  colstats_kernel and
+// prepare_from_R_kernel both follow it, so P (and everything after it) has
+// the same bits whether it comes from the row pass or from a stored rho.
+constexpr int kChunks = 8;
+HAP_DEV int chunk_lo(int w, int G) { return (int)(((int64_t)w * G) / kChunks); }
+
+// P_j from the cluster partials; b and tau's column part.  Block (32, kChunks):
+// x picks one of 32 consecutive (l, j), y one range of clusters.
+__global__ void __launch_bounds__(32 * kChunks) colstats_kernel(
+    const float* __restrict__ partials, int G, int L, int64_t N, int64_t ld, const float* __restrict__ c,
+    const float* __restrict__ phi, const float* __restrict__ rdiag, float* __restrict__ b,
+    float* __restrict__ tpart) {
+    __shared__ float red[kChunks][32];
+    const int x = threadIdx.x, w = threadIdx.y;
+    const int64_t idx = (int64_t)blockIdx.x * 32 + x;
+    const bool valid = idx < (int64_t)L * N;
+    const int l = valid ? (int)(idx / N) : 0;
+    const int64_t j = valid ? idx - (int64_t)l * N : 0;
+    float acc = 0.f;
+    if (valid) {
+        const float* pp = partials + (int64_t)l * ld + j;
+        const int64_t gstride = (int64_t)L * ld;
+        const int q1 = chunk_lo(w + 1, G);
+#pragma unroll 4
+        for (int q = chunk_lo(w, G); q < q1; ++q) acc = __fadd_rn(acc, pp[q * gstride]);
+    }
+    red[w][x] = acc;
+    __syncthreads();
+    if (w != 0 || !valid) return;
+    float P = red[0][x];
+#pragma unroll
+    for (int u = 1; u < kChunks; ++u) P = __fadd_rn(P, red[u][x]);
     const int64_t v = (int64_t)l * ld + j;
     const float rd = rdiag[v];
     b[v] = __fadd_rn(__fadd_rn(__fadd_rn(c[v], phi[v]), rd), P);
@@ -362,8 +382,9 @@ __global__ void colstats_kernel(const float* __restrict__ partials, int G, int L
 }
 
 // The same column statistics recomputed from a stored rho (after the state is
-// replaced), summing rows in exactly the order the row pass uses: cluster q
-// owns rows q, q+G, q+2G, ... and its partial is summed over q in order.
+// replaced), summing rows in exactly the order the row pass and
+// colstats_kernel use: cluster q owns rows q, q+G, q+2G, ... and its sum is
+// folded into P in the chunked cluster order above.
 __global__ void prepare_from_R_kernel(const float* __restrict__ R, int G, int L, int64_t N, int64_t ld,
                                       float* __restrict__ rdiag, float* __restrict__ tpart) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -372,13 +393,17 @@ __global__ void prepare_from_R_kernel(const float* __restrict__ R, int G, int L,
     const int64_t j = idx - (int64_t)l * N;
     const float* Rl = R + (int64_t)l * N * ld;
     float P = 0.f;
-    for (int q = 0; q < G; ++q) {
-        float acc = 0.f;
-        for (int64_t i = q; i < N; i += G) {
-            const float rv = Rl[i * ld + j];
-            acc = __fadd_rn(acc, (i != j) ? fmaxf(rv, 0.f) : 0.f);
+    for (int w = 0; w < kChunks; ++w) {
+        float part = 0.f;
+        for (int q = chunk_lo(w, G); q < chunk_lo(w + 1, G); ++q) {
+            float acc = 0.f;
+            for (int64_t i = q; i < N; i += G) {
+                const float rv = Rl[i * ld + j];
+                acc = __fadd_rn(acc, (i != j) ? fmaxf(rv, 0.f) : 0.f);
+            }
+            part = __fadd_rn(part, acc);
         }
-        P = __fadd_rn(P, acc);
+        P = w == 0 ? part : __fadd_rn(P, part);
     }
     const float rd = Rl[j * ld + j];
     rdiag[(int64_t)l * ld + j] = rd;
@@ -485,9 +510,8 @@ cudaError_t launch_colstats(const float* partials, int G, int L, int64_t N, int6
                             const float* c, const float* phi, const float* rdiag,
                             float* b, float* tpart, cudaStream_t st) {
     const int64_t total = (int64_t)L * N;
-    const int threads = 256;
-    const unsigned blocks = (unsigned)((total + threads - 1) / threads);
-    colstats_kernel<<<blocks, threads, 0, st>>>(partials, G, L, N, ld, c, phi, rdiag, b, tpart);
+    const unsigned blocks = (unsigned)((total + 31) / 32);
+    colstats_kernel<<<blocks, dim3(32, kChunks), 0, st>>>(partials, G, L, N, ld, c, phi, rdiag, b, tpart);
     return cudaGetLastError();
 }
 

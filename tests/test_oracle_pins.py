@@ -1,7 +1,8 @@
 """Pins of the FP64 reference against facts fixed by the paper and by
 mathematics, independent of the reference's own code:
 
-* a worked example derived by hand from Eqs. 2.1-2.6 (tests/golden),
+* worked examples derived by hand from Eqs. 2.1-2.7 under both level
+  schedules (tests/golden),
 * L = 1 with c fixed at 0 is flat affinity propagation (Frey & Dueck), written
   here separately with literal loops and literal sums,
 * exhaustive search of exemplar sets on tiny inputs (net similarity),
@@ -42,7 +43,7 @@ def test_hand_example(g, name, t):
     S = H.level_similarities(np.array(case.get("S_offdiag", g["S_offdiag"]), float), case["prefs"])
     st = H.init_state(S.shape[0], 3)
     for _ in range(t):
-        st = H.step(S, st, g["lam"], case["c_mode"])
+        st = H.step(S, st, g["lam"], case["c_mode"], case.get("schedule", H.JACOBI), case.get("kappa", 0.0))
     exp = case[f"t{t}"]
     for fld, val in exp.items():
         if fld == "e":
@@ -300,3 +301,52 @@ def test_row_block_column_sums_partition():
     parts = [np.arange(0, 10), np.arange(10, 11), np.arange(11, 37)]
     total = sum(H.row_block_column_sums(R[b], b) for b in parts)
     assert np.allclose(total, H.positive_column_sums(R), rtol=0, atol=1e-12)
+
+
+# ------------------------------------------------ level schedule and Eq. 2.7
+@pytest.mark.parametrize("c_mode", [H.PAPER, H.FIXED])
+def test_one_level_gauss_seidel_equals_data_parallel(c_mode):
+    """With one level there is no inter-level message, and c enters the
+    availability update with the same value under both schedules (the row
+    maximum of the previous iteration's A + R), so A and R agree exactly."""
+    X, _ = W.gmm_points(12, 2, 3, sigma=0.5, seed=7, means="uniform", mean_scale=5.0)
+    S = H.level_similarities(H.neg_sq_euclidean(X), [-8.0])
+    a = H.init_state(1, 12)
+    b = H.init_state(1, 12)
+    for _ in range(25):
+        a = H.step(S, a, 0.5, c_mode, H.JACOBI)
+        b = H.step(S, b, 0.5, c_mode, H.GAUSS_SEIDEL)
+        assert np.array_equal(a.A, b.A) and np.array_equal(a.R, b.R)
+
+
+@pytest.mark.parametrize("schedule,kappa", [(H.GAUSS_SEIDEL, 0.0), (H.JACOBI, 0.25), (H.GAUSS_SEIDEL, 0.25)])
+def test_variants_scale_exactly(schedule, kappa):
+    """Power-of-two scaling of S scales every message bitwise under the
+    sequential schedule and with Eq. 2.7 (kappa times a scaled sum)."""
+    X, _ = W.gmm_points(15, 2, 3, sigma=0.5, seed=3, means="uniform", mean_scale=5.0)
+    S = H.level_similarities(H.neg_sq_euclidean(X), [-6.0, -9.0, -12.0])
+    a = H.run(S, 7, 0.5, H.PAPER, schedule=schedule, kappa=kappa)
+    b = H.run(S * 8.0, 7, 0.5, H.PAPER, schedule=schedule, kappa=kappa)
+    for f in ("A", "R", "c", "tau", "phi"):
+        assert np.array_equal(getattr(a, f) * 8.0, getattr(b, f)), f
+
+
+@pytest.mark.parametrize("schedule,kappa", [(H.GAUSS_SEIDEL, 0.0), (H.JACOBI, 0.25)])
+def test_variants_permutation_equivariant(schedule, kappa):
+    X, _ = W.gmm_points(14, 2, 3, sigma=0.5, seed=9, means="uniform", mean_scale=5.0)
+    S = H.level_similarities(H.neg_sq_euclidean(X), [-6.0, -9.0])
+    perm = np.random.default_rng(2).permutation(14)
+    a = H.run(S, 6, 0.5, H.PAPER, schedule=schedule, kappa=kappa)
+    b = H.run(S[:, perm][:, :, perm], 6, 0.5, H.PAPER, schedule=schedule, kappa=kappa)
+    np.testing.assert_allclose(a.A[:, perm][:, :, perm], b.A, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(a.R[:, perm][:, :, perm], b.R, rtol=0, atol=1e-12)
+
+
+def test_purity():
+    """Purity (§4): hand example and its extreme cases."""
+    assert H.purity([0, 0, 1, 1, 1], ["a", "a", "a", "b", "b"]) == 4 / 5
+    truth = np.array([0, 0, 1, 2, 2, 2])
+    assert H.purity(truth, truth) == 1.0
+    assert H.purity(np.arange(6), truth) == 1.0
+    assert H.purity(np.zeros(6), truth) == 3 / 6
+    assert H.purity(np.array([5, 5, 5, 7, 7, 7]), truth) == (2 + 3) / 6
