@@ -50,8 +50,16 @@ extern "C" {
 #define HAP_C_PAPER 0
 #define HAP_C_FIXED 1
 /* Level schedule.  JACOBI: all levels of an iteration read the state at the
- * start of the iteration (the MR-HAP jobs of §3).                            */
-#define HAP_SCHED_JACOBI 0
+ * start of the iteration (the MR-HAP jobs of §3); neither c nor tau is
+ * updated in the first iteration.  GAUSS_SEIDEL: Algorithm 1's sequential
+ * level loop - for l = 1..L: rho^l (Eq. 2.1 with the tau^l that level l-1
+ * sent in this iteration), then alpha^l (Eqs. 2.2-2.3), then the messages
+ * level l sends: c^l (Eq. 2.6, c_mode PAPER), tau^{l+1} (Eq. 2.4) and
+ * phi^{l-1} (Eq. 2.5) from the new alpha^l and rho^l; updates from the first
+ * iteration on.  Three launches per level and about 32 B moved per message
+ * update instead of 17.                                                       */
+#define HAP_SCHED_JACOBI       0
+#define HAP_SCHED_GAUSS_SEIDEL 1
 /* Storage type of the similarity S.                                          */
 #define HAP_S_F32  0
 #define HAP_S_BF16 1
@@ -90,7 +98,7 @@ extern "C" {
 
 typedef struct hap_options {
     int c_mode;        /* HAP_C_PAPER (default) or HAP_C_FIXED                         */
-    int schedule;      /* HAP_SCHED_JACOBI                                             */
+    int schedule;      /* HAP_SCHED_JACOBI (default) or HAP_SCHED_GAUSS_SEIDEL         */
     int s_dtype;       /* HAP_S_F32 (default) or HAP_S_BF16                            */
     int s_per_level;   /* 0 (default): one N x N similarity shared by all levels, the
                           diagonal of level l being the preferences of level l;
@@ -101,6 +109,14 @@ typedef struct hap_options {
     int elems_per_thread; /* 0 = automatic (8); 4, 8 or 16 columns per thread          */
     int profile;       /* 1: time every row-pass launch with CUDA events               */
     int col_sums;      /* HAP_COLSUM_AUTO (default), HAP_COLSUM_SMEM or HAP_COLSUM_TMEM */
+    float kappa;       /* Eq. 2.7, the optional level-wise similarity update, read
+                          element-wise: s^{l+1}_ij = s^l_ij + kappa (alpha^l_ij +
+                          rho^l_ij) for i != j (the printed index j is both free and
+                          bound), from the start-of-iteration messages; the
+                          diagonal stays the preference of level l+1.  In [0, 1]
+                          (the paper's range); 0 (default) = off.  Needs the JACOBI
+                          schedule and one S shared by all levels; the net
+                          similarity keeps using the given S.                         */
 } hap_options;
 
 typedef struct hap_ctx hap_ctx;
@@ -165,8 +181,9 @@ int hap_build_similarity(hap_ctx* ctx, const float* X, int64_t d, int mode);
  * widened exactly.  Asynchronous. */
 int hap_get_similarity(hap_ctx* ctx, int level, float* S);
 
-/* Runs n iterations of HAP (Eqs. 2.1-2.6 with damping, §3 schedule) on the
- * bound stream.  Asynchronous; n >= 0. */
+/* Runs n iterations of HAP (Eqs. 2.1-2.6 with damping, and Eq. 2.7 when
+ * kappa > 0) under the context's level schedule on the bound stream.
+ * Asynchronous; n >= 0. */
 int hap_iterate(hap_ctx* ctx, int n);
 
 /* Eq. 2.8: e_i^l = argmax_j (alpha_ij^l + rho_ij^l), lowest index on ties,
@@ -187,10 +204,12 @@ int hap_net_similarity(hap_ctx* ctx, double* ns);
  * Asynchronous; does not change the context's state. */
 int hap_get_state(hap_ctx* ctx, float* A, float* R, float* vecs, int64_t* iter);
 
-/* Replaces the messages (A, R device [L][N][N]; vecs device [3][L][N] whose c
- * part is used, tau and phi being recomputed by the next iteration) and the
- * completed-iteration count, e.g. to resume from a checkpoint.  The next
- * hap_iterate continues exactly as an uninterrupted run would. */
+/* Replaces the messages (A, R device [L][N][N]; vecs device [3][L][N]: c, tau,
+ * phi) and the completed-iteration count, e.g. to resume from a checkpoint.
+ * JACOBI uses the c part (tau and phi are recomputed by the next iteration);
+ * GAUSS_SEIDEL uses c and phi (phi^l carries the top-down message of the
+ * previous iteration).  The next hap_iterate continues exactly as an
+ * uninterrupted run would. */
 int hap_set_state(hap_ctx* ctx, const float* A, const float* R, const float* vecs, int64_t iter);
 
 /* Waits for the bound stream and checks the device status word. */

@@ -196,7 +196,9 @@ Layout make_layout(int64_t N, int L, const hap_options& o, const LaunchShape& sh
 
 int check_opts(const hap_options& o) {
     if (o.c_mode != HAP_C_PAPER && o.c_mode != HAP_C_FIXED) return HAP_EINVAL;
-    if (o.schedule != HAP_SCHED_JACOBI) return HAP_EINVAL;
+    if (o.schedule != HAP_SCHED_JACOBI && o.schedule != HAP_SCHED_GAUSS_SEIDEL) return HAP_EINVAL;
+    if (!(o.kappa >= 0.f && o.kappa <= 1.f)) return HAP_EINVAL;
+    if (o.kappa != 0.f && (o.schedule != HAP_SCHED_JACOBI || o.s_per_level)) return HAP_EUNSUPPORTED;
     if (o.s_dtype != HAP_S_F32 && o.s_dtype != HAP_S_BF16) return HAP_EINVAL;
     if (o.s_per_level != 0 && o.s_per_level != 1) return HAP_EINVAL;
     return HAP_OK;
@@ -449,6 +451,72 @@ int hap_get_similarity(hap_ctx* h, int level, float* S) {
     return HAP_OK;
 }
 
+// Algorithm 1's sequential level loop: per level, the fused row pass on that
+// level alone (alpha final, tau^l as the previous level sent it), the column
+// statistics (b^l; rho_jj + P_j into tpart's level-l row) and the availability
+// step that also sends c^l, phi^{l-1} and tau^{l+1}.
+static int iterate_gauss_seidel(hap_ctx* h, RowPassArgs a, int n) {
+    const int s_bf16 = h->opt.s_dtype == HAP_S_BF16;
+    const int64_t N = h->N, ld = h->ld, L = h->L;
+    const int64_t mat = N * ld;
+    for (int it = 0; it < n; ++it) {
+        for (int64_t l = 0; l < L; ++l) {
+            RowPassArgs v = a;
+            v.A = h->A + l * mat;
+            v.R = h->R + l * mat;
+            v.S = static_cast<char*>(h->S) + (size_t)(l * h->s_level_stride) * (s_bf16 ? 2 : 4);
+            v.s_level_stride = 0;
+            v.L = 1;
+            v.pref = h->pref + l * ld;
+            v.c = h->c + l * ld;
+            v.tau = h->tau + l * ld;
+            v.phi = h->phi + l * ld;
+            v.tpart = h->tpart + l * ld;
+            v.b = h->b + l * ld;
+            v.rdiag = h->rdiag + l * ld;
+            v.pending = 0;
+            v.update_c = 0;
+            v.use_tau = 0;
+            v.tau_in = l > 0 ? h->tau + l * ld : nullptr;
+            v.kappa = 0.f;
+            cudaEvent_t e0 = nullptr, e1 = nullptr;
+            if (h->opt.profile) {
+                CU(cudaEventCreate(&e0));
+                CU(cudaEventCreate(&e1));
+                CU(cudaEventRecord(e0, h->stream));
+            }
+            CU(launch_rowpass(v, h->sh, s_bf16, h->stream));
+            if (h->opt.profile) {
+                CU(cudaEventRecord(e1, h->stream));
+                h->ev.push_back(e0);
+                h->ev.push_back(e1);
+            }
+            CU(launch_colstats(h->partials, h->sh.G, 1, N, ld, v.c, v.phi, v.rdiag, h->b + l * ld, nullptr, h->stream,
+                               h->tpart + l * ld));
+            GsArgs g;
+            g.A = v.A;
+            g.R = v.R;
+            g.S = v.S;
+            g.b = v.b;
+            g.pref = v.pref;
+            g.c = v.c;
+            g.tp = h->tpart + l * ld;
+            g.phi_out = l > 0 ? h->phi + (l - 1) * ld : nullptr;
+            g.tau_next = l + 1 < L ? h->tau + (l + 1) * ld : nullptr;
+            g.N = N;
+            g.ld = ld;
+            g.lam = a.lam;
+            g.oml = a.oml;
+            g.update_c = h->opt.c_mode == HAP_C_PAPER ? 1 : 0;
+            CU(launch_gs_availability(g, s_bf16, h->stream));
+            h->launches += 3;
+        }
+        h->pending = false;
+        h->iter += 1;
+    }
+    return HAP_OK;
+}
+
 int hap_iterate(hap_ctx* h, int n) {
     if (!h || n < 0) return HAP_EINVAL;
     RowPassArgs a;
@@ -470,7 +538,9 @@ int hap_iterate(hap_ctx* h, int n) {
     a.status = h->status;
     a.lam = h->lam;
     a.oml = 1.0f - h->lam;
+    a.kappa = h->opt.kappa;
     const int s_bf16 = h->opt.s_dtype == HAP_S_BF16;
+    if (h->opt.schedule == HAP_SCHED_GAUSS_SEIDEL) return iterate_gauss_seidel(h, a, n);
     for (int it = 0; it < n; ++it) {
         const int64_t t = h->iter + 1;
         a.pending = h->pending ? 1 : 0;

@@ -559,6 +559,7 @@ int hap_batch_create(int B, const int64_t* N, const int* L, float damping, const
     hap_default_options(&o);
     if (opt) o = *opt;
     if (o.c_mode != HAP_C_PAPER && o.c_mode != HAP_C_FIXED) return HAP_EINVAL;
+    if (o.schedule != HAP_SCHED_JACOBI || o.kappa != 0.f) return HAP_EUNSUPPORTED;
     hap_batch* h = new (std::nothrow) hap_batch();
     if (!h) return HAP_ENOMEM;
     h->B = B;

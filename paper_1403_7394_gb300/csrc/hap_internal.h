@@ -35,6 +35,8 @@ struct RowPassArgs {
     int pending;           // alpha of the previous iteration still to be applied
     int update_c;          // apply Eq. 2.6 this iteration
     int use_tau;           // tau from Eq. 2.4 this iteration (else +inf)
+    const float* tau_in = nullptr;  // [L][ld] tau given per row (sequential level schedule), else computed
+    float kappa = 0.f;     // Eq. 2.7 level-wise similarity update (0 = off; shared S only)
 };
 
 struct LaunchShape {
@@ -53,9 +55,30 @@ size_t rowpass_smem_bytes(const LaunchShape& sh, int L, int s_bf16);
 int rowpass_tmem_columns(const LaunchShape& sh, int L);  // 0 for shared-memory sums
 cudaError_t launch_fill_alpha_padding(float* A, int64_t rows, int64_t N, int64_t ld, cudaStream_t st);
 
+// tp_level (may be null) receives rho_jj + P_j at each level's own index.
 cudaError_t launch_colstats(const float* partials, int G, int L, int64_t N, int64_t ld,
                             const float* c, const float* phi, const float* rdiag,
-                            float* b, float* tpart, cudaStream_t st);
+                            float* b, float* tpart, cudaStream_t st, float* tp_level = nullptr);
+
+// One level of the sequential (Gauss-Seidel) schedule after its rho pass and
+// column statistics: alpha^l (Eqs. 2.2-2.3, damped), then c^l (Eq. 2.6, when
+// update_c), phi^{l-1} (Eq. 2.5, when phi_out) and tau^{l+1} = c^l + tp
+// (Eq. 2.4, when tau_next).  A, R, S point at level l; vectors at level l.
+struct GsArgs {
+    float* A;
+    const float* R;
+    const void* S;
+    const float* b;
+    const float* pref;
+    float* c;
+    const float* tp;
+    float* phi_out;
+    float* tau_next;
+    int64_t N, ld;
+    float lam, oml;
+    int update_c;
+};
+cudaError_t launch_gs_availability(const GsArgs& a, int s_bf16, cudaStream_t st);
 cudaError_t launch_prepare_from_R(const float* R, int G, int L, int64_t N, int64_t ld,
                                   float* rdiag, float* tpart, cudaStream_t st);
 

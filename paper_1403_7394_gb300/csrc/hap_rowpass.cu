@@ -77,6 +77,7 @@ __global__ void __launch_bounds__(MAXT, 1) rowpass_kernel(const RowPassArgs p) {
     const float lam = p.lam, oml = p.oml;
     const bool pending = p.pending != 0;
     const bool s_each_level = p.s_level_stride != 0;
+    const bool kap = p.kappa != 0.f;  // shared S only (checked on the host)
     const ST* Sb = reinterpret_cast<const ST*>(p.S);
 
     // ---- shared memory carve-up ------------------------------------------------
@@ -155,7 +156,7 @@ __global__ void __launch_bounds__(MAXT, 1) rowpass_kernel(const RowPassArgs p) {
     // Per-column b of the pending availability update and per-row scalars
     // (preference, fixed c, tau's column part), loaded one step ahead.
     float4 nb[K];
-    float npref = 0.f, nc = 0.f, ntp = 0.f;
+    float npref = 0.f, nc = 0.f, ntp = 0.f, ntau = kInf;
     auto prefetch = [&](int prow, int pl) {
         const int64_t pv = (int64_t)pl * ld;
 #pragma unroll
@@ -164,6 +165,7 @@ __global__ void __launch_bounds__(MAXT, 1) rowpass_kernel(const RowPassArgs p) {
         npref = __ldg(p.pref + pv + prow);
         nc = p.update_c ? 0.f : p.c[pv + prow];
         ntp = (p.use_tau && pl > 0) ? __ldg(p.tpart + pv + prow) : 0.f;
+        if (p.tau_in) ntau = p.tau_in[pv + prow];
     };
     if (nsteps > 0) prefetch(row, 0);
 
@@ -181,7 +183,7 @@ __global__ void __launch_bounds__(MAXT, 1) rowpass_kernel(const RowPassArgs p) {
         float4 bcur[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) bcur[k] = nb[k];
-        const float pref_i = npref, c_fixed = nc, tpart_i = ntp;
+        const float pref_i = npref, c_fixed = nc, tpart_i = ntp, tau_given = ntau;
         {
             int prow = row, pl = l + 1;
             if (pl == L) { pl = 0; prow += (int)G; }
@@ -214,6 +216,13 @@ __global__ void __launch_bounds__(MAXT, 1) rowpass_kernel(const RowPassArgs p) {
             if ((unsigned)dd < 4u) {  // this float4 holds the diagonal element
                 f4_set(s4, dd, pref_i);
                 if (pending) f4_set(an, dd, damp(f4_get(a4, dd), avail_target(f4_get(b4, dd), f4_get(r4, dd), true), lam, oml));
+            }
+            if (kap) {  // Eq. 2.7: the next level's similarity from this level's start-of-iteration messages
+                const float kp = p.kappa;
+                srow[k].x = __fadd_rn(srow[k].x, __fmul_rn(kp, __fadd_rn(an.x, r4.x)));
+                srow[k].y = __fadd_rn(srow[k].y, __fmul_rn(kp, __fadd_rn(an.y, r4.y)));
+                srow[k].z = __fadd_rn(srow[k].z, __fmul_rn(kp, __fadd_rn(an.z, r4.z)));
+                srow[k].w = __fadd_rn(srow[k].w, __fmul_rn(kp, __fadd_rn(an.w, r4.w)));
             }
             if (pending && ok[k] && !bad) st_stream(p.A + off + col[k], an);
             top2_push(__fadd_rn(an.x, s4.x), col[k] + 0, m1, k1, m2);
@@ -253,7 +262,7 @@ __global__ void __launch_bounds__(MAXT, 1) rowpass_kernel(const RowPassArgs p) {
 
         // ---- inter-level messages of (i, l): Eqs. 2.4-2.6 --------------------
         const float cval = p.update_c ? cm : c_fixed;
-        const float tauv = (p.use_tau && l > 0) ? __fadd_rn(c_prev, tpart_i) : kInf;
+        const float tauv = p.tau_in ? tau_given : (p.use_tau && l > 0) ? __fadd_rn(c_prev, tpart_i) : kInf;
         c_prev = cval;
         if (rank == 0 && tid == 0 && !bad) {
             if (p.update_c) p.c[voff + row] = cval;
@@ -354,7 +363,7 @@ HAP_DEV int chunk_lo(int w, int G) { return (int)(((int64_t)w * G) / kChunks); }
 __global__ void __launch_bounds__(32 * kChunks) colstats_kernel(
     const float* __restrict__ partials, int G, int L, int64_t N, int64_t ld, const float* __restrict__ c,
     const float* __restrict__ phi, const float* __restrict__ rdiag, float* __restrict__ b,
-    float* __restrict__ tpart) {
+    float* __restrict__ tpart, float* __restrict__ tp_level) {
     __shared__ float red[kChunks][32];
     const int x = threadIdx.x, w = threadIdx.y;
     const int64_t idx = (int64_t)blockIdx.x * 32 + x;
@@ -379,6 +388,7 @@ __global__ void __launch_bounds__(32 * kChunks) colstats_kernel(
     const float rd = rdiag[v];
     b[v] = __fadd_rn(__fadd_rn(__fadd_rn(c[v], phi[v]), rd), P);
     if (l + 1 < L) tpart[v + ld] = __fadd_rn(rd, P);
+    if (tp_level) tp_level[v] = __fadd_rn(rd, P);
 }
 
 // The same column statistics recomputed from a stored rho (after the state is
@@ -508,10 +518,10 @@ cudaError_t rowpass_max_clusters(const LaunchShape& sh, int L, int s_bf16, int* 
 
 cudaError_t launch_colstats(const float* partials, int G, int L, int64_t N, int64_t ld,
                             const float* c, const float* phi, const float* rdiag,
-                            float* b, float* tpart, cudaStream_t st) {
+                            float* b, float* tpart, cudaStream_t st, float* tp_level) {
     const int64_t total = (int64_t)L * N;
     const unsigned blocks = (unsigned)((total + 31) / 32);
-    colstats_kernel<<<blocks, dim3(32, kChunks), 0, st>>>(partials, G, L, N, ld, c, phi, rdiag, b, tpart);
+    colstats_kernel<<<blocks, dim3(32, kChunks), 0, st>>>(partials, G, L, N, ld, c, phi, rdiag, b, tpart, tp_level);
     return cudaGetLastError();
 }
 

@@ -23,13 +23,15 @@ Q_BLOCK_THREADS, Q_CLUSTER_SIZE, Q_GRID_CLUSTERS, Q_LD, Q_ITER, Q_ELEMS_PER_THRE
 Q_BATCH_ITEMS_PER_CTA = 8
 Q_COL_SUMS, Q_STAGES = 9, 10
 COL_SUMS = {"auto": 0, "smem": 1, "tmem": 2}
+SCHEDULES = {"jacobi": 0, "gauss_seidel": 1}
 
 
 class HapOptions(ctypes.Structure):
     _fields_ = [("c_mode", ctypes.c_int), ("schedule", ctypes.c_int), ("s_dtype", ctypes.c_int),
                 ("s_per_level", ctypes.c_int), ("block_threads", ctypes.c_int),
                 ("cluster_size", ctypes.c_int), ("grid_clusters", ctypes.c_int),
-                ("elems_per_thread", ctypes.c_int), ("profile", ctypes.c_int), ("col_sums", ctypes.c_int)]
+                ("elems_per_thread", ctypes.c_int), ("profile", ctypes.c_int), ("col_sums", ctypes.c_int),
+                ("kappa", ctypes.c_float)]
 
 
 def _load():
@@ -124,7 +126,8 @@ def _ptr(t: torch.Tensor | None):
 
 
 def options(c_mode="paper", s_dtype="f32", s_per_level=False, block_threads=0, cluster_size=0,
-            grid_clusters=0, elems_per_thread=0, profile=False, col_sums="auto") -> HapOptions:
+            grid_clusters=0, elems_per_thread=0, profile=False, col_sums="auto", schedule="jacobi",
+            kappa=0.0) -> HapOptions:
     o = HapOptions()
     lib.hap_default_options(ctypes.byref(o))
     o.c_mode = C_MODES[c_mode]
@@ -136,6 +139,8 @@ def options(c_mode="paper", s_dtype="f32", s_per_level=False, block_threads=0, c
     o.elems_per_thread = int(elems_per_thread)
     o.profile = int(bool(profile))
     o.col_sums = COL_SUMS[col_sums]
+    o.schedule = SCHEDULES[schedule]
+    o.kappa = float(kappa)
     return o
 
 
@@ -319,13 +324,13 @@ class HAPBatch:
     persistent launch per iteration (hap_batch_* in the C ABI)."""
 
     def __init__(self, N, L, damping: float = 0.5, device="cuda", stream: torch.cuda.Stream | None = None,
-                 c_mode="paper", s_dtype="f32"):
+                 c_mode="paper", s_dtype="f32", **opt):
         import numpy as np
         self.N = [int(x) for x in N]
         self.L = [int(x) for x in L]
         self.B = len(self.N)
         self.device = torch.device(device)
-        o = options(c_mode=c_mode, s_dtype=s_dtype)
+        o = options(c_mode=c_mode, s_dtype=s_dtype, **opt)
         n_arr = np.ascontiguousarray(self.N, dtype=np.int64)
         l_arr = np.ascontiguousarray(self.L, dtype=np.int32)
         with torch.cuda.device(self.device):
