@@ -5,15 +5,21 @@
 // Work items are (instance, band) pairs: band g of an instance owns the row
 // blocks g, g + G, g + 2G, ... (a block = `rps` consecutive rows, which are
 // contiguous in memory, so one TMA bulk copy per tensor moves a whole block).
-// A 512-thread CTA is split into rps row groups of tg = 512 / rps threads;
-// each group holds one row of the block (tg * 8 >= ld), so instances with
-// small N process up to 16 rows per step.  Each CTA walks a list of items
-// assigned by a host-side longest-processing-time scheduler; the TMA ring
-// runs ahead across item boundaries.  Per-group column sums of max(0, rho)
-// stay in shared memory and are combined in group order into the band's
-// partials; a batched kernel sums bands in order (fixed-order reductions,
-// bitwise reproducible for a fixed schedule).  The equations are those of
-// the single-instance row pass (Eqs. 2.1-2.6 with damping, §3 schedule).
+// A 512-thread CTA (16 warps) is split into rps row groups of g whole warps,
+// g = ceil(ld / (32 * 4K)) with 4K columns per thread, rps = floor(16 / g);
+// each group holds one row of the block, so instances with small N process
+// up to 16 rows per step and every instance keeps at least 15 of 16 warps
+// busy for g <= 5.  Groups synchronise only among themselves (a named barrier
+// per group); a stage of the TMA ring is refilled once every warp has
+// released it (an "empty" mbarrier per stage), so groups never wait for a
+// CTA-wide barrier.  Each thread keeps the running column sums of max(0, rho)
+// of its columns for all levels of the current item in tensor memory (TMEM),
+// so shared memory holds only the ring; at the end of an item every group
+// writes its sums as one partial row (band * rps + group) and the batched
+// column-statistics kernel sums an instance's partial rows in order
+// (fixed-order reductions, bitwise reproducible for a fixed schedule).  The
+// equations are those of the single-instance row pass (Eqs. 2.1-2.6 with
+// damping, §3 schedule).
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -30,10 +36,13 @@
 namespace hap {
 namespace {
 
-constexpr int kBT = 512;       // threads per CTA
-constexpr int kBK = 2;         // float4 groups per thread and row (8 columns)
-constexpr int kBStages = 3;    // TMA ring depth
-constexpr int kBMaxLd = kBT * 4 * kBK;  // 4096: longest row one CTA holds
+constexpr int kBT = 512;            // threads per CTA
+constexpr int kBW = kBT / 32;       // warps per CTA
+constexpr int kBMaxLd = 4096;       // longest row the batched path takes
+// 16 columns per thread when every instance has at most 8 levels (TMEM holds
+// 4 warp slots x L x 16 columns <= 512), else 8 columns per thread.
+__host__ __device__ constexpr int b_stages(int K) { return K == 4 ? 2 : 4; }
+__host__ __device__ constexpr int b_stage_elems(int K) { return kBT * 4 * K; }
 
 struct BInst {
     float* A;
@@ -46,8 +55,8 @@ struct BInst {
     float* tpart;
     float* b;
     float* rdiag;
-    float* partials;  // [G][L][ld]
-    int N, L, ld, rps, tg, G;
+    float* partials;  // [G * rps][L][ld]: one row per (band, row group)
+    int N, L, ld, rps, g, G;
 };
 struct BItem {
     int inst, band, nsteps;
@@ -61,10 +70,26 @@ struct BatchArgs {
     int pending, update_c, use_tau;
 };
 
-size_t batched_smem_bytes(int maxL, int s_elem) {
-    const size_t W = (size_t)kBT * 4 * kBK;
-    const size_t a = W * 4, sb = W * s_elem;
-    return kBStages * (2 * a + sb) + (size_t)maxL * W * 4 + 2 * 32 * 16 + kBStages * 8;
+size_t batched_smem_bytes(int K, int s_elem) {
+    const size_t E = (size_t)b_stage_elems(K);
+    const size_t stage = 2 * E * 4 + E * s_elem;
+    const size_t bytes = b_stages(K) * stage + 2 * kBW * 16 + 2 * b_stages(K) * 8 + 8;
+    // more than half an SM's shared memory: one CTA per SM, so its TMEM
+    // allocation never waits for another CTA
+    return std::max<size_t>(bytes, 116 * 1024);
+}
+
+int batched_tmem_cols(int K, int maxL) {
+    int n = 32;
+    while (n < 4 * maxL * 4 * K) n *= 2;
+    return n;
+}
+
+HAP_DEV void named_barrier(int id, int threads) {
+    asm volatile("bar.sync %0, %1;" :: "r"(id), "r"(threads) : "memory");
+}
+HAP_DEV void mbar_arrive_local(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(bar) : "memory");
 }
 
 template <typename ST>
@@ -76,26 +101,36 @@ HAP_DEV float4 bload_s<__nv_bfloat16>(const __nv_bfloat16* p) {
     return SVec<__nv_bfloat16>::to_f4(*reinterpret_cast<const uint2*>(p));
 }
 
-template <typename ST>
-__global__ void __launch_bounds__(kBT, 1) rowpass_batched_kernel(const BatchArgs p, int maxL) {
+template <typename ST, int K>
+__global__ void __launch_bounds__(kBT, 1) rowpass_batched_kernel(const BatchArgs p, int maxL, int tcols) {
+    constexpr int NST = b_stages(K);
+    constexpr int E = b_stage_elems(K);
+    constexpr uint32_t A_BYTES = E * 4, S_BYTES = E * sizeof(ST);
+    constexpr uint32_t STAGE = 2 * A_BYTES + S_BYTES;
     extern __shared__ __align__(128) unsigned char sm[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    constexpr int W = kBT * 4 * kBK;
-    constexpr uint32_t A_BYTES = W * 4, S_BYTES = W * sizeof(ST);
-    constexpr uint32_t STAGE = 2 * A_BYTES + S_BYTES;
-    float4* acc = reinterpret_cast<float4*>(sm + kBStages * STAGE);  // [maxL][K][kBT] (row groups side by side)
-    float4* red = acc + (size_t)maxL * kBK * kBT;                      // [2][16]
-    const uint32_t bar0 = smem_addr(red + 2 * 16);
+    float4* red = reinterpret_cast<float4*>(sm + NST * STAGE);  // [2][kBW] warp summaries
+    const uint32_t full0 = smem_addr(red + 2 * kBW);            // full[NST] (TMA landed)
+    const uint32_t empty0 = full0 + 8 * NST;                    // empty[NST] (every warp released)
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(red + 2 * kBW) + 4 * NST;
     const uint32_t sm0 = smem_addr(sm);
     const float lam = p.lam, oml = p.oml;
     const bool pending = p.pending != 0;
 
     const int it0 = p.cta_begin[blockIdx.x], it1 = p.cta_begin[blockIdx.x + 1];
     if (tid == 0) {
-        for (int q = 0; q < kBStages; ++q) mbar_init(bar0 + 8 * q, 1);
+        for (int q = 0; q < NST; ++q) {
+            mbar_init(full0 + 8 * q, 1);
+            mbar_init(empty0 + 8 * q, kBW);
+        }
         fence_mbarrier_init();
     }
+    if (warp == 0) tmem_alloc(smem_addr(tslot), (uint32_t)tcols);
+    tc_fence_before();
     __syncthreads();
+    tc_fence_after();
+    // this thread's sums of level l: lane 32*(warp%4)+lane, columns tq + l*4K ..
+    const uint32_t tq = *tslot + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((warp >> 2) * maxL * 4 * K);
     bool bad = false;
 
     // ---- producer (thread 0): a cursor over (item, step) ahead of the consumers
@@ -108,8 +143,10 @@ __global__ void __launch_bounds__(kBT, 1) rowpass_batched_kernel(const BatchArgs
         const int m = pq / in.L, l = pq % in.L;
         const int i0 = (itm.band + m * in.G) * in.rps;
         const int nrows = min(in.rps, in.N - i0);
-        const int st = issued % kBStages;
-        const uint32_t bar = bar0 + 8 * st, dst = sm0 + (uint32_t)st * STAGE;
+        const int st = issued % NST;
+        // the stage's previous contents (step issued - NST) must be released by every warp
+        if (issued >= NST && !bad) bad = !mbar_wait(empty0 + 8 * st, (uint32_t)((issued / NST - 1) & 1), p.status);
+        const uint32_t bar = full0 + 8 * st, dst = sm0 + (uint32_t)st * STAGE;
         const bool load_s = l == 0;
         const uint32_t n = (uint32_t)nrows * (uint32_t)in.ld;
         mbar_arrive_expect_tx(bar, n * (8u + (load_s ? (uint32_t)sizeof(ST) : 0u)));
@@ -122,38 +159,47 @@ __global__ void __launch_bounds__(kBT, 1) rowpass_batched_kernel(const BatchArgs
         return true;
     };
     if (tid == 0)
-        for (int q = 0; q < kBStages; ++q)
+        for (int q = 0; q < NST; ++q)
             if (!issue_next()) break;
 
     int step = 0;  // consumer step counter of this CTA (ring position)
     for (int it = it0; it < it1; ++it) {
         const BItem itm = p.items[it];
         const BInst in = p.inst[itm.inst];
-        const int tg = in.tg, r = tid / tg, t = tid - r * tg;
+        const int g = in.g, tg = 32 * g, rps = in.rps;
+        const int r = warp / g;
+        const bool active = r < rps;  // warps beyond rps * g only keep the ring in step
+        const int t = (warp - r * g) * 32 + lane;
         const int L = in.L, N = in.N;
         const int64_t ld = in.ld;
-        int col[kBK];
-        bool ok[kBK];
+        int col[K];
+        bool ok[K];
 #pragma unroll
-        for (int k = 0; k < kBK; ++k) {
+        for (int k = 0; k < K; ++k) {
             col[k] = 4 * (k * tg + t);
-            ok[k] = col[k] < (int)ld;
+            ok[k] = active && col[k] < (int)ld;
         }
-        for (int q = tid; q < L * kBK * kBT; q += kBT) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-        float4 srow[kBK];
+        {
+            float z[4 * K];
 #pragma unroll
-        for (int k = 0; k < kBK; ++k) srow[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int q = 0; q < 4 * K; ++q) z[q] = 0.f;
+            __syncwarp();
+            for (int ll = 0; ll < L; ++ll) tmem_store<4 * K>(tq + (uint32_t)(ll * 4 * K), z);
+        }
+        float4 srow[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) srow[k] = make_float4(0.f, 0.f, 0.f, 0.f);
         float c_prev = 0.f;
         // per-column b and per-row scalars of the next step, loaded ahead
-        float4 nb[kBK];
+        float4 nb[K];
         float npref = 0.f, nc = 0.f, ntp = 0.f;
         auto prefetch = [&](int q) {
             const int pm = q / L, pl = q % L;
-            const int prow = (itm.band + pm * in.G) * in.rps + r;
-            const bool prv = prow < N;
+            const int prow = (itm.band + pm * in.G) * rps + r;
+            const bool prv = active && prow < N;
             const int64_t pv = (int64_t)pl * ld;
 #pragma unroll
-            for (int k = 0; k < kBK; ++k)
+            for (int k = 0; k < K; ++k)
                 nb[k] = (pending && ok[k] && prv) ? __ldg(reinterpret_cast<const float4*>(in.b + pv + col[k])) : f4_splat(0.f);
             npref = prv ? __ldg(in.pref + pv + prow) : 0.f;
             nc = (!p.update_c && prv) ? in.c[pv + prow] : 0.f;
@@ -162,28 +208,30 @@ __global__ void __launch_bounds__(kBT, 1) rowpass_batched_kernel(const BatchArgs
         if (itm.nsteps > 0) prefetch(0);
         for (int q = 0; q < itm.nsteps; ++q, ++step) {
             const int m = q / L, l = q % L;
-            const int i0 = (itm.band + m * in.G) * in.rps;
+            const int i0 = (itm.band + m * in.G) * rps;
             const int row = i0 + r;
-            const bool rv = row < N;  // this group's row exists
-            float4 bcur[kBK];
+            const bool rv = active && row < N;  // this group's row exists
+            float4 bcur[K];
 #pragma unroll
-            for (int k = 0; k < kBK; ++k) bcur[k] = nb[k];
+            for (int k = 0; k < K; ++k) bcur[k] = nb[k];
             const float pref_i = npref, c_fixed = nc, tpart_i = ntp;
             if (q + 1 < itm.nsteps) prefetch(q + 1);
-            const int st = step % kBStages;
+            const int st = step % NST;
             const unsigned char* base = sm + (size_t)st * STAGE;
-            const float* sA = reinterpret_cast<const float*>(base) + (size_t)r * ld;
-            const float* sR = reinterpret_cast<const float*>(base + A_BYTES) + (size_t)r * ld;
-            const ST* sS = reinterpret_cast<const ST*>(base + 2 * A_BYTES) + (size_t)r * ld;
-            if (!bad) bad = !mbar_wait(bar0 + 8 * st, (uint32_t)(step / kBStages) & 1u, p.status);
+            const int rr0 = active ? r : 0;
+            const float* sA = reinterpret_cast<const float*>(base) + (size_t)rr0 * ld;
+            const float* sR = reinterpret_cast<const float*>(base + A_BYTES) + (size_t)rr0 * ld;
+            const ST* sS = reinterpret_cast<const ST*>(base + 2 * A_BYTES) + (size_t)rr0 * ld;
+            if (!bad) bad = !mbar_wait(full0 + 8 * st, (uint32_t)(step / NST) & 1u, p.status);
             const int64_t voff = (int64_t)l * ld;
             const int64_t off = ((int64_t)l * N + row) * ld;
 
+            // ---- pass 1: pending availability (Eqs. 2.2/2.3), row statistics ------
             float m1 = -kInf, m2 = -kInf, cm = -kInf;
             int k1 = 0x7fffffff;
-            float4 rr[kBK], ss[kBK];
+            float4 rr[K], ss[K];
 #pragma unroll
-            for (int k = 0; k < kBK; ++k) {
+            for (int k = 0; k < K; ++k) {
                 float4 a4 = f4_splat(-kInf), r4 = f4_splat(0.f), s4 = f4_splat(0.f);
                 const bool live = ok[k] && rv;
                 if (live) {
@@ -215,20 +263,25 @@ __global__ void __launch_bounds__(kBT, 1) rowpass_batched_kernel(const BatchArgs
                 rr[k] = r4;
                 ss[k] = s4;
             }
+            // this warp has read stage st
+            __syncwarp();
+            if (lane == 0) mbar_arrive_local(empty0 + 8 * st);
             // ---- exact reduction within the row group ----------------------------
             warp_top2(m1, k1, m2, cm);
             const int par = step & 1;
-            if (lane == 0) red[par * 16 + warp] = make_float4(m1, m2, cm, __int_as_float(k1));
-            __syncthreads();
-            if (tid == 0 && issued < step + 1 + kBStages) issue_next();  // stage `st` is free
-            const int gw = tg >> 5, w0 = (r * tg) >> 5;
+            if (lane == 0) red[par * kBW + warp] = make_float4(m1, m2, cm, __int_as_float(k1));
+            if (g == 1) __syncwarp();
+            else if (active) named_barrier(1 + r, tg);
             m1 = m2 = cm = -kInf;
             k1 = 0x7fffffff;
-            for (int w = 0; w < gw; ++w) {
-                const float4 v = red[par * 16 + w0 + w];
-                top2_merge(m1, k1, m2, v.x, __float_as_int(v.w), v.y);
-                cm = fmaxf(cm, v.z);
+            if (active) {
+                for (int w = 0; w < g; ++w) {
+                    const float4 v = red[par * kBW + r * g + w];
+                    top2_merge(m1, k1, m2, v.x, __float_as_int(v.w), v.y);
+                    cm = fmaxf(cm, v.z);
+                }
             }
+            if (tid == 0) issue_next();  // refills stage st once every warp released it
             // ---- inter-level messages (Eqs. 2.4-2.6) ---------------------------
             const float cval = p.update_c ? cm : c_fixed;
             const float tauv = (p.use_tau && l > 0 && rv) ? __fadd_rn(c_prev, tpart_i) : kInf;
@@ -240,8 +293,9 @@ __global__ void __launch_bounds__(kBT, 1) rowpass_batched_kernel(const BatchArgs
             }
             // ---- responsibilities (Eq. 2.1) and column sums ------------------------
             const float mm1 = fminf(tauv, -m1), mm2 = fminf(tauv, -m2);
+            float addv[4 * K];
 #pragma unroll
-            for (int k = 0; k < kBK; ++k) {
+            for (int k = 0; k < K; ++k) {
                 const float4 r4 = rr[k], s4 = ss[k];
                 float4 rn;
                 rn.x = damp(r4.x, __fadd_rn(s4.x, mm1), lam, oml);
@@ -251,42 +305,53 @@ __global__ void __launch_bounds__(kBT, 1) rowpass_batched_kernel(const BatchArgs
                 const int dk = k1 - col[k];
                 if ((unsigned)dk < 4u) f4_set(rn, dk, damp(f4_get(r4, dk), __fadd_rn(f4_get(s4, dk), mm2), lam, oml));
                 float4 add = make_float4(fmaxf(rn.x, 0.f), fmaxf(rn.y, 0.f), fmaxf(rn.z, 0.f), fmaxf(rn.w, 0.f));
-                if (!rv) add = f4_splat(0.f);
+                if (!(ok[k] && rv)) add = f4_splat(0.f);
                 const int dd = row - col[k];
                 if ((unsigned)dd < 4u) {
                     f4_set(add, dd, 0.f);
-                    if (!bad) in.rdiag[voff + row] = f4_get(rn, dd);
+                    if (rv && !bad) in.rdiag[voff + row] = f4_get(rn, dd);
                 }
                 if (ok[k] && rv && !bad) st_stream(in.R + off + col[k], rn);
-                float4& a = acc[(l * kBK + k) * kBT + tid];
-                a.x = __fadd_rn(a.x, add.x);
-                a.y = __fadd_rn(a.y, add.y);
-                a.z = __fadd_rn(a.z, add.z);
-                a.w = __fadd_rn(a.w, add.w);
+                addv[4 * k + 0] = add.x;
+                addv[4 * k + 1] = add.y;
+                addv[4 * k + 2] = add.z;
+                addv[4 * k + 3] = add.w;
+            }
+            __syncwarp();  // tcgen05.ld / st are warp-collective
+            float cur[4 * K];
+            const uint32_t ta = tq + (uint32_t)(l * 4 * K);
+            tmem_load<4 * K>(ta, cur);
+#pragma unroll
+            for (int q2 = 0; q2 < 4 * K; ++q2) cur[q2] = __fadd_rn(cur[q2], addv[q2]);
+            tmem_store<4 * K>(ta, cur);
+        }
+        // ---- this item's sums: partial row (band * rps + group) -------------------
+        for (int ll = 0; ll < L; ++ll) {
+            float cur[4 * K];
+            __syncwarp();
+            tmem_load<4 * K>(tq + (uint32_t)(ll * 4 * K), cur);
+            if (active) {
+                float* dst = in.partials + ((int64_t)(itm.band * rps + r) * L + ll) * ld;
+#pragma unroll
+                for (int k = 0; k < K; ++k)
+                    if (ok[k])
+                        *reinterpret_cast<float4*>(dst + col[k]) =
+                            make_float4(cur[4 * k], cur[4 * k + 1], cur[4 * k + 2], cur[4 * k + 3]);
             }
         }
-        // ---- band partials: row groups combined in group order ------------------
-        __syncthreads();
-        const int rps = in.rps;
-        for (int q = tid; q < L * kBK * tg; q += kBT) {
-            const int ll = q / (kBK * tg), rem = q - ll * kBK * tg, k = rem / tg, tt = rem - k * tg;
-            const int cc = 4 * (k * tg + tt);
-            if (cc >= (int)ld) continue;
-            float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
-            for (int rg = 0; rg < rps; ++rg) {
-                const float4 v = acc[(ll * kBK + k) * kBT + rg * tg + tt];
-                s.x = __fadd_rn(s.x, v.x);
-                s.y = __fadd_rn(s.y, v.y);
-                s.z = __fadd_rn(s.z, v.z);
-                s.w = __fadd_rn(s.w, v.w);
-            }
-            *reinterpret_cast<float4*>(in.partials + ((int64_t)itm.band * L + ll) * ld + cc) = s;
-        }
+        // The next item may group the warps differently: no warp may reuse a
+        // named-barrier id with another thread count while a group of this
+        // item still waits on it.
         __syncthreads();
     }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(*tslot, (uint32_t)tcols);
 }
 
-// Column statistics of every instance: one thread per (instance, level, column).
+// Column statistics of every instance: one thread per (instance, level, column);
+// G is the instance's number of partial rows (bands x row groups).
 struct BCol {
     const float* partials;
     const float* c;
@@ -394,6 +459,10 @@ struct hap_batch {
     bool own_ws = false;
     int s_bf16 = 0;
     int maxL = 1;
+    int K = 4;                       // float4 groups per thread (16 columns; 8 when an instance has > 8 levels)
+    int tcols = 32;                  // TMEM columns of a row-pass CTA
+    float* partials = nullptr;       // all instances' partial rows (sized by the schedule)
+    size_t partials_bytes = 0;
     std::vector<BInst> inst;         // host copy of the descriptors
     std::vector<size_t> inst_bytes;  // workspace bytes per instance (before partials)
     BInst* d_inst = nullptr;
@@ -432,12 +501,11 @@ size_t al(size_t x) { return (x + kAl - 1) / kAl * kAl; }
         }                                   \
     } while (0)
 
-// rows per step for a row of ld columns: groups of tg >= ld / 8 threads
-void group_shape(int ld, int* rps, int* tg) {
-    int t = 32;
-    while (t * 4 * kBK < ld) t *= 2;
-    *tg = t;
-    *rps = kBT / t;
+// Row groups for a row of ld columns at 4K columns per thread: g whole warps
+// per row (32 g 4K >= ld), rps = floor(16 / g) rows per step.
+void group_shape(int ld, int K, int* rps, int* g) {
+    *g = (ld + 32 * 4 * K - 1) / (32 * 4 * K);
+    *rps = kBW / *g;
 }
 
 // Bands per instance (total ~ items_per_cta x grid, proportional to work) and
@@ -474,6 +542,22 @@ int schedule(hap_batch* h) {
         per[p].push_back(o);
         load[p] += iw[o] + 1e3;  // + per-item overhead
     }
+    // partial rows: G bands x rps groups per instance
+    size_t need = 0;
+    std::vector<size_t> poff(B);
+    for (int b = 0; b < B; ++b) {
+        poff[b] = need;
+        need += al((size_t)h->inst[b].G * h->inst[b].rps * h->L[b] * h->ld[b] * 4);
+    }
+    if (need > h->partials_bytes) {
+        if (h->partials) cudaFree(h->partials);
+        h->partials = nullptr;
+        h->partials_bytes = 0;
+        BCU(cudaMalloc(&h->partials, need));
+        h->partials_bytes = need;
+    }
+    for (int b = 0; b < B; ++b)
+        h->inst[b].partials = reinterpret_cast<float*>(reinterpret_cast<char*>(h->partials) + poff[b]);
     std::vector<BItem> flat;
     std::vector<int> begin(h->grid + 1, 0);
     for (int p = 0; p < h->grid; ++p) {
@@ -492,7 +576,7 @@ int schedule(hap_batch* h) {
     int64_t first = 0;
     for (int b = 0; b < B; ++b) {
         const BInst& in = h->inst[b];
-        cols[b] = BCol{in.partials, in.c, in.phi, in.rdiag, in.b, in.tpart, in.N, in.L, in.ld, in.G, first};
+        cols[b] = BCol{in.partials, in.c, in.phi, in.rdiag, in.b, in.tpart, in.N, in.L, in.ld, in.G * in.rps, first};
         first += (int64_t)in.L * in.N;
     }
     BCU(cudaMemcpy(h->d_cols, cols.data(), B * sizeof(BCol), cudaMemcpyHostToDevice));
@@ -535,11 +619,18 @@ cudaError_t launch_batched_iteration(hap_batch* h, int pending, int update_c, in
     a.pending = pending;
     a.update_c = update_c;
     a.use_tau = use_tau;
-    const size_t smem = batched_smem_bytes(h->maxL, h->s_bf16 ? 2 : 4);
-    if (h->s_bf16)
-        rowpass_batched_kernel<__nv_bfloat16><<<h->grid, kBT, smem, st>>>(a, h->maxL);
-    else
-        rowpass_batched_kernel<float><<<h->grid, kBT, smem, st>>>(a, h->maxL);
+    const size_t smem = batched_smem_bytes(h->K, h->s_bf16 ? 2 : 4);
+    if (h->K == 4) {
+        if (h->s_bf16)
+            rowpass_batched_kernel<__nv_bfloat16, 4><<<h->grid, kBT, smem, st>>>(a, h->maxL, h->tcols);
+        else
+            rowpass_batched_kernel<float, 4><<<h->grid, kBT, smem, st>>>(a, h->maxL, h->tcols);
+    } else {
+        if (h->s_bf16)
+            rowpass_batched_kernel<__nv_bfloat16, 2><<<h->grid, kBT, smem, st>>>(a, h->maxL, h->tcols);
+        else
+            rowpass_batched_kernel<float, 2><<<h->grid, kBT, smem, st>>>(a, h->maxL, h->tcols);
+    }
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
     const unsigned blocks = (unsigned)((h->total_cols + 255) / 256);
@@ -578,35 +669,42 @@ int hap_batch_create(int B, const int64_t* N, const int* L, float damping, const
         maxL = std::max(maxL, L[b]);
     }
     h->maxL = maxL;
+    h->K = maxL <= 8 ? 4 : 2;
+    h->tcols = batched_tmem_cols(h->K, maxL);
     int dev = 0, sms = 0, smem_limit = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&smem_limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    const size_t smem = batched_smem_bytes(maxL, h->s_bf16 ? 2 : 4);
-    if (smem > (size_t)smem_limit) { delete h; return HAP_EUNSUPPORTED; }
+    const size_t smem = batched_smem_bytes(h->K, h->s_bf16 ? 2 : 4);
+    if (smem > (size_t)smem_limit || h->tcols > 512) { delete h; return HAP_EUNSUPPORTED; }
     // the shared-memory opt-in is set here, never inside a stream capture
-    if (cudaFuncSetAttribute(rowpass_batched_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
-        cudaFuncSetAttribute(rowpass_batched_kernel<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+    cudaError_t fa = h->K == 4
+        ? cudaFuncSetAttribute(h->s_bf16 ? (const void*)rowpass_batched_kernel<__nv_bfloat16, 4>
+                                         : (const void*)rowpass_batched_kernel<float, 4>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+        : cudaFuncSetAttribute(h->s_bf16 ? (const void*)rowpass_batched_kernel<__nv_bfloat16, 2>
+                                         : (const void*)rowpass_batched_kernel<float, 2>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (fa != cudaSuccess) {
         cudaGetLastError();
         delete h;
         return HAP_ECUDA;
     }
     h->grid = sms;
-    // workspace: per instance A, R, S, 8 vectors, partials sized for the most
-    // bands any schedule gives it (its row-block count, at most grid*items)
+    // workspace: per instance A, R, S, 8 vectors (the partial rows are sized
+    // by the schedule, in a buffer of their own)
     std::vector<size_t> off(B);
     h->inst.resize(B);
     for (int b = 0; b < B; ++b) {
-        int rps, tg;
-        group_shape(h->ld[b], &rps, &tg);
+        int rps, g;
+        group_shape(h->ld[b], h->K, &rps, &g);
         h->inst[b].rps = rps;
-        h->inst[b].tg = tg;
-        const int nblk = (int)((N[b] + rps - 1) / rps);
+        h->inst[b].g = g;
         const size_t mat = (size_t)L[b] * N[b] * h->ld[b] * 4;
         const size_t vec = (size_t)L[b] * h->ld[b] * 4;
         const size_t s = (size_t)N[b] * h->ld[b] * (h->s_bf16 ? 2 : 4);
         off[b] = total;
-        total += al(mat) * 2 + al(s) + 8 * al(vec) + al((size_t)nblk * vec);
+        total += al(mat) * 2 + al(s) + 8 * al(vec);
     }
     int64_t ecount = 0, levels = 0;
     for (int b = 0; b < B; ++b) { ecount += (int64_t)L[b] * N[b]; levels += L[b]; }
@@ -632,7 +730,7 @@ int hap_batch_create(int B, const int64_t* N, const int* L, float damping, const
         for (int q = 0; q < 8; ++q) { v[q] = reinterpret_cast<float*>(p); p += vec; }
         in.pref = v[0]; in.c = v[1]; in.tau = v[2]; in.phi = v[3]; in.tpart = v[4]; in.b = v[5]; in.rdiag = v[6];
         h->c0.push_back(v[7]);
-        in.partials = reinterpret_cast<float*>(p);
+        in.partials = nullptr;
         in.N = (int)N[b];
         in.L = L[b];
         in.ld = h->ld[b];
@@ -695,6 +793,7 @@ void hap_batch_destroy(hap_batch* h) {
     cudaFree(h->d_e_first);
     cudaFree(h->d_lev_inst);
     cudaFree(h->d_lev_l);
+    cudaFree(h->partials);
     if (h->own_ws) cudaFree(h->ws);
     delete h;
 }

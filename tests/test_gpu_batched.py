@@ -96,3 +96,58 @@ def test_batch_build_similarity_tensor_cores():
         assert all(e <= TOL for e in errs.values()), (b, errs)
         ctx.close()
     bt.close()
+
+
+@pytest.mark.parametrize("Ns,Ls", [([2600, 3100, 1500, 40], [3, 2, 4, 2]),     # 6, 7, 3, 1 warps per row
+                                   ([700, 2000, 150], [9, 2, 10])])          # > 8 levels: 8 columns per thread
+def test_batch_row_group_shapes(Ns, Ls, report):
+    """Row groups of every width (1..8 warps) and the 8-column variant used
+    when an instance has more than 8 levels, against single-instance runs."""
+    from paper_1403_7394_gb300 import hap
+    insts = _instances(Ns, Ls, seed=40)
+    bt = hap.HAPBatch(Ns, Ls, damping=0.5, device=DEV)
+    bt.set_preferences([x[2] for x in insts])
+    for b, (_, S32, _) in enumerate(insts):
+        bt.set_similarity(b, torch.from_numpy(S32).to(DEV))
+    bt.iterate(5)
+    worst = 0.0
+    for b, (_, S32, prefs) in enumerate(insts):
+        ctx = hap.HAP(Ns[b], Ls[b], prefs=prefs, damping=0.5, device=DEV)
+        ctx.set_similarity(torch.from_numpy(S32).to(DEV))
+        ctx.iterate(5)
+        errs = _errs(bt.get_state(b), ctx.get_state())
+        worst = max(worst, max(errs.values()))
+        assert all(e <= TOL for e in errs.values()), (b, errs)
+        ctx.close()
+    report(worst=worst)
+    bt.close()
+
+
+def test_batch_many_items_per_cta(report):
+    """More items than CTAs, so every CTA walks several (instance, band) items
+    whose row groups differ in width (1..2 warps here) and level count; after
+    the tuner, sampled instances against single-instance runs."""
+    from paper_1403_7394_gb300 import hap
+    rng = np.random.default_rng(11)
+    B = 400
+    Ns = [int(x) for x in rng.integers(30, 900, size=B)]
+    Ls = [int(x) for x in rng.integers(1, 5, size=B)]
+    insts = _instances(Ns, Ls, seed=500)
+    bt = hap.HAPBatch(Ns, Ls, damping=0.5, device=DEV)
+    bt.set_preferences([x[2] for x in insts])
+    for b, (_, S32, _) in enumerate(insts):
+        bt.set_similarity(b, torch.from_numpy(S32).to(DEV))
+    bt.tune()
+    bt.iterate(4)
+    worst = 0.0
+    for b in rng.choice(B, 12, replace=False):
+        _, S32, prefs = insts[b]
+        ctx = hap.HAP(Ns[b], Ls[b], prefs=prefs, damping=0.5, device=DEV)
+        ctx.set_similarity(torch.from_numpy(S32).to(DEV))
+        ctx.iterate(4)
+        errs = _errs(bt.get_state(int(b)), ctx.get_state())
+        worst = max(worst, max(errs.values()))
+        assert all(e <= TOL for e in errs.values()), (b, errs)
+        ctx.close()
+    report(worst=worst, items_per_cta=bt.query(8))
+    bt.close()
