@@ -229,10 +229,13 @@ int hap_row_pass_time(hap_ctx* ctx, double* ms, int64_t* launches, int reset);
  * batched column-statistics launch, replayed from a CUDA graph from the second
  * iteration on.  Instance b has N[b] points (2 <= N[b] <= 4096) and L[b] levels
  * (1..16); rows of small instances are processed up to 16 per step by row
- * groups of one CTA.  Same equations and schedule as hap_iterate.  The
- * context allocates its own device memory (hap_batch_destroy frees it).
+ * groups of one CTA; CTAs claim (instance, band) items largest first from one
+ * list, so results do not depend on which CTA ran what.  Same equations and
+ * schedule as hap_iterate (data-parallel schedule, kappa = 0).  The context
+ * allocates its own device memory (hap_batch_destroy frees it).
  *   N, L   host arrays of B entries.
- * Options used: c_mode, s_dtype (opt may be NULL). */
+ * Options used: c_mode, s_dtype (opt may be NULL); another schedule or
+ * kappa != 0 gives HAP_EUNSUPPORTED. */
 typedef struct hap_batch hap_batch;
 int hap_batch_create(int B, const int64_t* N, const int* L, float damping, const hap_options* opt,
                      hap_batch** out);

@@ -64,7 +64,8 @@ struct BItem {
 struct BatchArgs {
     const BInst* inst;
     const BItem* items;
-    const int* cta_begin;  // items of CTA p: [cta_begin[p], cta_begin[p + 1])
+    int* counter;          // next unclaimed item (zeroed before every launch)
+    int n_items;           // items, sorted by decreasing work
     unsigned* status;
     float lam, oml;
     int pending, update_c, use_tau;
@@ -73,7 +74,7 @@ struct BatchArgs {
 size_t batched_smem_bytes(int K, int s_elem) {
     const size_t E = (size_t)b_stage_elems(K);
     const size_t stage = 2 * E * 4 + E * s_elem;
-    const size_t bytes = b_stages(K) * stage + 2 * kBW * 16 + 2 * b_stages(K) * 8 + 8;
+    const size_t bytes = b_stages(K) * stage + 2 * kBW * 16 + 2 * b_stages(K) * 8 + 8 + 4 * (b_stages(K) + 2) + 256;
     // more than half an SM's shared memory: one CTA per SM, so its TMEM
     // allocation never waits for another CTA
     return std::max<size_t>(bytes, 116 * 1024);
@@ -113,11 +114,22 @@ __global__ void __launch_bounds__(kBT, 1) rowpass_batched_kernel(const BatchArgs
     const uint32_t full0 = smem_addr(red + 2 * kBW);            // full[NST] (TMA landed)
     const uint32_t empty0 = full0 + 8 * NST;                    // empty[NST] (every warp released)
     uint32_t* tslot = reinterpret_cast<uint32_t*>(red + 2 * kBW) + 4 * NST;
+    // items claimed by the producer, in claim order; -1 = no more work
+    constexpr int F = NST + 2;
+    int* fifo = reinterpret_cast<int*>(tslot + 2);
+    // the current item's descriptors (read from shared memory where used, which
+    // keeps them out of registers) and the producer's cursor
+    struct BProd {
+        int pi, pq, issued, claimed, done;
+    };
+    BInst* s_in = reinterpret_cast<BInst*>(reinterpret_cast<unsigned char*>(fifo + F) +
+                                           ((16 - (reinterpret_cast<uintptr_t>(fifo + F) & 15)) & 15));
+    BItem* s_it = reinterpret_cast<BItem*>(s_in + 1);
+    BProd* prod = reinterpret_cast<BProd*>(s_it + 1);
     const uint32_t sm0 = smem_addr(sm);
     const float lam = p.lam, oml = p.oml;
     const bool pending = p.pending != 0;
 
-    const int it0 = p.cta_begin[blockIdx.x], it1 = p.cta_begin[blockIdx.x + 1];
     if (tid == 0) {
         for (int q = 0; q < NST; ++q) {
             mbar_init(full0 + 8 * q, 1);
@@ -133,11 +145,26 @@ __global__ void __launch_bounds__(kBT, 1) rowpass_batched_kernel(const BatchArgs
     const uint32_t tq = *tslot + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((warp >> 2) * maxL * 4 * K);
     bool bad = false;
 
-    // ---- producer (thread 0): a cursor over (item, step) ahead of the consumers
-    int pi = it0, pq = 0, issued = 0;
+    // ---- producer (thread 0): claims items from the global list (largest
+    // first) and streams their steps ahead of the consumers.  Which CTA takes
+    // which item does not change any result: every item writes only its own
+    // rows and partial rows.
+    if (tid == 0) *prod = BProd{-1, 0, 0, 0, 0};
     auto issue_next = [&]() {
-        while (pi < it1 && pq >= p.items[pi].nsteps) { ++pi; pq = 0; }
-        if (pi >= it1) return false;
+        BProd c = *prod;
+        if (c.done) return false;
+        while (c.pi < 0 || c.pq >= p.items[c.pi].nsteps) {
+            c.pi = atomicAdd(p.counter, 1);
+            c.pq = 0;
+            fifo[c.claimed % F] = c.pi < p.n_items ? c.pi : -1;
+            ++c.claimed;
+            if (c.pi >= p.n_items) {
+                c.done = 1;
+                *prod = c;
+                return false;
+            }
+        }
+        const int pi = c.pi, pq = c.pq, issued = c.issued;
         const BItem itm = p.items[pi];
         const BInst in = p.inst[itm.inst];
         const int m = pq / in.L, l = pq % in.L;
@@ -154,18 +181,28 @@ __global__ void __launch_bounds__(kBT, 1) rowpass_batched_kernel(const BatchArgs
         bulk_g2s(dst, in.A + off, n * 4u, bar);
         bulk_g2s(dst + A_BYTES, in.R + off, n * 4u, bar);
         if (load_s) bulk_g2s(dst + 2 * A_BYTES, static_cast<const ST*>(in.S) + (int64_t)i0 * in.ld, n * (uint32_t)sizeof(ST), bar);
-        ++pq;
-        ++issued;
+        c.pq = pq + 1;
+        c.issued = issued + 1;
+        *prod = c;
         return true;
     };
     if (tid == 0)
         for (int q = 0; q < NST; ++q)
             if (!issue_next()) break;
+    __syncthreads();  // the first claimed item is in fifo[0]
 
     int step = 0;  // consumer step counter of this CTA (ring position)
-    for (int it = it0; it < it1; ++it) {
-        const BItem itm = p.items[it];
-        const BInst in = p.inst[itm.inst];
+    for (int kit = 0;; ++kit) {
+        // read by every thread after a CTA barrier: the item is CTA-uniform
+        const int it = fifo[kit % F];
+        if (it < 0) break;
+        if (tid == 0) {
+            *s_it = p.items[it];
+            *s_in = p.inst[s_it->inst];
+        }
+        __syncthreads();
+        const BItem itm = *s_it;
+        const BInst& in = *s_in;
         const int g = in.g, tg = 32 * g, rps = in.rps;
         const int r = warp / g;
         const bool active = r < rps;  // warps beyond rps * g only keep the ring in step
@@ -211,11 +248,7 @@ __global__ void __launch_bounds__(kBT, 1) rowpass_batched_kernel(const BatchArgs
             const int i0 = (itm.band + m * in.G) * rps;
             const int row = i0 + r;
             const bool rv = active && row < N;  // this group's row exists
-            float4 bcur[K];
-#pragma unroll
-            for (int k = 0; k < K; ++k) bcur[k] = nb[k];
             const float pref_i = npref, c_fixed = nc, tpart_i = ntp;
-            if (q + 1 < itm.nsteps) prefetch(q + 1);
             const int st = step % NST;
             const unsigned char* base = sm + (size_t)st * STAGE;
             const int rr0 = active ? r : 0;
@@ -229,7 +262,7 @@ __global__ void __launch_bounds__(kBT, 1) rowpass_batched_kernel(const BatchArgs
             // ---- pass 1: pending availability (Eqs. 2.2/2.3), row statistics ------
             float m1 = -kInf, m2 = -kInf, cm = -kInf;
             int k1 = 0x7fffffff;
-            float4 rr[K], ss[K];
+            float4 rr[K];
 #pragma unroll
             for (int k = 0; k < K; ++k) {
                 float4 a4 = f4_splat(-kInf), r4 = f4_splat(0.f), s4 = f4_splat(0.f);
@@ -241,7 +274,7 @@ __global__ void __launch_bounds__(kBT, 1) rowpass_batched_kernel(const BatchArgs
                     s4 = srow[k];
                 }
                 float4 an = a4;
-                const float4 b4 = bcur[k];
+                const float4 b4 = nb[k];
                 if (pending) {
                     an.x = damp(a4.x, avail_target(b4.x, r4.x, false), lam, oml);
                     an.y = damp(a4.y, avail_target(b4.y, r4.y, false), lam, oml);
@@ -261,11 +294,12 @@ __global__ void __launch_bounds__(kBT, 1) rowpass_batched_kernel(const BatchArgs
                 cm = fmaxf(cm, fmaxf(fmaxf(__fadd_rn(an.x, r4.x), __fadd_rn(an.y, r4.y)),
                                      fmaxf(__fadd_rn(an.z, r4.z), __fadd_rn(an.w, r4.w))));
                 rr[k] = r4;
-                ss[k] = s4;
             }
-            // this warp has read stage st
+            // this warp has read stage st; b and the row scalars of the next step
+            // load while the reductions and pass 2 run
             __syncwarp();
             if (lane == 0) mbar_arrive_local(empty0 + 8 * st);
+            if (q + 1 < itm.nsteps) prefetch(q + 1);
             // ---- exact reduction within the row group ----------------------------
             warp_top2(m1, k1, m2, cm);
             const int par = step & 1;
@@ -296,7 +330,10 @@ __global__ void __launch_bounds__(kBT, 1) rowpass_batched_kernel(const BatchArgs
             float addv[4 * K];
 #pragma unroll
             for (int k = 0; k < K; ++k) {
-                const float4 r4 = rr[k], s4 = ss[k];
+                const float4 r4 = rr[k];
+                float4 s4 = (ok[k] && rv) ? srow[k] : f4_splat(0.f);
+                const int dd = row - col[k];
+                if ((unsigned)dd < 4u) f4_set(s4, dd, pref_i);
                 float4 rn;
                 rn.x = damp(r4.x, __fadd_rn(s4.x, mm1), lam, oml);
                 rn.y = damp(r4.y, __fadd_rn(s4.y, mm1), lam, oml);
@@ -306,7 +343,6 @@ __global__ void __launch_bounds__(kBT, 1) rowpass_batched_kernel(const BatchArgs
                 if ((unsigned)dk < 4u) f4_set(rn, dk, damp(f4_get(r4, dk), __fadd_rn(f4_get(s4, dk), mm2), lam, oml));
                 float4 add = make_float4(fmaxf(rn.x, 0.f), fmaxf(rn.y, 0.f), fmaxf(rn.z, 0.f), fmaxf(rn.w, 0.f));
                 if (!(ok[k] && rv)) add = f4_splat(0.f);
-                const int dd = row - col[k];
                 if ((unsigned)dd < 4u) {
                     f4_set(add, dd, 0.f);
                     if (rv && !bad) in.rdiag[voff + row] = f4_get(rn, dd);
@@ -341,8 +377,9 @@ __global__ void __launch_bounds__(kBT, 1) rowpass_batched_kernel(const BatchArgs
         }
         // The next item may group the warps differently: no warp may reuse a
         // named-barrier id with another thread count while a group of this
-        // item still waits on it.
-        __syncthreads();
+        // item still waits on it.  A timed-out wait anywhere ends the CTA's
+        // work uniformly (the status word already records it).
+        if (__syncthreads_or(bad)) break;
     }
     tc_fence_before();
     __syncthreads();
@@ -468,7 +505,8 @@ struct hap_batch {
     BInst* d_inst = nullptr;
     BCol* d_cols = nullptr;
     BItem* d_items = nullptr;
-    int* d_cta_begin = nullptr;
+    int* d_counter = nullptr;        // item claim counter of the row pass
+    int n_items = 0;
     int64_t* d_row_first = nullptr;
     int64_t* d_e_first = nullptr;
     int* d_lev_inst = nullptr;
@@ -535,13 +573,6 @@ int schedule(hap_batch* h) {
     std::vector<int> order(items.size());
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return iw[a] > iw[b]; });
-    std::vector<std::vector<int>> per(h->grid);
-    std::vector<double> load(h->grid, 0.0);
-    for (int o : order) {
-        const int p = (int)(std::min_element(load.begin(), load.end()) - load.begin());
-        per[p].push_back(o);
-        load[p] += iw[o] + 1e3;  // + per-item overhead
-    }
     // partial rows: G bands x rps groups per instance
     size_t need = 0;
     std::vector<size_t> poff(B);
@@ -558,19 +589,14 @@ int schedule(hap_batch* h) {
     }
     for (int b = 0; b < B; ++b)
         h->inst[b].partials = reinterpret_cast<float*>(reinterpret_cast<char*>(h->partials) + poff[b]);
+    // one list, largest items first: CTAs claim them in this order (dynamic
+    // longest-processing-time balancing)
     std::vector<BItem> flat;
-    std::vector<int> begin(h->grid + 1, 0);
-    for (int p = 0; p < h->grid; ++p) {
-        begin[p] = (int)flat.size();
-        for (int o : per[p]) flat.push_back(items[o]);
-    }
-    begin[h->grid] = (int)flat.size();
+    for (int o : order) flat.push_back(items[o]);
+    h->n_items = (int)flat.size();
     if (h->d_items) cudaFree(h->d_items);
-    if (h->d_cta_begin) cudaFree(h->d_cta_begin);
     BCU(cudaMalloc(&h->d_items, std::max<size_t>(1, flat.size()) * sizeof(BItem)));
-    BCU(cudaMalloc(&h->d_cta_begin, begin.size() * sizeof(int)));
     BCU(cudaMemcpy(h->d_items, flat.data(), flat.size() * sizeof(BItem), cudaMemcpyHostToDevice));
-    BCU(cudaMemcpy(h->d_cta_begin, begin.data(), begin.size() * sizeof(int), cudaMemcpyHostToDevice));
     BCU(cudaMemcpy(h->d_inst, h->inst.data(), B * sizeof(BInst), cudaMemcpyHostToDevice));
     std::vector<BCol> cols(B);
     int64_t first = 0;
@@ -612,7 +638,10 @@ cudaError_t launch_batched_iteration(hap_batch* h, int pending, int update_c, in
     BatchArgs a;
     a.inst = h->d_inst;
     a.items = h->d_items;
-    a.cta_begin = h->d_cta_begin;
+    a.counter = h->d_counter;
+    a.n_items = h->n_items;
+    cudaError_t err0 = cudaMemsetAsync(h->d_counter, 0, sizeof(int), st);
+    if (err0 != cudaSuccess) return err0;
     a.status = h->status;
     a.lam = h->lam;
     a.oml = 1.0f - h->lam;
@@ -759,6 +788,7 @@ int hap_batch_create(int B, const int64_t* N, const int* L, float damping, const
                cudaMalloc(&h->d_e_first, B * sizeof(int64_t)) == cudaSuccess &&
                cudaMalloc(&h->d_lev_inst, levels * sizeof(int)) == cudaSuccess &&
                cudaMalloc(&h->d_lev_l, levels * sizeof(int)) == cudaSuccess &&
+               cudaMalloc(&h->d_counter, sizeof(int)) == cudaSuccess &&
                cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
     if (!okm) { cudaGetLastError(); hap_batch_destroy(h); return HAP_ENOMEM; }
     cudaMemcpy(h->d_row_first, row_first.data(), B * sizeof(int64_t), cudaMemcpyHostToDevice);
@@ -788,7 +818,7 @@ void hap_batch_destroy(hap_batch* h) {
     cudaFree(h->d_inst);
     cudaFree(h->d_cols);
     cudaFree(h->d_items);
-    cudaFree(h->d_cta_begin);
+    cudaFree(h->d_counter);
     cudaFree(h->d_row_first);
     cudaFree(h->d_e_first);
     cudaFree(h->d_lev_inst);
@@ -942,11 +972,13 @@ int hap_batch_get_state(hap_batch* h, int b, float* A, float* R, float* vecs, in
 }
 
 // Autotuner: times one steady-state iteration (CUDA events) for each
-// scheduling granularity in {1, 2, 3, 4, 6} items per CTA and keeps the
-// fastest; the messages are reset to Algorithm 1's start afterwards.
+// scheduling granularity in {2, 4, 6, 8, 12, 16} items per CTA (finer items
+// balance the dynamic claiming better but cost a CTA barrier, TMEM
+// zeroing and partial rows each) and keeps the fastest; the messages are
+// reset to Algorithm 1's start afterwards.
 int hap_batch_tune(hap_batch* h, double* best_ms) {
     if (!h) return HAP_EINVAL;
-    const int cands[5] = {1, 2, 3, 4, 6};
+    const int cands[6] = {2, 4, 6, 8, 12, 16};
     double best = 1e30;
     int best_c = h->items_per_cta;
     cudaEvent_t e0, e1;
