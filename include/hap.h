@@ -280,12 +280,36 @@ int hap_batch_sync(hap_batch* batch);
  * Asynchronous on `stream`. */
 int hap_knn(const float* X, int64_t N, int64_t d, int M, int32_t* idx, float* dist, void* stream);
 
+/* hap_knn with an explicit method (hap_knn uses HAP_KNN_AUTO):
+ *   HAP_KNN_CUDA_CORES    FP32 direct differences for every pair.
+ *   HAP_KNN_TENSOR_CORES  first pass on tcgen05 tensor cores with the BF16 hi/lo
+ *                         split (x.y ~ hi.hi + hi.lo + lo.hi, error ~2^-16 of the
+ *                         norms), keeping the M + 16 smallest per query, then the
+ *                         exact FP32 direct-difference distances of those
+ *                         candidates and the M nearest by (distance, index) - the
+ *                         CUDA-core result whenever the true M nearest are among
+ *                         the M + 16 first-pass candidates.  M <= 64; allocates
+ *                         stream-ordered scratch; if its bounded waits give up
+ *                         (a stalled GPU) every output index is -1.
+ *   HAP_KNN_AUTO          tensor cores when N*N >= 16e6 and M <= 64. */
+#define HAP_KNN_AUTO          0
+#define HAP_KNN_CUDA_CORES    1
+#define HAP_KNN_TENSOR_CORES  2
+int hap_knn_with(const float* X, int64_t N, int64_t d, int M, int method, int32_t* idx, float* dist, void* stream);
+
 /* M nearest members of a subset for every point: candidates are the points
  * subset[0..Ns) (device int32 global indices), a point never takes itself;
  * idx holds global indices.  Uses a temporary device buffer of Ns*d floats
  * (stream-ordered allocation).  Otherwise as hap_knn. */
 int hap_knn_subset(const float* X, int64_t N, int64_t d, const int32_t* subset, int64_t Ns, int M, int32_t* idx,
                    float* dist, void* stream);
+/* Kernels launched so far by this process through the stateless proposal
+ * entry points (kNN, features, scores, candidates, MLP). */
+int64_t hap_proposal_launches(void);
+
+/* hap_knn_subset with an explicit method (HAP_KNN_*). */
+int hap_knn_subset_with(const float* X, int64_t N, int64_t d, const int32_t* subset, int64_t Ns, int M, int method,
+                        int32_t* idx, float* dist, void* stream);
 
 /* Indices of the H highest scores (device [N]), lower index first on ties,
  * ordered by decreasing score, into hubs device int32 [H].  Asynchronous. */

@@ -60,6 +60,14 @@ cudaError_t launch_colstats(const float* partials, int G, int L, int64_t N, int6
                             const float* c, const float* phi, const float* rdiag,
                             float* b, float* tpart, cudaStream_t st, float* tp_level = nullptr);
 
+// Nearest neighbours with tensor-core first-pass distances (BF16 hi/lo split)
+// and an exact FP32 re-rank of the M2 >= M best candidates per query row.
+// Queries Q [Nq][d], candidates C [Nc][d] (global ids cid, null = index);
+// a query never takes its own id.  d <= 64, M2 <= knn_tc_max_candidates().
+int knn_tc_max_candidates();
+cudaError_t launch_knn_tc(const float* Q, int64_t Nq, const float* C, const int32_t* cid, int64_t Nc, int64_t d, int M,
+                          int M2, int32_t* idx, float* dist, cudaStream_t st);
+
 // One level of the sequential (Gauss-Seidel) schedule after its rho pass and
 // column statistics: alpha^l (Eqs. 2.2-2.3, damped), then c^l (Eq. 2.6, when
 // update_c), phi^{l-1} (Eq. 2.5, when phi_out) and tau^{l+1} = c^l + tp

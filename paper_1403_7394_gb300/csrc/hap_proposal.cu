@@ -9,6 +9,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+#include <atomic>
 #include <new>
 #include <vector>
 
@@ -545,10 +547,28 @@ struct hap_mlp {
     cudaStream_t stream = nullptr;
 };
 
+// kernels launched by the stateless proposal entry points (hap_proposal_launches)
+static std::atomic<int64_t> g_launches{0};
+
 extern "C" {
 
+int64_t hap_proposal_launches(void) { return g_launches.load(); }
+
 static int knn_launch(const float* Q, int64_t Nq, const float* C, const int32_t* cid, int64_t Nc, int64_t d, int M,
-                      int32_t* idx, float* dist, cudaStream_t st) {
+                      int32_t* idx, float* dist, cudaStream_t st, int method) {
+    if (method != HAP_KNN_AUTO && method != HAP_KNN_CUDA_CORES && method != HAP_KNN_TENSOR_CORES) return HAP_EINVAL;
+    const int M2 = std::min(M + 16, knn_tc_max_candidates());
+    const bool tc_ok = d <= 64 && M + 16 <= knn_tc_max_candidates();
+    if (method == HAP_KNN_TENSOR_CORES && !tc_ok) return HAP_EUNSUPPORTED;
+    // tensor cores once the N_q x N_c distances dominate (the first pass keeps
+    // M + 16 candidates per query for the exact re-rank)
+    if (method == HAP_KNN_TENSOR_CORES || (method == HAP_KNN_AUTO && tc_ok && (double)Nq * (double)Nc >= 16e6)) {
+        cudaError_t err = launch_knn_tc(Q, Nq, C, cid, Nc, d, M, M2, idx, dist, st);
+        if (err == cudaErrorNotSupported) { cudaGetLastError(); return HAP_EUNSUPPORTED; }
+        PCU(err);
+        g_launches += 4;  // two operand packs, the tensor-core pass, the re-rank
+        return HAP_OK;
+    }
     const int D = d <= 4 ? 4 : d <= 8 ? 8 : d <= 16 ? 16 : d <= 32 ? 32 : 64;
     const size_t smem = ((size_t)KNN_TILE * D + (size_t)M * KNN_ROWS * 2) * 4;
     const unsigned grid = (unsigned)((Nq + KNN_ROWS - 1) / KNN_ROWS);
@@ -560,16 +580,26 @@ static int knn_launch(const float* Q, int64_t Nq, const float* C, const int32_t*
     HAP_KNN_CASE(4) HAP_KNN_CASE(8) HAP_KNN_CASE(16) HAP_KNN_CASE(32) HAP_KNN_CASE(64)
 #undef HAP_KNN_CASE
     PCU(cudaGetLastError());
+    g_launches += 1;
     return HAP_OK;
 }
 
-int hap_knn(const float* X, int64_t N, int64_t d, int M, int32_t* idx, float* dist, void* stream) {
+int hap_knn_with(const float* X, int64_t N, int64_t d, int M, int method, int32_t* idx, float* dist, void* stream) {
     if (!X || !idx || !dist || N < 2 || d < 1 || d > 64 || M < 1 || M > KNN_MAXM || M >= N) return HAP_EINVAL;
-    return knn_launch(X, N, X, nullptr, N, d, M, idx, dist, static_cast<cudaStream_t>(stream));
+    return knn_launch(X, N, X, nullptr, N, d, M, idx, dist, static_cast<cudaStream_t>(stream), method);
+}
+
+int hap_knn(const float* X, int64_t N, int64_t d, int M, int32_t* idx, float* dist, void* stream) {
+    return hap_knn_with(X, N, d, M, HAP_KNN_AUTO, idx, dist, stream);
 }
 
 int hap_knn_subset(const float* X, int64_t N, int64_t d, const int32_t* subset, int64_t Ns, int M, int32_t* idx,
                    float* dist, void* stream) {
+    return hap_knn_subset_with(X, N, d, subset, Ns, M, HAP_KNN_AUTO, idx, dist, stream);
+}
+
+int hap_knn_subset_with(const float* X, int64_t N, int64_t d, const int32_t* subset, int64_t Ns, int M, int method,
+                        int32_t* idx, float* dist, void* stream) {
     if (!X || !subset || !idx || !dist || N < 1 || Ns < 1 || d < 1 || d > 64 || M < 1 || M > KNN_MAXM || M > Ns)
         return HAP_EINVAL;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -579,8 +609,9 @@ int hap_knn_subset(const float* X, int64_t N, int64_t d, const int32_t* subset, 
     for (int64_t q = 0; q < Ns; q += 65535) {
         const int64_t nb = Ns - q < 65535 ? Ns - q : 65535;
         gather_rows_kernel<<<(unsigned)nb, 64, 0, st>>>(X, d, subset + q, C + q * d);
+        g_launches += 1;
     }
-    int rc = knn_launch(X, N, C, subset, Ns, d, M, idx, dist, st);
+    int rc = knn_launch(X, N, C, subset, Ns, d, M, idx, dist, st, method);
     cudaFreeAsync(C, st);
     return rc;
 }
@@ -597,6 +628,9 @@ int hap_top_scores(const float* score, int64_t N, int64_t H, int32_t* hubs, void
     for (int k = 2; k <= n2; k <<= 1)
         for (int j = k >> 1; j > 0; j >>= 1) bitonic_step_kernel<<<g, 256, 0, st>>>(keys, n2, j, k);
     hub_ids_kernel<<<(unsigned)((H + 255) / 256), 256, 0, st>>>(keys, (int)H, hubs);
+    for (int k = 2; k <= n2; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) g_launches += 1;
+    g_launches += 2;
     cudaError_t err = cudaGetLastError();
     cudaFreeAsync(keys, st);
     PCU(err);
@@ -609,6 +643,7 @@ int hap_select_hub_candidates(const int32_t* pool, int64_t N, int Mp, const int3
     select_hub_candidates_kernel<<<(unsigned)((N + 127) / 128), 128, 0, static_cast<cudaStream_t>(stream)>>>(
         pool, Mp, hubnn, Mh, (int)N, K, K_near, cand);
     PCU(cudaGetLastError());
+    g_launches += 1;
     return HAP_OK;
 }
 
@@ -631,6 +666,7 @@ int hap_knn_features(const float* dist, int64_t N, int M, int F, float* feats, f
     const int64_t n = N * F;
     features_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(dist, (int)N, M, F, ls, feats);
     PCU(cudaGetLastError());
+    g_launches += 2;
     return HAP_OK;
 }
 
@@ -701,6 +737,7 @@ int hap_mlp_forward(hap_mlp* h, const float* feats, int64_t n, float* logits) {
     mlp_forward_kernel<<<grid, MH, mlp_smem_bytes(false), h->stream>>>(feats, n, h->F, h->W1h, h->theta + y.ob1, h->W2h,
                                                                        h->theta + y.ob2, h->W3h, h->theta + y.ob3, logits);
     PCU(cudaGetLastError());
+    g_launches += 1;
     return HAP_OK;
 }
 
@@ -715,6 +752,7 @@ int hap_mlp_gradients(hap_mlp* h, const float* feats, const float* labels, int64
     mlp_reduce_kernel<<<(unsigned)((y.P + 255) / 256), 256, 0, h->stream>>>(h->gpart, h->lpart, h->ncta, y.P, n,
                                                                            h->grads, h->loss);
     PCU(cudaGetLastError());
+    g_launches += 2;
     if (grads_host) PCU(cudaMemcpyAsync(grads_host, h->grads, (size_t)y.P * 4, cudaMemcpyDeviceToHost, h->stream));
     if (loss_host) PCU(cudaMemcpyAsync(loss_host, h->loss, 4, cudaMemcpyDeviceToHost, h->stream));
     if (grads_host || loss_host) PCU(cudaStreamSynchronize(h->stream));
@@ -731,6 +769,7 @@ int hap_mlp_train_step(hap_mlp* h, const float* feats, const float* labels, int6
     adam_kernel<<<(unsigned)((h->y.P + 255) / 256), 256, 0, h->stream>>>(h->theta, h->m, h->v, h->grads, h->y.P, lr, b1,
                                                                         b2, 1e-8f, c1, c2, h->F, h->W1h, h->W2h, h->W3h);
     PCU(cudaGetLastError());
+    g_launches += 1;
     if (loss_host) {
         PCU(cudaMemcpyAsync(loss_host, h->loss, 4, cudaMemcpyDeviceToHost, h->stream));
         PCU(cudaStreamSynchronize(h->stream));
@@ -745,6 +784,7 @@ int hap_select_candidates(const int32_t* pool, int64_t N, int M, const float* sc
     select_candidates_kernel<<<(unsigned)((N + 127) / 128), 128, 0, static_cast<cudaStream_t>(stream)>>>(
         pool, (int)N, M, score, K, K_near, cand);
     PCU(cudaGetLastError());
+    g_launches += 1;
     return HAP_OK;
 }
 

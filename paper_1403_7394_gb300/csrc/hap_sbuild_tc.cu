@@ -190,8 +190,8 @@ __global__ void __launch_bounds__(128, 1) sbuild_tc_kernel(const __grid_constant
     if (warp == 0) tmem_dealloc(tmem, kTmemCols);
 }
 
-// Operands of the contraction (zero-padded to [npad][kpad] BF16) and FP32
-// row norms (accumulated in FP64 from the FP32 points).
+// Operands of the contraction (zero-padded to [npad][kpad] BF16; A or B may
+// be null) and FP32 row norms (accumulated in FP64 from the FP32 points).
 __global__ void pack_operands_kernel(const float* __restrict__ X, int N, int d, int split, int kpad,
                                      __nv_bfloat16* __restrict__ A, __nv_bfloat16* __restrict__ B,
                                      float* __restrict__ norms) {
@@ -201,15 +201,15 @@ __global__ void pack_operands_kernel(const float* __restrict__ X, int N, int d, 
         const float x = X[(int64_t)i * d + k];
         acc += (double)x * (double)x;
         const __nv_bfloat16 hi = __float2bfloat16_rn(x);
-        __nv_bfloat16* a = A + (int64_t)i * kpad;
-        __nv_bfloat16* b = B + (int64_t)i * kpad;
+        __nv_bfloat16* a = A ? A + (int64_t)i * kpad : nullptr;
+        __nv_bfloat16* b = B ? B + (int64_t)i * kpad : nullptr;
         if (split) {
             const __nv_bfloat16 lo = __float2bfloat16_rn(x - __bfloat162float(hi));
-            a[k] = hi; a[d + k] = hi; a[2 * d + k] = lo;
-            b[k] = hi; b[d + k] = lo; b[2 * d + k] = hi;
+            if (a) { a[k] = hi; a[d + k] = hi; a[2 * d + k] = lo; }
+            if (b) { b[k] = hi; b[d + k] = lo; b[2 * d + k] = hi; }
         } else {
-            a[k] = hi;
-            b[k] = hi;
+            if (a) a[k] = hi;
+            if (b) b[k] = hi;
         }
     }
     __shared__ double red[32];
@@ -220,6 +220,315 @@ __global__ void pack_operands_kernel(const float* __restrict__ X, int N, int d, 
         double t = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
         norms[i] = (float)t;
+    }
+}
+
+// ---- nearest neighbours with tensor-core candidate distances ----------------
+// One CTA per 128 query rows streams every 128-column tile of candidates:
+// warp 4 loads the query operand once and the candidate K-chunks through a
+// TMA ring, warp 5 issues the tcgen05.mma contractions into one of two TMEM
+// accumulators (128 columns each) so that the next tile's products overlap
+// the epilogue of this one, and warps 0-3 (one query row per thread, its
+// TMEM lane) turn dot products into squared distances
+// ||q||^2 + ||c||^2 - 2 q.c and keep the M2 smallest per row in shared
+// memory.  The candidate norm enters the contraction as two extra K columns
+// (A: 1, 1; B: -||c||^2/2 split into BF16 hi and lo), so the accumulator
+// holds v = q.c - ||c||^2/2 and the row's ranking key ||c||^2 - 2 q.c = -2v
+// needs no per-candidate arithmetic: a 32-column batch is skipped after one
+// max-reduction unless its largest v beats the row's threshold.  With the
+// BF16 hi/lo split the keys carry an error of about 2^-16 of the norms; a
+// second kernel recomputes the M2 candidates' distances exactly in FP32 and
+// keeps the M nearest, so the M2 - M spare candidates absorb the rounding of
+// the first pass.
+constexpr int KT_RING_MAX = 4;  // candidate K-chunk stages (fewer when shared memory is short)
+constexpr int KT_MAXM2 = 80;    // candidates kept per row by the first pass
+constexpr int KT_PEND = 32;     // per-row buffer of threshold-passing candidates of one 32-column batch
+constexpr int KT_THREADS = 192; // 4 epilogue warps, 1 producer warp, 1 MMA warp
+
+struct KnnTcArgs {
+    const float* qnorm;   // [Nq] query norms
+    const float* cnorm;   // [ncpad] candidate norms (0 beyond Nc)
+    const int32_t* cid;   // candidate j's global id (null: j)
+    int Nq, Nc, M2, kchunks, ring;
+    int32_t* cand;        // out [Nq][M2] candidate columns, -1 where fewer
+    unsigned* status;
+};
+
+// at least 116 KB: one CTA per SM, so its 256-column TMEM allocation never waits
+size_t knn_tc_smem_bytes(int kchunks, int ring, int M2) {
+    const size_t b = 1024 + (size_t)kchunks * BM * BK * 2 + (size_t)ring * BN * BK * 2 + (size_t)M2 * BM * 8 +
+                     (size_t)KT_PEND * BM * 8;
+    return b < 116 * 1024 ? 116 * 1024 : b;
+}
+
+__global__ void __launch_bounds__(KT_THREADS, 1) knn_tc_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                              const __grid_constant__ CUtensorMap tmB,
+                                                              const KnnTcArgs p) {
+    extern __shared__ unsigned char smem_raw[];
+    const uint32_t raw = smem_addr(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    const uint32_t sA = base;                                          // kchunks x [128][64] BF16
+    const uint32_t sB = sA + (uint32_t)p.kchunks * BM * BK * 2;        // ring x [128][64] BF16
+    const int R = p.ring;
+    float* tdist = reinterpret_cast<float*>(smem_raw + (sB + R * BN * BK * 2 - raw));  // heap [M2][128]
+    int* tidx = reinterpret_cast<int*>(tdist + p.M2 * BM);                                   // [M2][128]
+    float* pdist = reinterpret_cast<float*>(tidx + p.M2 * BM);                               // [KT_PEND][128]
+    int* pidx = reinterpret_cast<int*>(pdist + KT_PEND * BM);                                // [KT_PEND][128]
+    __shared__ uint64_t bars[1 + 2 * KT_RING_MAX + 4];  // a_full, b_full[R], b_empty[R], acc_full[2], acc_empty[2]
+    __shared__ uint32_t tmem_slot;
+    __shared__ int s_abort;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t a_full = smem_addr(&bars[0]);
+    const uint32_t b_full = a_full + 8, b_empty = b_full + 8 * KT_RING_MAX;
+    const uint32_t acc_full = b_empty + 8 * KT_RING_MAX, acc_empty = acc_full + 16;
+    const int m0 = blockIdx.x * BM;
+    const int ntiles = (p.Nc + BN - 1) / BN;
+    if (tid == 0) {
+        mbar_init(a_full, 1);
+        for (int q = 0; q < R; ++q) {
+            mbar_init(b_full + 8 * q, 1);
+            mbar_init(b_empty + 8 * q, 1);
+        }
+        for (int q = 0; q < 2; ++q) {
+            mbar_init(acc_full + 8 * q, 1);
+            mbar_init(acc_empty + 8 * q, BM);
+        }
+        s_abort = 0;
+        fence_mbarrier_init();
+    }
+    if (warp == 0) tmem_alloc(smem_addr(&tmem_slot), 256);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+    volatile int* abort_flag = &s_abort;
+
+    if (warp == 4) {
+        if (lane == 0) {  // ---- producer
+            mbar_arrive_expect_tx(a_full, (uint32_t)p.kchunks * BM * BK * 2);
+            for (int kc = 0; kc < p.kchunks; ++kc) tma_load_2d(sA + (uint32_t)kc * BM * BK * 2, &tmA, kc * BK, m0, a_full);
+            const int total = ntiles * p.kchunks;
+            for (int g = 0; g < total && !*abort_flag; ++g) {
+                const int st = g % R;
+                if (g >= R && !mbar_wait(b_empty + 8 * st, (uint32_t)((g / R - 1) & 1), p.status)) {
+                    *abort_flag = 1;
+                    break;
+                }
+                const int t = g / p.kchunks, kc = g - t * p.kchunks;
+                mbar_arrive_expect_tx(b_full + 8 * st, BN * BK * 2);
+                tma_load_2d(sB + (uint32_t)st * BN * BK * 2, &tmB, kc * BK, t * BN, b_full + 8 * st);
+            }
+        }
+    } else if (warp == 5) {
+        if (lane == 0) {  // ---- MMA issuer
+            bool ok = mbar_wait(a_full, 0u, p.status);
+            for (int t = 0; t < ntiles && ok && !*abort_flag; ++t) {
+                const int buf = t & 1;
+                if (t >= 2 && !(ok = mbar_wait(acc_empty + 8 * buf, (uint32_t)((t / 2 - 1) & 1), p.status))) break;
+                tc_fence_after();
+                for (int kc = 0; kc < p.kchunks; ++kc) {
+                    const int g = t * p.kchunks + kc, st = g % R;
+                    if (!(ok = mbar_wait(b_full + 8 * st, (uint32_t)((g / R) & 1), p.status))) break;
+                    tc_fence_after();
+                    const uint32_t a_s = sA + (uint32_t)kc * BM * BK * 2, b_s = sB + (uint32_t)st * BN * BK * 2;
+#pragma unroll
+                    for (int kk = 0; kk < BK / 16; ++kk)
+                        umma_bf16(tmem + (uint32_t)(buf * BN), desc_kmajor_sw128(a_s + 32 * kk),
+                                  desc_kmajor_sw128(b_s + 32 * kk), kIdesc, (kc > 0 || kk > 0) ? 1u : 0u);
+                    umma_commit(b_empty + 8 * st);
+                }
+                if (!ok) break;
+                umma_commit(acc_full + 8 * buf);
+            }
+            if (!ok) *abort_flag = 1;
+        }
+    } else {  // ---- epilogue: warps 0-3, thread = query row = TMEM lane
+        const int row = m0 + tid;
+        // the M2 smallest first-pass keys ||c||^2 - 2 q.c of this row as a
+        // max-heap in shared memory (root = current threshold); columns below
+        // the threshold are first appended to a short buffer (cheap even when
+        // few lanes of the warp take the branch) and then pushed into the
+        // heap by all lanes with pending candidates together
+        int cnt = 0;
+        float thr = kInf, vthr = -kInf;  // key < thr  <=>  v > vthr = -thr / 2
+        const int M2 = p.M2;
+        auto heap_push = [&](float dv, int j) {
+            if (cnt < M2) {  // sift up
+                int c = cnt++;
+                while (c > 0) {
+                    const int par = (c - 1) >> 1;
+                    const float pd = tdist[par * BM + tid];
+                    if (pd >= dv) break;
+                    tdist[c * BM + tid] = pd;
+                    tidx[c * BM + tid] = tidx[par * BM + tid];
+                    c = par;
+                }
+                tdist[c * BM + tid] = dv;
+                tidx[c * BM + tid] = j;
+            } else if (dv < tdist[tid]) {  // replace the root, sift down
+                int c = 0;
+                for (;;) {
+                    int ch = 2 * c + 1;
+                    if (ch >= M2) break;
+                    float cd = tdist[ch * BM + tid];
+                    if (ch + 1 < M2) {
+                        const float cd2 = tdist[(ch + 1) * BM + tid];
+                        if (cd2 > cd) { cd = cd2; ++ch; }
+                    }
+                    if (cd <= dv) break;
+                    tdist[c * BM + tid] = cd;
+                    tidx[c * BM + tid] = tidx[ch * BM + tid];
+                    c = ch;
+                }
+                tdist[c * BM + tid] = dv;
+                tidx[c * BM + tid] = j;
+            }
+            thr = cnt == M2 ? tdist[tid] : kInf;
+            vthr = -0.5f * thr;
+        };
+        for (int t = 0; t < ntiles; ++t) {
+            // warp-uniform decisions: the TMEM loads below are warp-collective
+            if (__any_sync(0xffffffffu, *abort_flag != 0)) break;
+            const int buf = t & 1;
+            const bool got = mbar_wait(acc_full + 8 * buf, (uint32_t)((t >> 1) & 1), p.status);
+            if (!__all_sync(0xffffffffu, got)) {
+                *abort_flag = 1;
+                break;
+            }
+            tc_fence_after();
+            const bool full_tile = (t + 1) * BN <= p.Nc;
+#pragma unroll 1
+            for (int cc = 0; cc < BN / 32; ++cc) {
+                float v[32];
+                __syncwarp();
+                tmem_ld_32x32b_x32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(buf * BN + 32 * cc), v);
+                const int jb = t * BN + 32 * cc;
+                float vm = v[0];
+#pragma unroll
+                for (int q = 1; q < 32; ++q) vm = fmaxf(vm, v[q]);
+                int np = 0;
+                if (vm > vthr) {
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) {
+                        if (v[q] > vthr && (full_tile || jb + q < p.Nc)) {
+                            pdist[np * BM + tid] = -2.f * v[q];
+                            pidx[np * BM + tid] = jb + q;
+                            ++np;
+                        }
+                    }
+                }
+                for (int k = 0; k < np; ++k) {
+                    const int j = pidx[k * BM + tid];
+                    const int gid = p.cid ? p.cid[j] : j;
+                    if (gid != row) heap_push(pdist[k * BM + tid], j);
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(acc_empty + 8 * buf);
+        }
+        if (row < p.Nq)
+            for (int m = 0; m < M2; ++m) p.cand[(int64_t)row * M2 + m] = m < cnt ? tidx[m * BM + tid] : -1;
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, 256);
+}
+
+// Exact re-rank of the first pass's candidates: one warp per query row,
+// FP32 direct-difference distances accumulated in dimension order (the
+// CUDA-core kNN's arithmetic), the M nearest by (distance, global index).
+__global__ void knn_rerank_kernel(const float* __restrict__ Q, const float* __restrict__ C,
+                                  const int32_t* __restrict__ cid, int Nq, int d, int M2, int M,
+                                  const int32_t* __restrict__ cand, const unsigned* __restrict__ status,
+                                  int32_t* __restrict__ out_idx, float* __restrict__ out_dist) {
+    const int lane = threadIdx.x & 31;
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= Nq) return;
+    if (*status) {  // the first pass gave up waiting: no result
+        for (int m = lane; m < M; m += 32) {
+            out_idx[i * M + m] = -1;
+            out_dist[i * M + m] = __int_as_float(0x7fc00000);
+        }
+        return;
+    }
+    constexpr int PER = (KT_MAXM2 + 31) / 32;
+    float dv[PER];
+    int gv[PER];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int q = lane + 32 * u;
+        const int j = q < M2 ? cand[i * M2 + q] : -1;
+        dv[u] = kInf;
+        gv[u] = 0x7fffffff;
+        if (j >= 0) {
+            float acc = 0.f;
+            for (int k = 0; k < d; ++k) {
+                const float e = Q[i * d + k] - C[(int64_t)j * d + k];
+                acc = fmaf(e, e, acc);
+            }
+            dv[u] = acc;
+            gv[u] = cid ? cid[j] : j;
+        }
+    }
+    for (int m = 0; m < M; ++m) {
+        // lane-local best, then a warp argmin by (distance, global index)
+        float bd = kInf;
+        int bg = 0x7fffffff, bu = -1;
+#pragma unroll
+        for (int u = 0; u < PER; ++u)
+            if (dv[u] < bd || (dv[u] == bd && gv[u] < bg)) { bd = dv[u]; bg = gv[u]; bu = u; }
+        float wd = bd;
+        int wg = bg;
+        for (int o = 16; o > 0; o >>= 1) {
+            const float od = __shfl_xor_sync(0xffffffffu, wd, o);
+            const int og = __shfl_xor_sync(0xffffffffu, wg, o);
+            if (od < wd || (od == wd && og < wg)) { wd = od; wg = og; }
+        }
+        if (bu >= 0 && bd == wd && bg == wg) {  // the unique owner removes it
+#pragma unroll
+            for (int u = 0; u < PER; ++u)
+                if (u == bu) { dv[u] = kInf; gv[u] = 0x7fffffff; }
+        }
+        if (lane == 0) {
+            out_idx[i * M + m] = wg == 0x7fffffff ? -1 : wg;
+            out_dist[i * M + m] = wd;
+        }
+    }
+}
+
+// Operands of the nearest-neighbour contraction (zero-padded to [npad][kpad]
+// BF16): queries A = [hi, hi, lo, 1, 1], candidates B = [hi, lo, hi, h, l]
+// with h + l = -||c||^2 / 2 (BF16 hi and lo; the norm accumulated in FP64).
+__global__ void pack_knn_kernel(const float* __restrict__ X, int N, int d, int kpad, int is_b,
+                                __nv_bfloat16* __restrict__ out) {
+    const int i = blockIdx.x;
+    __nv_bfloat16* o = out + (int64_t)i * kpad;
+    double acc = 0.0;
+    for (int k = threadIdx.x; k < d; k += blockDim.x) {
+        const float x = X[(int64_t)i * d + k];
+        acc += (double)x * (double)x;
+        const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+        const __nv_bfloat16 lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+        o[k] = hi;
+        o[d + k] = is_b ? lo : hi;
+        o[2 * d + k] = is_b ? hi : lo;
+    }
+    __shared__ double red[32];
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        if (is_b) {
+            const float h = (float)(-0.5 * t);
+            const __nv_bfloat16 bh = __float2bfloat16_rn(h);
+            o[3 * d] = bh;
+            o[3 * d + 1] = __float2bfloat16_rn((float)(-0.5 * t - (double)__bfloat162float(bh)));
+        } else {
+            o[3 * d] = __float2bfloat16_rn(1.f);
+            o[3 * d + 1] = __float2bfloat16_rn(1.f);
+        }
     }
 }
 
@@ -306,4 +615,71 @@ cudaError_t launch_sbuild_tc(const float* X, int64_t N, int64_t d, int split, vo
     return err;
 }
 
+
+int knn_tc_max_candidates() { return KT_MAXM2; }
+
+cudaError_t launch_knn_tc(const float* Q, int64_t Nq, const float* C, const int32_t* cid, int64_t Nc, int64_t d, int M,
+                          int M2, int32_t* idx, float* dist, cudaStream_t st) {
+    if (M2 > KT_MAXM2 || M2 < M || d > 64) return cudaErrorInvalidValue;
+    const int64_t kpad = (3 * d + 2 + BK - 1) / BK * BK;
+    const int64_t qpad = (Nq + BM - 1) / BM * BM, cpad = (Nc + BN - 1) / BN * BN;
+    const size_t aB = (size_t)qpad * kpad * 2, bB = (size_t)cpad * kpad * 2;
+    const size_t off_b = (aB + 1023) / 1024 * 1024, off_qn = off_b + (bB + 1023) / 1024 * 1024;
+    const size_t off_cn = off_qn + ((size_t)qpad * 4 + 255) / 256 * 256;
+    const size_t off_cand = off_cn + ((size_t)cpad * 4 + 255) / 256 * 256;
+    const size_t off_status = off_cand + ((size_t)Nq * M2 * 4 + 255) / 256 * 256;
+    const size_t total = off_status + 256 + 1024;
+    char* raw = nullptr;
+    cudaError_t err = cudaMallocAsync(reinterpret_cast<void**>(&raw), total, st);
+    if (err != cudaSuccess) return err;
+    char* base = reinterpret_cast<char*>(((uintptr_t)raw + 1023) & ~(uintptr_t)1023);
+    __nv_bfloat16* A = reinterpret_cast<__nv_bfloat16*>(base);
+    __nv_bfloat16* B = reinterpret_cast<__nv_bfloat16*>(base + off_b);
+    float* qn = reinterpret_cast<float*>(base + off_qn);
+    float* cn = reinterpret_cast<float*>(base + off_cn);
+    int32_t* cand = reinterpret_cast<int32_t*>(base + off_cand);
+    unsigned* status = reinterpret_cast<unsigned*>(base + off_status);
+    do {
+        if ((err = cudaMemsetAsync(base, 0, off_cand, st)) != cudaSuccess) break;
+        if ((err = cudaMemsetAsync(status, 0, 16, st)) != cudaSuccess) break;
+        pack_knn_kernel<<<(unsigned)Nq, 64, 0, st>>>(Q, (int)Nq, (int)d, (int)kpad, 0, A);
+        pack_knn_kernel<<<(unsigned)Nc, 64, 0, st>>>(C, (int)Nc, (int)d, (int)kpad, 1, B);
+        if ((err = cudaGetLastError()) != cudaSuccess) break;
+        CUtensorMap mA, mB;
+        if (!encode_operand_map(&mA, A, qpad, kpad) || !encode_operand_map(&mB, B, cpad, kpad)) {
+            err = cudaErrorNotSupported;
+            break;
+        }
+        KnnTcArgs a;
+        a.qnorm = qn;
+        a.cnorm = cn;
+        a.cid = cid;
+        a.Nq = (int)Nq;
+        a.Nc = (int)Nc;
+        a.M2 = M2;
+        a.kchunks = (int)(kpad / BK);
+        a.cand = cand;
+        a.status = status;
+        int dev = 0, smem_limit = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&smem_limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        a.ring = KT_RING_MAX;
+        while (a.ring > 2 && knn_tc_smem_bytes(a.kchunks, a.ring, M2) > (size_t)smem_limit) --a.ring;
+        const size_t smem = knn_tc_smem_bytes(a.kchunks, a.ring, M2);
+        if (smem > (size_t)smem_limit) {
+            err = cudaErrorNotSupported;
+            break;
+        }
+        if ((err = cudaFuncSetAttribute(knn_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+            cudaSuccess)
+            break;
+        knn_tc_kernel<<<(unsigned)(qpad / BM), KT_THREADS, smem, st>>>(mA, mB, a);
+        if ((err = cudaGetLastError()) != cudaSuccess) break;
+        knn_rerank_kernel<<<(unsigned)((Nq * 32 + 255) / 256), 256, 0, st>>>(Q, C, cid, (int)Nq, (int)d, M2, M, cand,
+                                                                            status, idx, dist);
+        err = cudaGetLastError();
+    } while (0);
+    cudaError_t e2 = cudaFreeAsync(raw, st);
+    return err != cudaSuccess ? err : e2;
+}
 }  // namespace hap

@@ -7,9 +7,14 @@
 // Layout: cand [N][K] int32, s [N][K] FP32 (= -||x_i - x_cand||^2, the
 // preference on the self entry), alpha and rho [L][N][K].  Row pass: one warp
 // per row walks the L levels (alpha kept one step behind exactly as in the
-// dense row pass).  Column statistics read rho through a CSC map (for every
-// column j the entries (k, q) with cand[k][q] = j, in entry order), so every
-// sum has a fixed order.
+// dense row pass; the next level's alpha, rho and b are loaded while the
+// current level reduces).  The column index (CSC: for every column j the
+// entries (k, q) with cand[k][q] = j, in entry order) is built on the GPU by
+// a stable radix sort of the entries by column; the row pass writes the
+// positive off-diagonal responsibilities straight to their CSC slots (in a
+// buffer zeroed before the pass: most responsibilities are negative, so few
+// scattered writes), and the column statistics sum contiguous segments in a
+// fixed order.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -28,6 +33,8 @@ constexpr int SP_MAXK = 64;
 
 struct SparseArgs {
     const int32_t* cand;
+    const int32_t* pos;    // [N][K] CSC slot of every entry
+    float* cval;           // [L][N*K] max(0, rho) in CSC order (0 on the diagonal), zeroed before the pass
     const float* s;
     float* A;
     float* R;
@@ -51,9 +58,10 @@ __global__ void __launch_bounds__(256) sparse_rowpass_kernel(const SparseArgs p)
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int K = p.K, L = p.L, N = p.N;
+    const int64_t NK = (int64_t)N * K;
     const bool pending = p.pending != 0;
     for (int64_t i = wid; i < N; i += nw) {
-        int jq[2];
+        int jq[2], pq[2];
         float sq[2];
         bool has[2];
 #pragma unroll
@@ -61,26 +69,47 @@ __global__ void __launch_bounds__(256) sparse_rowpass_kernel(const SparseArgs p)
             const int q = lane + 32 * h;
             has[h] = q < K;
             jq[h] = has[h] ? p.cand[i * K + q] : 0x7fffffff;
+            pq[h] = has[h] ? p.pos[i * K + q] : 0;
             sq[h] = has[h] ? p.s[i * K + q] : 0.f;
+        }
+        // level 0's messages; later levels are loaded one level ahead
+        float a[2], r[2], bb[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int64_t at = i * K + lane + 32 * h;
+            a[h] = has[h] ? p.A[at] : -kInf;
+            r[h] = has[h] ? p.R[at] : 0.f;
+            bb[h] = (has[h] && pending) ? __ldg(p.b + jq[h]) : 0.f;
         }
         float c_prev = 0.f;
         for (int l = 0; l < L; ++l) {
             const int64_t base = ((int64_t)l * N + i) * K;
             const int64_t voff = (int64_t)l * N;
-            float a[2], r[2], x[2];
+            float na[2] = {-kInf, -kInf}, nr[2] = {0.f, 0.f}, nbb[2] = {0.f, 0.f};
+            if (l + 1 < L) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int64_t at = base + NK + lane + 32 * h;
+                    if (has[h]) {
+                        na[h] = p.A[at];
+                        nr[h] = p.R[at];
+                        if (pending) nbb[h] = __ldg(p.b + voff + N + jq[h]);
+                    }
+                }
+            }
+            const float pref_i = __ldg(p.pref + voff + i);
+            float x[2];
             float m1 = -kInf, m2 = -kInf, cm = -kInf;
             int k1 = 0x7fffffff;
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int q = lane + 32 * h;
-                if (!has[h]) { a[h] = -kInf; r[h] = 0.f; x[h] = -kInf; continue; }
+                if (!has[h]) { x[h] = -kInf; continue; }
                 const bool diag = jq[h] == (int)i;
-                const float sv = diag ? p.pref[voff + i] : sq[h];
+                const float sv = diag ? pref_i : sq[h];
                 x[h] = sv;
-                a[h] = p.A[base + q];
-                r[h] = p.R[base + q];
                 if (pending) {
-                    a[h] = damp(a[h], avail_target(p.b[voff + jq[h]], r[h], diag), p.lam, p.oml);
+                    a[h] = damp(a[h], avail_target(bb[h], r[h], diag), p.lam, p.oml);
                     p.A[base + q] = a[h];
                 }
                 top2_push(__fadd_rn(a[h], sv), jq[h], m1, k1, m2);
@@ -102,37 +131,220 @@ __global__ void __launch_bounds__(256) sparse_rowpass_kernel(const SparseArgs p)
                 const float mx = jq[h] == k1 ? m2 : m1;
                 const float rn = damp(r[h], __fadd_rn(x[h], fminf(tauv, -mx)), p.lam, p.oml);
                 p.R[base + q] = rn;
-                if (jq[h] == (int)i) p.rdiag[voff + i] = rn;
+                const bool diag = jq[h] == (int)i;
+                if (diag) p.rdiag[voff + i] = rn;
+                // the CSC values start at zero each iteration: only positive
+                // off-diagonal responsibilities are written (a few per row)
+                if (!diag && rn > 0.f) p.cval[(int64_t)l * NK + pq[h]] = rn;
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                a[h] = na[h];
+                r[h] = nr[h];
+                bb[h] = nbb[h];
             }
         }
     }
 }
 
-// P_j = sum over the column's entries (rows k != j) of max(0, rho): one warp
-// per (level, column); lane t sums entries t, t + 32, ... in order, then a
-// fixed xor-shuffle tree (columns of popular candidates hold thousands of
-// entries, so a thread per column would serialise on them)
-__global__ void sparse_colstats_kernel(const float* __restrict__ R, const int64_t* __restrict__ cptr,
-                                       const int32_t* __restrict__ cent, int N, int L, int K,
-                                       const float* __restrict__ c, const float* __restrict__ phi,
+// P_j = sum over the column's entries (rows k != j) of max(0, rho), read from
+// the CSC-ordered values the row pass wrote: one warp per column for every
+// level (the levels' loads overlap); per level, lane t sums slots t, t + 32,
+// ... in order, then a fixed xor-shuffle tree (columns of popular candidates
+// hold thousands of entries)
+constexpr int kColLevels = 4;  // levels summed together
+__global__ void sparse_colstats_kernel(const float* __restrict__ cval, const int64_t* __restrict__ cptr, int N, int L,
+                                       int K, const float* __restrict__ c, const float* __restrict__ phi,
                                        const float* __restrict__ rdiag, float* __restrict__ b, float* __restrict__ tpart) {
-    const int64_t idx = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (idx >= (int64_t)L * N) return;
-    const int l = (int)(idx / N);
-    const int64_t j = idx - (int64_t)l * N;
-    const float* Rl = R + (int64_t)l * N * K;
-    float P = 0.f;
-    for (int64_t e = cptr[j] + lane; e < cptr[j + 1]; e += 32) {
-        const int32_t ent = cent[e];
-        if (ent / K != j) P = __fadd_rn(P, fmaxf(Rl[ent], 0.f));
+    if (j >= N) return;
+    const int64_t e0 = cptr[j], e1 = cptr[j + 1];
+    const int64_t NK = (int64_t)N * K;
+    for (int l0 = 0; l0 < L; l0 += kColLevels) {
+        float P[kColLevels];
+#pragma unroll
+        for (int u = 0; u < kColLevels; ++u) P[u] = 0.f;
+        for (int64_t e = e0 + lane; e < e1; e += 32) {
+#pragma unroll
+            for (int u = 0; u < kColLevels; ++u)
+                if (l0 + u < L) P[u] = __fadd_rn(P[u], __ldcs(cval + (int64_t)(l0 + u) * NK + e));
+        }
+#pragma unroll
+        for (int u = 0; u < kColLevels; ++u) {
+            for (int o = 16; o > 0; o >>= 1) P[u] = __fadd_rn(P[u], __shfl_xor_sync(0xffffffffu, P[u], o));
+            const int l = l0 + u;
+            if (lane == 0 && l < L) {
+                const int64_t idx = (int64_t)l * N + j;
+                const float rd = rdiag[idx];
+                b[idx] = __fadd_rn(__fadd_rn(__fadd_rn(c[idx], phi[idx]), rd), P[u]);
+                if (l + 1 < L) tpart[idx + N] = __fadd_rn(rd, P[u]);
+            }
+        }
     }
-    for (int o = 16; o > 0; o >>= 1) P = __fadd_rn(P, __shfl_xor_sync(0xffffffffu, P, o));
-    if (lane == 0) {
-        const float rd = rdiag[idx];
-        b[idx] = __fadd_rn(__fadd_rn(__fadd_rn(c[idx], phi[idx]), rd), P);
-        if (l + 1 < L) tpart[idx + N] = __fadd_rn(rd, P);
+}
+
+// ---- candidate graph on the GPU: checks, column index (CSC) -----------------
+// Every row must be strictly increasing, in range and contain its own index;
+// a violation sets ST_BOUNDS.  Also counts the entries of every column.
+__global__ void sparse_check_count_kernel(const int32_t* __restrict__ cand, int N, int K, unsigned* status,
+                                          int* __restrict__ cnt) {
+    const int lane = threadIdx.x & 31;
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= N) return;
+    bool bad = false, self = false;
+    for (int q = lane; q < K; q += 32) {
+        const int j = cand[i * K + q];
+        const int prev = q > 0 ? cand[i * K + q - 1] : -1;
+        if (j < 0 || j >= N || j <= prev) {
+            bad = true;
+        } else {
+            atomicAdd(cnt + j, 1);
+            self |= j == (int)i;
+        }
     }
+    bad = __any_sync(0xffffffffu, bad);
+    self = __any_sync(0xffffffffu, self);
+    if (lane == 0 && (bad || !self)) atomicOr(status, ST_BOUNDS);
+}
+
+// Exclusive prefix sums of int counts (3 launches: tile sums, one-CTA scan of
+// the tile sums, tile-local scans plus offsets).
+constexpr int kScanT = 256, kScanPer = 8, kScanTile = kScanT * kScanPer;
+
+HAP_DEV int64_t block_exclusive_scan(int64_t v, int64_t* warp_sums, int64_t* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int64_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[warp] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int64_t run = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            const int64_t t = warp_sums[w];
+            warp_sums[w] = run;
+            run += t;
+        }
+        *total = run;
+    }
+    __syncthreads();
+    const int64_t out = x - v + warp_sums[warp];
+    __syncthreads();
+    return out;
+}
+
+__global__ void scan_tile_sums_kernel(const int* __restrict__ in, int64_t n, int64_t* __restrict__ tsum) {
+    __shared__ int64_t ws[kScanT / 32];
+    __shared__ int64_t tot;
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanPer;
+    int64_t v = 0;
+    for (int u = 0; u < kScanPer; ++u) v += (base + u < n) ? in[base + u] : 0;
+    block_exclusive_scan(v, ws, &tot);
+    if (threadIdx.x == 0) tsum[blockIdx.x] = tot;
+}
+
+__global__ void scan_tile_offsets_kernel(int64_t* __restrict__ tsum, int64_t ntiles) {
+    __shared__ int64_t ws[kScanT / 32];
+    __shared__ int64_t tot;
+    int64_t carry = 0;
+    for (int64_t b0 = 0; b0 < ntiles; b0 += kScanT) {
+        const int64_t k = b0 + threadIdx.x;
+        const int64_t v = k < ntiles ? tsum[k] : 0;
+        const int64_t ex = block_exclusive_scan(v, ws, &tot);
+        if (k < ntiles) tsum[k] = carry + ex;
+        carry += tot;
+        __syncthreads();
+    }
+}
+
+template <typename OT>
+__global__ void scan_apply_kernel(const int* __restrict__ in, int64_t n, const int64_t* __restrict__ toff,
+                                  OT* __restrict__ out) {
+    __shared__ int64_t ws[kScanT / 32];
+    __shared__ int64_t tot;
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanPer;
+    int64_t v = 0;
+    for (int u = 0; u < kScanPer; ++u) v += (base + u < n) ? in[base + u] : 0;
+    int64_t run = block_exclusive_scan(v, ws, &tot) + toff[blockIdx.x];
+    for (int u = 0; u < kScanPer; ++u) {
+        if (base + u < n) {
+            out[base + u] = (OT)run;
+            run += in[base + u];
+        }
+    }
+}
+
+// Stable least-significant-digit radix sort of (column, entry) pairs, 9-bit
+// digits, chunks of kRadixChunk consecutive elements per CTA.  Pass p orders
+// by digit p with ties kept in their current order, so after the last pass
+// the entries of every column are in increasing entry order.
+constexpr int kRadixBits = 9, kRadixBins = 1 << kRadixBits, kRadixT = 256, kRadixRounds = 16;
+constexpr int kRadixChunk = kRadixT * kRadixRounds;
+
+__global__ void radix_hist_kernel(const int32_t* __restrict__ key, int64_t n, int shift, int nchunks,
+                                  int* __restrict__ hist) {
+    __shared__ int h[kRadixBins];
+    for (int d = threadIdx.x; d < kRadixBins; d += kRadixT) h[d] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kRadixChunk;
+    for (int r = 0; r < kRadixRounds; ++r) {
+        const int64_t idx = base + (int64_t)r * kRadixT + threadIdx.x;
+        if (idx < n) atomicAdd(&h[(key[idx] >> shift) & (kRadixBins - 1)], 1);
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < kRadixBins; d += kRadixT) hist[(int64_t)d * nchunks + blockIdx.x] = h[d];
+}
+
+__global__ void __launch_bounds__(kRadixT) radix_scatter_kernel(
+    const int32_t* __restrict__ key, const int32_t* __restrict__ val, int64_t n, int shift, int nchunks,
+    const int* __restrict__ off, int32_t* __restrict__ okey, int32_t* __restrict__ oval) {
+    __shared__ int running[kRadixBins];
+    __shared__ int wcnt[kRadixT / 32][kRadixBins];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int d = tid; d < kRadixBins; d += kRadixT) {
+        running[d] = 0;
+        for (int w = 0; w < kRadixT / 32; ++w) wcnt[w][d] = 0;
+    }
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kRadixChunk;
+    for (int r = 0; r < kRadixRounds; ++r) {
+        const int64_t idx = base + (int64_t)r * kRadixT + tid;
+        const bool valid = idx < n;
+        const int32_t k = valid ? key[idx] : 0;
+        const int32_t v = valid ? (val ? val[idx] : (int32_t)idx) : 0;
+        const int d = valid ? ((k >> shift) & (kRadixBins - 1)) : kRadixBins;  // invalid: own class
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const int rank = __popc(peers & ((1u << lane) - 1u));
+        if (valid && rank == 0) wcnt[warp][d] = __popc(peers);
+        __syncthreads();
+        if (valid) {
+            int before = running[d] + rank;
+            for (int w = 0; w < warp; ++w) before += wcnt[w][d];
+            const int64_t pos = (int64_t)off[(int64_t)d * nchunks + blockIdx.x] + before;
+            okey[pos] = k;
+            oval[pos] = v;
+        }
+        __syncthreads();
+        for (int d2 = tid; d2 < kRadixBins; d2 += kRadixT) {
+            int sum = 0;
+            for (int w = 0; w < kRadixT / 32; ++w) {
+                sum += wcnt[w][d2];
+                wcnt[w][d2] = 0;
+            }
+            running[d2] += sum;
+        }
+        __syncthreads();
+    }
+}
+
+// pos[cent[x]] = x: the CSC slot of every entry
+__global__ void inverse_perm_kernel(const int32_t* __restrict__ cent, int64_t n, int32_t* __restrict__ pos) {
+    const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (x < n) pos[cent[x]] = (int32_t)x;
 }
 
 // s_iq = -||x_i - x_cand||^2 (FP32, direct differences); one warp per row
@@ -230,6 +442,13 @@ struct hap_sparse {
           *rdiag = nullptr;
     int64_t* cptr = nullptr;
     int32_t* cent = nullptr;
+    int32_t* pos = nullptr;       // [N*K] CSC slot of every entry
+    float* cval = nullptr;        // [L][N*K] max(0, rho) in CSC order
+    int32_t* tmp[4] = {nullptr, nullptr, nullptr, nullptr};  // radix-sort key / value buffers
+    int* cnt = nullptr;           // [N + 1] column counts
+    int* hist = nullptr;          // radix histograms, then their offsets
+    int* hoff = nullptr;
+    int64_t* tsum = nullptr;      // scan tile sums
     int32_t* e = nullptr;
     double* ns = nullptr;
     unsigned* status = nullptr;
@@ -241,6 +460,18 @@ struct hap_sparse {
 };
 
 namespace {
+
+int64_t radix_chunks(int64_t nk) { return (nk + kRadixChunk - 1) / kRadixChunk; }
+
+// exclusive prefix sums of n ints into out (int or int64)
+template <typename OT>
+cudaError_t scan_exclusive(const int* in, int64_t n, OT* out, int64_t* tsum, cudaStream_t st) {
+    const int64_t tiles = (n + kScanTile - 1) / kScanTile;
+    scan_tile_sums_kernel<<<(unsigned)tiles, kScanT, 0, st>>>(in, n, tsum);
+    scan_tile_offsets_kernel<<<1, kScanT, 0, st>>>(tsum, tiles);
+    scan_apply_kernel<OT><<<(unsigned)tiles, kScanT, 0, st>>>(in, n, tsum, out);
+    return cudaGetLastError();
+}
 
 int sparse_reset(hap_sparse* h) {
     const size_t mat = (size_t)h->L * h->N * h->K * 4, vec = (size_t)h->L * h->N * 4;
@@ -283,7 +514,13 @@ int hap_sparse_create(int64_t N, int L, int K, const float* prefs, float damping
               cudaMalloc(&h->b, vec) == cudaSuccess && cudaMalloc(&h->rdiag, vec) == cudaSuccess &&
               cudaMalloc(&h->cptr, (N + 1) * 8) == cudaSuccess && cudaMalloc(&h->cent, nk * 4) == cudaSuccess &&
               cudaMalloc(&h->e, (size_t)L * N * 4) == cudaSuccess && cudaMalloc(&h->ns, (size_t)L * 8) == cudaSuccess &&
-              cudaMalloc(&h->status, 16) == cudaSuccess;
+              cudaMalloc(&h->status, 16) == cudaSuccess && cudaMalloc(&h->pos, nk * 4) == cudaSuccess &&
+              cudaMalloc(&h->cval, mat) == cudaSuccess && cudaMalloc(&h->cnt, (N + 1) * 4) == cudaSuccess;
+    const int64_t nhist = (int64_t)kRadixBins * radix_chunks((int64_t)nk);
+    const int64_t ntiles = (std::max<int64_t>(nhist, N + 1) + kScanTile - 1) / kScanTile;
+    for (int q = 0; q < 4 && ok; ++q) ok = cudaMalloc(&h->tmp[q], nk * 4) == cudaSuccess;
+    ok = ok && cudaMalloc(&h->hist, nhist * 4) == cudaSuccess && cudaMalloc(&h->hoff, nhist * 4) == cudaSuccess &&
+         cudaMalloc(&h->tsum, ntiles * 8) == cudaSuccess;
     if (!ok) { cudaGetLastError(); hap_sparse_destroy(h); return HAP_ENOMEM; }
     cudaMemset(h->c0, 0, vec);
     cudaMemset(h->status, 0, 16);
@@ -304,6 +541,8 @@ void hap_sparse_destroy(hap_sparse* h) {
     cudaFree(h->cand); cudaFree(h->s); cudaFree(h->A); cudaFree(h->R); cudaFree(h->pref); cudaFree(h->c);
     cudaFree(h->c0); cudaFree(h->tau); cudaFree(h->phi); cudaFree(h->tpart); cudaFree(h->b); cudaFree(h->rdiag);
     cudaFree(h->cptr); cudaFree(h->cent); cudaFree(h->e); cudaFree(h->ns); cudaFree(h->status);
+    cudaFree(h->pos); cudaFree(h->cval); cudaFree(h->cnt); cudaFree(h->hist); cudaFree(h->hoff); cudaFree(h->tsum);
+    for (int q = 0; q < 4; ++q) cudaFree(h->tmp[q]);
     delete h;
 }
 
@@ -326,31 +565,43 @@ int hap_sparse_set_preferences(hap_sparse* h, const float* prefs, int per_point)
 int hap_sparse_set_candidates(hap_sparse* h, const int32_t* cand, const float* X, int64_t d) {
     if (!h || !cand || !X || d < 1) return HAP_EINVAL;
     const int64_t N = h->N, K = h->K, nk = N * K;
-    // candidate rows must contain the row itself, sorted, in range (host check)
-    std::vector<int32_t> hc(nk);
-    SCU(cudaMemcpyAsync(hc.data(), cand, nk * 4, cudaMemcpyDeviceToHost, h->stream));
-    SCU(cudaStreamSynchronize(h->stream));
-    std::vector<int64_t> cnt(N + 1, 0);
-    for (int64_t i = 0; i < N; ++i) {
-        bool self = false;
-        for (int64_t q = 0; q < K; ++q) {
-            const int32_t j = hc[i * K + q];
-            if (j < 0 || j >= N || (q > 0 && j <= hc[i * K + q - 1])) return HAP_EINVAL;
-            self |= j == i;
-            cnt[j + 1] += 1;
-        }
-        if (!self) return HAP_EINVAL;
-    }
-    for (int64_t j = 0; j < N; ++j) cnt[j + 1] += cnt[j];
-    std::vector<int32_t> ent(nk);
-    std::vector<int64_t> pos(cnt.begin(), cnt.end() - 1);
-    for (int64_t e = 0; e < nk; ++e) ent[pos[hc[e]]++] = (int32_t)e;  // entry order within each column
-    SCU(cudaMemcpyAsync(h->cand, hc.data(), nk * 4, cudaMemcpyHostToDevice, h->stream));
-    SCU(cudaMemcpyAsync(h->cptr, cnt.data(), (N + 1) * 8, cudaMemcpyHostToDevice, h->stream));
-    SCU(cudaMemcpyAsync(h->cent, ent.data(), nk * 4, cudaMemcpyHostToDevice, h->stream));
-    sparse_similarity_kernel<<<(unsigned)((nk + 255) / 256), 256, 0, h->stream>>>(X, d, h->cand, (int)N, (int)K, h->s);
+    cudaStream_t st = h->stream;
+    SCU(cudaMemcpyAsync(h->cand, cand, nk * 4, cudaMemcpyDeviceToDevice, st));
+    // checks (sorted, distinct, in range, contains the row) and column counts
+    SCU(cudaMemsetAsync(h->cnt, 0, (N + 1) * 4, st));
+    SCU(cudaMemsetAsync(h->status, 0, 16, st));
+    sparse_check_count_kernel<<<(unsigned)((N * 32 + 255) / 256), 256, 0, st>>>(h->cand, (int)N, (int)K, h->status, h->cnt);
     SCU(cudaGetLastError());
-    h->launches += 1;
+    SCU(scan_exclusive<int64_t>(h->cnt, N + 1, h->cptr, h->tsum, st));
+    // entries sorted by column, stable: the CSC entry order
+    int passes = 1;
+    while (passes * kRadixBits < 31 && ((int64_t)1 << (passes * kRadixBits)) < N) ++passes;
+    const int nchunks = (int)radix_chunks(nk);
+    const int32_t* kin = h->cand;
+    const int32_t* vin = nullptr;  // first pass: value = entry index
+    for (int p = 0; p < passes; ++p) {
+        const bool last = p + 1 == passes;
+        int32_t* ko = (kin == h->tmp[0]) ? h->tmp[2] : h->tmp[0];
+        int32_t* vo = last ? h->cent : ((vin == h->tmp[1]) ? h->tmp[3] : h->tmp[1]);
+        radix_hist_kernel<<<nchunks, kRadixT, 0, st>>>(kin, nk, p * kRadixBits, nchunks, h->hist);
+        SCU(cudaGetLastError());
+        SCU(scan_exclusive<int>(h->hist, (int64_t)kRadixBins * nchunks, h->hoff, h->tsum, st));
+        radix_scatter_kernel<<<nchunks, kRadixT, 0, st>>>(kin, vin, nk, p * kRadixBits, nchunks, h->hoff, ko, vo);
+        SCU(cudaGetLastError());
+        kin = ko;
+        vin = vo;
+    }
+    inverse_perm_kernel<<<(unsigned)((nk + 255) / 256), 256, 0, st>>>(h->cent, nk, h->pos);
+    sparse_similarity_kernel<<<(unsigned)((nk + 255) / 256), 256, 0, st>>>(X, d, h->cand, (int)N, (int)K, h->s);
+    SCU(cudaGetLastError());
+    h->launches += 6 + 3 * passes + 3 * passes;
+    unsigned stw = 0;
+    SCU(cudaMemcpyAsync(&stw, h->status, 4, cudaMemcpyDeviceToHost, st));
+    SCU(cudaStreamSynchronize(st));
+    if (stw & ST_BOUNDS) {
+        SCU(cudaMemset(h->status, 0, 16));
+        return HAP_EINVAL;
+    }
     h->X = X;
     h->d = d;
     return sparse_reset(h);
@@ -359,7 +610,8 @@ int hap_sparse_set_candidates(hap_sparse* h, const int32_t* cand, const float* X
 int hap_sparse_iterate(hap_sparse* h, int n) {
     if (!h || n < 0) return HAP_EINVAL;
     SparseArgs a;
-    a.cand = h->cand; a.s = h->s; a.A = h->A; a.R = h->R; a.pref = h->pref; a.c = h->c; a.tau = h->tau;
+    a.cand = h->cand; a.pos = h->pos; a.cval = h->cval;
+    a.s = h->s; a.A = h->A; a.R = h->R; a.pref = h->pref; a.c = h->c; a.tau = h->tau;
     a.phi = h->phi; a.tpart = h->tpart; a.b = h->b; a.rdiag = h->rdiag; a.status = h->status;
     a.N = h->N; a.L = h->L; a.K = h->K; a.lam = h->lam; a.oml = 1.0f - h->lam;
     int dev = 0, sms = 0;
@@ -372,11 +624,12 @@ int hap_sparse_iterate(hap_sparse* h, int n) {
         a.pending = h->pending ? 1 : 0;
         a.update_c = (h->c_mode == HAP_C_PAPER && t >= 2) ? 1 : 0;
         a.use_tau = t >= 2 ? 1 : 0;
+        SCU(cudaMemsetAsync(h->cval, 0, (size_t)h->L * h->N * h->K * 4, h->stream));
         sparse_rowpass_kernel<<<grid, 256, 0, h->stream>>>(a);
         SCU(cudaGetLastError());
-        const int64_t tot = (int64_t)h->L * h->N * 32;
+        const int64_t tot = (int64_t)h->N * 32;
         sparse_colstats_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, h->stream>>>(
-            h->R, h->cptr, h->cent, h->N, h->L, h->K, h->c, h->phi, h->rdiag, h->b, h->tpart);
+            h->cval, h->cptr, h->N, h->L, h->K, h->c, h->phi, h->rdiag, h->b, h->tpart);
         SCU(cudaGetLastError());
         h->launches += 2;
         h->pending = true;

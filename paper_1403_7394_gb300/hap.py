@@ -74,6 +74,9 @@ def _load():
         "hap_batch_query": (i32, [vp, i32, ctypes.POINTER(i64)]),
         "hap_batch_sync": (i32, [vp]),
         "hap_knn": (i32, [vp, i64, i64, i32, vp, vp, vp]),
+        "hap_knn_with": (i32, [vp, i64, i64, i32, i32, vp, vp, vp]),
+        "hap_proposal_launches": (i64, []),
+        "hap_knn_subset_with": (i32, [vp, i64, i64, vp, i64, i32, i32, vp, vp, vp]),
         "hap_knn_features": (i32, [vp, i64, i32, i32, vp, ctypes.POINTER(f32), vp]),
         "hap_knn_subset": (i32, [vp, i64, i64, vp, i64, i32, vp, vp, vp]),
         "hap_top_scores": (i32, [vp, i64, i64, vp, vp]),
@@ -424,25 +427,35 @@ def _stream_ptr(device, stream=None):
     return ctypes.c_void_p(st.cuda_stream)
 
 
-def knn(X: torch.Tensor, M: int, stream=None):
+KNN_METHODS = {"auto": 0, "cuda_cores": 1, "tensor_cores": 2}
+
+
+def proposal_launches() -> int:
+    """Kernels launched so far through the stateless proposal functions."""
+    return int(lib.hap_proposal_launches())
+
+
+def knn(X: torch.Tensor, M: int, stream=None, method: str = "auto"):
     """Exact M nearest neighbours (squared Euclidean, self excluded):
     (idx int32 (N, M), dist float32 (N, M)) on X's device."""
     X = X.contiguous()
     N, d = X.shape
     idx = torch.empty((N, M), dtype=torch.int32, device=X.device)
     dist = torch.empty((N, M), dtype=torch.float32, device=X.device)
-    check(lib.hap_knn(_ptr(X), N, d, int(M), _ptr(idx), _ptr(dist), _stream_ptr(X.device, stream)), "hap_knn")
+    check(lib.hap_knn_with(_ptr(X), N, d, int(M), KNN_METHODS[method], _ptr(idx), _ptr(dist),
+                           _stream_ptr(X.device, stream)), "hap_knn_with")
     return idx, dist
 
 
-def knn_subset(X: torch.Tensor, subset: torch.Tensor, M: int, stream=None):
+def knn_subset(X: torch.Tensor, subset: torch.Tensor, M: int, stream=None, method: str = "auto"):
     """For every point, its M nearest members of `subset` (global indices)."""
     X = X.contiguous()
     N, d = X.shape
     idx = torch.empty((N, M), dtype=torch.int32, device=X.device)
     dist = torch.empty((N, M), dtype=torch.float32, device=X.device)
-    check(lib.hap_knn_subset(_ptr(X), N, d, _ptr(subset.contiguous()), subset.numel(), int(M), _ptr(idx), _ptr(dist),
-                             _stream_ptr(X.device, stream)), "hap_knn_subset")
+    check(lib.hap_knn_subset_with(_ptr(X), N, d, _ptr(subset.contiguous()), subset.numel(), int(M),
+                                  KNN_METHODS[method], _ptr(idx), _ptr(dist), _stream_ptr(X.device, stream)),
+          "hap_knn_subset_with")
     return idx, dist
 
 
@@ -613,6 +626,12 @@ class HAPSparse:
         ns = np.zeros(self.L, dtype=np.float64)
         check(lib.hap_sparse_net_similarity(self._h, ns.ctypes.data_as(ctypes.c_void_p)), "hap_sparse_net_similarity")
         return ns
+
+    @property
+    def launches(self) -> int:
+        v = ctypes.c_int64(0)
+        check(lib.hap_sparse_query(self._h, Q_LAUNCHES, ctypes.byref(v)), "hap_sparse_query")
+        return v.value
 
     def get_state(self):
         A = torch.empty((self.L, self.N, self.K), dtype=torch.float32, device=self.device)

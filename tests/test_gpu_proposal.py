@@ -35,12 +35,15 @@ def _params_from_flat(theta, F, H_=128, round_weights=True):
     return out
 
 
-@pytest.mark.parametrize("N,d,M", [(1500, 32, 64), (700, 5, 100), (300, 2, 16)])
-def test_knn_exact(N, d, M):
+@pytest.mark.parametrize("method", ["cuda_cores", "tensor_cores"])
+@pytest.mark.parametrize("N,d,M", [(1500, 32, 64), (700, 5, 100), (300, 2, 16), (2100, 64, 64)])
+def test_knn_exact(N, d, M, method):
     hap = hapm()
+    if method == "tensor_cores" and M > 64:
+        pytest.skip("the tensor-core first pass keeps at most 80 candidates (M <= 64)")
     X, _ = W.gmm_points(N, d, 8, sigma=1.0, seed=d, means="normal", mean_scale=2.0)
     X32 = X.astype(np.float32)
-    idx, dist = hap.knn(torch.from_numpy(X32).to(DEV), M)
+    idx, dist = hap.knn(torch.from_numpy(X32).to(DEV), M, method=method)
     idx, dist = idx.cpu().numpy(), dist.cpu().numpy().astype(np.float64)
     ridx, rdist = P.knn(X32, M)
     assert np.abs(dist - rdist).max() <= 1e-5 * np.abs(rdist).max()
@@ -52,6 +55,26 @@ def test_knn_exact(N, d, M):
             dj = ((X32[i].astype(np.float64) - X32[j]) ** 2).sum()
             assert abs(dj - kth) <= 1e-5 * kth, (i, j)
         assert np.all(np.diff(dist[i]) >= 0)
+
+
+def test_knn_tensor_cores_match_cuda_cores(report):
+    """At a size where the tensor-core path is the automatic choice, its
+    re-ranked result equals the CUDA-core kNN (same FP32 distance arithmetic)
+    row for row; hub kNN (a subset of candidates) likewise up to the order of
+    exactly equal distances."""
+    hap = hapm()
+    X, _ = W.gmm_points(20000, 32, 64, sigma=1.0, seed=8, means="normal", mean_scale=2.0)
+    Xt = torch.from_numpy(X.astype(np.float32)).to(DEV)
+    i_tc, d_tc = hap.knn(Xt, 32, method="tensor_cores")
+    i_cc, d_cc = hap.knn(Xt, 32, method="cuda_cores")
+    same = (i_tc == i_cc).all(dim=1).float().mean().item()
+    report(rows_identical=same)
+    assert same == 1.0 and torch.equal(d_tc, d_cc)
+    sub = torch.from_numpy(np.sort(np.random.default_rng(1).choice(20000, 700, replace=False)).astype(np.int32)).to(DEV)
+    s_tc, e_tc = hap.knn_subset(Xt, sub, 48, method="tensor_cores")
+    s_cc, e_cc = hap.knn_subset(Xt, sub, 48, method="cuda_cores")
+    assert torch.equal(e_tc, e_cc)
+    assert torch.equal(torch.sort(s_tc, dim=1).values, torch.sort(s_cc, dim=1).values)
 
 
 def test_features_match_reference():
@@ -184,3 +207,77 @@ def test_full_candidate_graph_equals_dense_gpu():
     for k in ("A", "R", "c", "tau", "phi"):
         assert H.message_rel_error(gs[k].cpu().numpy(), gd[k].cpu().numpy()) <= 1e-5, k
     np.testing.assert_array_equal(sp.exemplars().cpu().numpy(), ctx.exemplars().cpu().numpy())
+
+
+def test_sparse_hub_columns_against_reference(report):
+    """A candidate graph with hub columns (every row keeps itself, its 20
+    nearest neighbours and 27 of 40 shared hubs, so hub columns hold about
+    2000 entries) and N > 512 (two radix passes in the GPU column index):
+    sparse HAP against the dense reference on the masked similarity, and
+    bitwise repeatable."""
+    hap = hapm()
+    N, L, K, T = 3000, 2, 48, 3
+    X, _ = W.gmm_points(N, 3, 8, sigma=0.7, seed=21, means="uniform", mean_scale=10.0)
+    X32 = X.astype(np.float32)
+    nn, _ = P.knn(X32, 20)
+    rng = np.random.default_rng(3)
+    hubs = rng.choice(N, 40, replace=False)
+    cn = np.empty((N, K), np.int32)
+    for i in range(N):
+        sel = [i] + [int(v) for v in nn[i]]
+        for hb in rng.permutation(hubs):
+            if len(sel) == K:
+                break
+            if hb not in sel:
+                sel.append(int(hb))
+        extra = 0
+        while len(sel) < K:  # rows whose neighbours overlap the hubs
+            if extra not in sel:
+                sel.append(extra)
+            extra += 1
+        cn[i] = np.sort(sel)
+    S64 = H.neg_sq_euclidean(X32.astype(np.float64))
+    prefs = np.array([-60.0, -120.0], dtype=np.float32)
+    S_full = H.level_similarities(S64, prefs.astype(np.float64))
+    S_mask = np.stack([P.masked_similarity(S_full[l], cn) for l in range(L)])
+    Xt = torch.from_numpy(X32).to(DEV)
+    cand = torch.from_numpy(cn).to(DEV)
+    outs = []
+    for _ in range(2):
+        sp = hap.HAPSparse(N, L, K, prefs=prefs, damping=0.5, c_mode="paper", device=DEV)
+        sp.set_candidates(cand, Xt)
+        sp.iterate(T)
+        outs.append(sp.get_state())
+        sp.close()
+    for k in ("A", "R", "c", "tau", "phi"):
+        assert torch.equal(outs[0][k], outs[1][k]), k
+    # the GPU's s uses the points' FP32 direct differences; the reference's S
+    # comes from the same FP32 points in FP64
+    ref = H.run(S_mask, T, 0.5, H.PAPER)
+    rows = np.repeat(np.arange(N), K)
+    errs = {}
+    for k in ("A", "R"):
+        got = outs[0][k].cpu().numpy().astype(np.float64)
+        errs[k] = H.message_rel_error(got, getattr(ref, k)[:, rows, cn.reshape(-1)].reshape(L, N, K))
+    for k in ("c", "tau", "phi"):
+        errs[k] = H.message_rel_error(outs[0][k].cpu().numpy().astype(np.float64), getattr(ref, k))
+    report(errs=errs, max_column=int(np.bincount(cn.reshape(-1)).max()))
+    assert all(v <= 1e-4 for v in errs.values()), errs
+
+
+def test_sparse_candidates_rejected():
+    hap = hapm()
+    N, K = 50, 4
+    Xt = torch.zeros((N, 2), device=DEV)
+    good = np.stack([np.sort(np.array([i, (i + 1) % N, (i + 2) % N, (i + 3) % N])) for i in range(N)]).astype(np.int32)
+    sp = hap.HAPSparse(N, 1, K, device=DEV)
+    sp.set_candidates(torch.from_numpy(good).to(DEV), Xt)
+    for bad in (good[:, ::-1].copy(),                                   # not increasing
+                np.where(good == np.arange(N)[:, None], (np.arange(N)[:, None] + 10) % N, good),  # no self
+                np.where(good == 3, N + 7, good)):                      # out of range
+        with pytest.raises(hap.HapError) as ei:
+            sp.set_candidates(torch.from_numpy(np.ascontiguousarray(bad, dtype=np.int32)).to(DEV), Xt)
+        assert ei.value.code == hap.HAP_EINVAL
+    sp.set_candidates(torch.from_numpy(good).to(DEV), Xt)
+    sp.iterate(2)
+    sp.close()
