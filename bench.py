@@ -178,7 +178,7 @@ def run_reference(args, world, rank):
     per = float(np.mean(times))
     value = n * n * L / per
     sample = f"one FP64 reference iteration (t>=2) of a {n}-point, L={L} instance of the workload family per step"
-    line = {"metric": "hap_message_updates_per_s", "value": value, "unit": "updates/s", "n_gpus": 0,
+    line = {"metric": "hap_message_updates_per_s", "value": value, "unit": "updates/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "desc": desc, "sample_points": n},

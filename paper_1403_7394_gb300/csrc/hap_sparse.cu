@@ -148,39 +148,25 @@ __global__ void __launch_bounds__(256) sparse_rowpass_kernel(const SparseArgs p)
 }
 
 // P_j = sum over the column's entries (rows k != j) of max(0, rho), read from
-// the CSC-ordered values the row pass wrote: one warp per column for every
-// level (the levels' loads overlap); per level, lane t sums slots t, t + 32,
-// ... in order, then a fixed xor-shuffle tree (columns of popular candidates
-// hold thousands of entries)
-constexpr int kColLevels = 4;  // levels summed together
+// the CSC-ordered values the row pass wrote: one warp per (level, column);
+// lane t sums slots t, t + 32, ... in order, then a fixed xor-shuffle tree
+// (columns of popular candidates hold thousands of entries)
 __global__ void sparse_colstats_kernel(const float* __restrict__ cval, const int64_t* __restrict__ cptr, int N, int L,
                                        int K, const float* __restrict__ c, const float* __restrict__ phi,
                                        const float* __restrict__ rdiag, float* __restrict__ b, float* __restrict__ tpart) {
-    const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t idx = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (j >= N) return;
-    const int64_t e0 = cptr[j], e1 = cptr[j + 1];
-    const int64_t NK = (int64_t)N * K;
-    for (int l0 = 0; l0 < L; l0 += kColLevels) {
-        float P[kColLevels];
-#pragma unroll
-        for (int u = 0; u < kColLevels; ++u) P[u] = 0.f;
-        for (int64_t e = e0 + lane; e < e1; e += 32) {
-#pragma unroll
-            for (int u = 0; u < kColLevels; ++u)
-                if (l0 + u < L) P[u] = __fadd_rn(P[u], __ldcs(cval + (int64_t)(l0 + u) * NK + e));
-        }
-#pragma unroll
-        for (int u = 0; u < kColLevels; ++u) {
-            for (int o = 16; o > 0; o >>= 1) P[u] = __fadd_rn(P[u], __shfl_xor_sync(0xffffffffu, P[u], o));
-            const int l = l0 + u;
-            if (lane == 0 && l < L) {
-                const int64_t idx = (int64_t)l * N + j;
-                const float rd = rdiag[idx];
-                b[idx] = __fadd_rn(__fadd_rn(__fadd_rn(c[idx], phi[idx]), rd), P[u]);
-                if (l + 1 < L) tpart[idx + N] = __fadd_rn(rd, P[u]);
-            }
-        }
+    if (idx >= (int64_t)L * N) return;
+    const int l = (int)(idx / N);
+    const int64_t j = idx - (int64_t)l * N;
+    const float* v = cval + (int64_t)l * N * K;
+    float P = 0.f;
+    for (int64_t e = cptr[j] + lane; e < cptr[j + 1]; e += 32) P = __fadd_rn(P, __ldcs(v + e));
+    for (int o = 16; o > 0; o >>= 1) P = __fadd_rn(P, __shfl_xor_sync(0xffffffffu, P, o));
+    if (lane == 0) {
+        const float rd = rdiag[idx];
+        b[idx] = __fadd_rn(__fadd_rn(__fadd_rn(c[idx], phi[idx]), rd), P);
+        if (l + 1 < L) tpart[idx + N] = __fadd_rn(rd, P);
     }
 }
 
@@ -627,7 +613,7 @@ int hap_sparse_iterate(hap_sparse* h, int n) {
         SCU(cudaMemsetAsync(h->cval, 0, (size_t)h->L * h->N * h->K * 4, h->stream));
         sparse_rowpass_kernel<<<grid, 256, 0, h->stream>>>(a);
         SCU(cudaGetLastError());
-        const int64_t tot = (int64_t)h->N * 32;
+        const int64_t tot = (int64_t)h->L * h->N * 32;
         sparse_colstats_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, h->stream>>>(
             h->cval, h->cptr, h->N, h->L, h->K, h->c, h->phi, h->rdiag, h->b, h->tpart);
         SCU(cudaGetLastError());
