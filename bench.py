@@ -39,9 +39,10 @@ BATCHED = {"c3": (256, 32, 200, "256 instances, N uniform in [200, 4000], L unif
                                "(5-50 components), S built BF16 hi/lo split, one persistent launch per iteration "
                                "in a CUDA graph, 200 iterations")}
 LEARNED = {"c4": (262144, 32, 3, 64, 400,
-                  "N=262144 d=32 1024-component GMM, L=3, K=64 candidates per row: itself, its 32 nearest "
-                  "neighbours and its nearest hubs (the N/64 points the MLP proposal scores highest; trained on "
+                  "N=262144 d=32 1024-component GMM, L=3, K=64 candidates per row: itself, its 4 nearest "
+                  "neighbours and its 59 nearest hubs (the N/16 points the MLP proposal scores highest; trained on "
                   "dense HAP labels of two N=8192 instances), sparse HAP 400 iterations, c fixed, lambda 0.9")}
+HUB_DIV, K_NEAR = 16, 4  # hubs = N / HUB_DIV; nearest neighbours kept besides the hubs
 CPU_SAMPLE_N = 4096
 
 
@@ -455,7 +456,7 @@ def run_learned(args, world, rank, local):
     N, d, L, K, T, desc = LEARNED[args.workload]
     if args.iters:
         T = args.iters
-    lam, M, F = 0.9, 32, 16
+    lam, M, F = 0.9, 16, 16  # kNN pool of 16 (the features use all 16 distances)
 
     def instance(n, seed):
         X, lab = W.gmm_points(n, d, max(1, n // 256), sigma=1.0, seed=seed, means="normal", mean_scale=2.0)
@@ -499,7 +500,7 @@ def run_learned(args, world, rank, local):
         if score == "mlp":
             pool, dist_ = hap.knn(Xt, M)
             f, _ = hap.knn_features(dist_, F)
-            hubs = hap.top_scores(mlp.forward(f), n // 64)
+            hubs = hap.top_scores(mlp.forward(f), n // HUB_DIV)
             hubnn, _ = hap.knn_subset(Xt, hubs, K)
             cand = hap.select_hub_candidates(pool, hubnn, K, k_near)
         else:
@@ -523,7 +524,7 @@ def run_learned(args, world, rank, local):
         ns_d = hap.net_similarity_points(Xjt, e_d, ptj)
         ed = e_d.cpu().numpy()
         judge = {"n": args.judge_n, "dense_exemplars_level1": int(len(np.unique(ed[0])))}
-        for name, sc, kn in (("learned", "mlp", M), ("knn", None, K - 1)):
+        for name, sc, kn in (("learned", "mlp", K_NEAR), ("knn", None, K - 1)):
             e_s, ns_s = sparse_solve(Xjt, pj, sc, kn, T)
             es = e_s.cpu().numpy()
             judge[name] = {"ns_gap_level1": float((ns_d[0] - ns_s[0]) / abs(ns_d[0])),
@@ -546,8 +547,8 @@ def run_learned(args, world, rank, local):
     def step(e_buf):
         pool, dist_ = hap.knn(Xt, M)
         f, _ = hap.knn_features(dist_, F)
-        hubnn, _ = hap.knn_subset(Xt, hap.top_scores(mlp.forward(f), N // 64), K)
-        sp.set_candidates(hap.select_hub_candidates(pool, hubnn, K, M), Xt)
+        hubnn, _ = hap.knn_subset(Xt, hap.top_scores(mlp.forward(f), N // HUB_DIV), K)
+        sp.set_candidates(hap.select_hub_candidates(pool, hubnn, K, K_NEAR), Xt)
         sp.iterate(T)
         sp.exemplars(e_buf)
         return sp.net_similarity()
