@@ -197,6 +197,13 @@ int hap_exemplars(hap_ctx* ctx, int32_t* e, int on_host);
  * ns: host double [L].  Synchronising. */
 int hap_net_similarity(hap_ctx* ctx, double* ns);
 
+/* Acceptance check of the current assignment (Eq. 2.8; the paper prints no
+ * convergence test, it runs a fixed count): per level, the number of points
+ * whose exemplar is its own exemplar (e_{e_i} = e_i, all N at a
+ * self-consistent fixed point) and the number of exemplars (e_i = i).
+ * consistent, exemplars: host int64 [L], either may be NULL.  Synchronising. */
+int hap_acceptance(hap_ctx* ctx, int64_t* consistent, int64_t* exemplars);
+
 /* Reads the messages after hap_query(HAP_Q_ITER) iterations.
  *   A, R  device float [L][N][N] (alpha, rho), either may be NULL
  *   vecs  device float [3][L][N]: c, tau, phi; may be NULL

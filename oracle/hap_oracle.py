@@ -432,6 +432,17 @@ def adjusted_rand_index(a, b) -> float:
     return float((sum_ij - expected) / (max_index - expected))
 
 
+def acceptance(e):
+    """Acceptance check of an assignment (Eq. 2.8), per level: the number of
+    points whose exemplar is its own exemplar (e[e_i] == e_i) and the number
+    of exemplars (e_i == i)."""
+    e = np.atleast_2d(np.asarray(e))
+    idx = np.arange(e.shape[1])
+    cons = np.array([int(np.sum(el[el] == el)) for el in e])
+    ex = np.array([int(np.sum(el == idx)) for el in e])
+    return cons, ex
+
+
 def purity(labels, truth) -> float:
     """Purity, the extrinsic cluster-quality measure of §4: the fraction of
     points that carry the most frequent true class of their cluster,

@@ -34,6 +34,7 @@ struct hap_ctx {
     float *tpart = nullptr, *b = nullptr, *rdiag = nullptr, *partials = nullptr;
     int32_t* e = nullptr;
     double* ns = nullptr;
+    long long* acc = nullptr;
     unsigned* status = nullptr;
     int64_t s_level_stride = 0;
     int s_levels = 1;
@@ -54,7 +55,7 @@ constexpr size_t kAlign = 256;
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
-    size_t A, R, xs, S, pref, c, c0, tau, phi, tpart, b, rdiag, partials, e, ns, status, total;
+    size_t A, R, xs, S, pref, c, c0, tau, phi, tpart, b, rdiag, partials, e, ns, acc, status, total;
 };
 
 // d up to which the tensor-core build always finds operand scratch in the
@@ -189,6 +190,7 @@ Layout make_layout(int64_t N, int L, const hap_options& o, const LaunchShape& sh
     y.partials = take((size_t)sh.G * L * ld * sizeof(float));
     y.e = take((size_t)L * N * sizeof(int32_t));
     y.ns = take((size_t)L * sizeof(double));
+    y.acc = take((size_t)2 * L * sizeof(long long));
     y.status = take(4 * sizeof(unsigned));
     y.total = off;
     return y;
@@ -332,6 +334,7 @@ int hap_create(int64_t N, int L, const float* prefs, float damping, const hap_op
     h->partials = reinterpret_cast<float*>(base + y.partials);
     h->e = reinterpret_cast<int32_t*>(base + y.e);
     h->ns = reinterpret_cast<double*>(base + y.ns);
+    h->acc = reinterpret_cast<long long*>(base + y.acc);
     h->status = reinterpret_cast<unsigned*>(base + y.status);
     h->s_levels = o.s_per_level ? L : 1;
     h->s_level_stride = o.s_per_level ? N * h->ld : 0;
@@ -583,6 +586,22 @@ int hap_net_similarity(hap_ctx* h, double* ns) {
     h->launches += 2;
     CU(cudaMemcpyAsync(ns, h->ns, (size_t)h->L * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     return hap_sync(h);
+}
+
+int hap_acceptance(hap_ctx* h, int64_t* consistent, int64_t* exemplars) {
+    if (!h) return HAP_EINVAL;
+    CU(launch_exemplars(h->A, h->R, h->b, h->pending, h->lam, 1.0f - h->lam, h->N, h->ld, h->L, h->e, h->stream));
+    CU(launch_acceptance(h->e, h->N, h->L, h->acc, h->stream));
+    h->launches += 2;
+    std::vector<long long> host((size_t)2 * h->L);
+    CU(cudaMemcpyAsync(host.data(), h->acc, host.size() * sizeof(long long), cudaMemcpyDeviceToHost, h->stream));
+    int rc = hap_sync(h);
+    if (rc) return rc;
+    for (int l = 0; l < h->L; ++l) {
+        if (consistent) consistent[l] = host[l];
+        if (exemplars) exemplars[l] = host[h->L + l];
+    }
+    return HAP_OK;
 }
 
 int hap_get_state(hap_ctx* h, float* A, float* R, float* vecs, int64_t* iter) {

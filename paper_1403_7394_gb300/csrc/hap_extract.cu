@@ -87,6 +87,35 @@ __global__ void netsim_kernel(const ST* __restrict__ S, int64_t s_level_stride, 
     if (threadIdx.x == 0) ns[l] = part[0];
 }
 
+// Acceptance check of an assignment (Eq. 2.8), one CTA per level: points
+// whose exemplar is its own exemplar (e_{e_i} = e_i) and exemplars (e_i = i);
+// integer counts, exact in any order.
+__global__ void acceptance_kernel(const int32_t* __restrict__ e, int64_t N, long long* __restrict__ out) {
+    __shared__ long long part[2][1024];
+    const int l = blockIdx.x;
+    const int32_t* el = e + (int64_t)l * N;
+    long long cons = 0, ex = 0;
+    for (int64_t i = threadIdx.x; i < N; i += blockDim.x) {
+        const int32_t ej = el[i];
+        cons += (ej >= 0 && ej < N && el[ej] == ej) ? 1 : 0;
+        ex += (ej == i) ? 1 : 0;
+    }
+    part[0][threadIdx.x] = cons;
+    part[1][threadIdx.x] = ex;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            part[0][threadIdx.x] += part[0][threadIdx.x + o];
+            part[1][threadIdx.x] += part[1][threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[l] = part[0][0];
+        out[gridDim.x + l] = part[1][0];
+    }
+}
+
 // Similarity copy with type conversion (FP32 <-> BF16, round to nearest).
 template <typename DT, typename ST>
 __global__ void copy_similarity_kernel(DT* __restrict__ dst, int64_t ld, const ST* __restrict__ src,
@@ -179,6 +208,11 @@ cudaError_t launch_netsim(const void* S, int s_bf16, int64_t s_level_stride, con
         netsim_kernel<__nv_bfloat16><<<L, 1024, 0, st>>>(static_cast<const __nv_bfloat16*>(S), s_level_stride, pref, e, N, ld, ns);
     else
         netsim_kernel<float><<<L, 1024, 0, st>>>(static_cast<const float*>(S), s_level_stride, pref, e, N, ld, ns);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_acceptance(const int32_t* e, int64_t N, int L, long long* out, cudaStream_t st) {
+    acceptance_kernel<<<L, 1024, 0, st>>>(e, N, out);
     return cudaGetLastError();
 }
 

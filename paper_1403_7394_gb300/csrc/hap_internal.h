@@ -96,6 +96,8 @@ cudaError_t launch_exemplars(const float* A, const float* R, const float* b, int
 cudaError_t launch_materialize_A(float* dst, const float* A, const float* R, const float* b,
                                  int pending, float lam, float oml, int64_t N, int64_t ld, int L,
                                  cudaStream_t st);
+// out: [2][L] counts, self-consistent points then exemplars per level
+cudaError_t launch_acceptance(const int32_t* e, int64_t N, int L, long long* out, cudaStream_t st);
 cudaError_t launch_netsim(const void* S, int s_bf16, int64_t s_level_stride, const float* pref,
                           const int32_t* e, int64_t N, int64_t ld, int L, double* ns,
                           cudaStream_t st);

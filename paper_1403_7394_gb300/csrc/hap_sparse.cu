@@ -60,18 +60,35 @@ __global__ void __launch_bounds__(256) sparse_rowpass_kernel(const SparseArgs p)
     const int K = p.K, L = p.L, N = p.N;
     const int64_t NK = (int64_t)N * K;
     const bool pending = p.pending != 0;
-    for (int64_t i = wid; i < N; i += nw) {
-        int jq[2], pq[2];
-        float sq[2];
-        bool has[2];
+    bool has[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) has[h] = lane + 32 * h < K;
+    // the next row's candidates, CSC slots and similarities load while this
+    // row's levels run
+    int njq[2] = {0x7fffffff, 0x7fffffff}, npq[2] = {0, 0};
+    float nsq[2] = {0.f, 0.f};
+    auto load_row = [&](int64_t r) {
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int q = lane + 32 * h;
-            has[h] = q < K;
-            jq[h] = has[h] ? p.cand[i * K + q] : 0x7fffffff;
-            pq[h] = has[h] ? p.pos[i * K + q] : 0;
-            sq[h] = has[h] ? p.s[i * K + q] : 0.f;
+            if (has[h] && r < N) {
+                njq[h] = p.cand[r * K + q];
+                npq[h] = p.pos[r * K + q];
+                nsq[h] = p.s[r * K + q];
+            }
         }
+    };
+    load_row(wid);
+    for (int64_t i = wid; i < N; i += nw) {
+        int jq[2], pq[2];
+        float sq[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            jq[h] = has[h] ? njq[h] : 0x7fffffff;
+            pq[h] = npq[h];
+            sq[h] = nsq[h];
+        }
+        load_row(i + nw);
         // level 0's messages; later levels are loaded one level ahead
         float a[2], r[2], bb[2];
 #pragma unroll
@@ -148,26 +165,81 @@ __global__ void __launch_bounds__(256) sparse_rowpass_kernel(const SparseArgs p)
 }
 
 // P_j = sum over the column's entries (rows k != j) of max(0, rho), read from
-// the CSC-ordered values the row pass wrote: one warp per (level, column);
-// lane t sums slots t, t + 32, ... in order, then a fixed xor-shuffle tree
-// (columns of popular candidates hold thousands of entries)
-__global__ void sparse_colstats_kernel(const float* __restrict__ cval, const int64_t* __restrict__ cptr, int N, int L,
-                                       int K, const float* __restrict__ c, const float* __restrict__ phi,
-                                       const float* __restrict__ rdiag, float* __restrict__ b, float* __restrict__ tpart) {
-    const int64_t idx = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (idx >= (int64_t)L * N) return;
-    const int l = (int)(idx / N);
-    const int64_t j = idx - (int64_t)l * N;
+// the CSC-ordered values the row pass wrote.  Columns with at most
+// kShortCol entries (most of them: a point is the candidate of a few
+// neighbours) are summed in entry order by one thread; longer ones (hubs,
+// thousands of entries) by one warp: lane t sums slots t, t + 32, ... in
+// order, then a fixed xor-shuffle tree.  The split depends only on the
+// column's length, so every sum has a fixed order.
+constexpr int kShortCol = 32;
+
+HAP_DEV void colstats_finish(int64_t idx, int l, int L, int N, float P, const float* __restrict__ c,
+                             const float* __restrict__ phi, const float* __restrict__ rdiag, float* __restrict__ b,
+                             float* __restrict__ tpart) {
+    const float rd = rdiag[idx];
+    b[idx] = __fadd_rn(__fadd_rn(__fadd_rn(c[idx], phi[idx]), rd), P);
+    if (l + 1 < L) tpart[idx + N] = __fadd_rn(rd, P);
+}
+
+__global__ void sparse_colstats_short_kernel(const float* __restrict__ cval, const int64_t* __restrict__ cptr,
+                                             const int32_t* __restrict__ cols, int ncols, int N, int L, int K,
+                                             const float* __restrict__ c, const float* __restrict__ phi,
+                                             const float* __restrict__ rdiag, float* __restrict__ b,
+                                             float* __restrict__ tpart) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)L * ncols) return;
+    const int l = (int)(t / ncols);
+    const int64_t j = cols[t - (int64_t)l * ncols];
     const float* v = cval + (int64_t)l * N * K;
     float P = 0.f;
-    for (int64_t e = cptr[j] + lane; e < cptr[j + 1]; e += 32) P = __fadd_rn(P, __ldcs(v + e));
-    for (int o = 16; o > 0; o >>= 1) P = __fadd_rn(P, __shfl_xor_sync(0xffffffffu, P, o));
-    if (lane == 0) {
-        const float rd = rdiag[idx];
-        b[idx] = __fadd_rn(__fadd_rn(__fadd_rn(c[idx], phi[idx]), rd), P);
-        if (l + 1 < L) tpart[idx + N] = __fadd_rn(rd, P);
+    for (int64_t e = cptr[j]; e < cptr[j + 1]; ++e) P = __fadd_rn(P, __ldcs(v + e));
+    colstats_finish((int64_t)l * N + j, l, L, N, P, c, phi, rdiag, b, tpart);
+}
+
+__global__ void sparse_colstats_long_kernel(const float* __restrict__ cval, const int64_t* __restrict__ cptr,
+                                            const int32_t* __restrict__ cols, int ncols, int N, int L, int K,
+                                            const float* __restrict__ c, const float* __restrict__ phi,
+                                            const float* __restrict__ rdiag, float* __restrict__ b,
+                                            float* __restrict__ tpart) {
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= (int64_t)L * ncols) return;
+    const int l = (int)(w / ncols);
+    const int64_t j = cols[w - (int64_t)l * ncols];
+    const float* v = cval + (int64_t)l * N * K;
+    float P = 0.f;
+    const int64_t e1 = cptr[j + 1];
+    int64_t e = cptr[j] + lane;
+    // eight loads in flight, added in slot order
+    for (; e + 7 * 32 < e1; e += 8 * 32) {
+        float x[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) x[u] = __ldcs(v + e + 32 * u);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) P = __fadd_rn(P, x[u]);
     }
+    for (; e < e1; e += 32) P = __fadd_rn(P, __ldcs(v + e));
+    for (int o = 16; o > 0; o >>= 1) P = __fadd_rn(P, __shfl_xor_sync(0xffffffffu, P, o));
+    if (lane == 0) colstats_finish((int64_t)l * N + j, l, L, N, P, c, phi, rdiag, b, tpart);
+}
+
+// Column classes: flag[j] = 1 for a long column; after the prefix sums the
+// columns of each class are listed in increasing order.
+__global__ void column_class_kernel(const int* __restrict__ cnt, int N, int* __restrict__ is_long,
+                                    int* __restrict__ is_short) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j > N) return;
+    const int lg = (j < N && cnt[j] > kShortCol) ? 1 : 0;
+    is_long[j] = lg;
+    is_short[j] = (j < N) ? 1 - lg : 0;
+}
+__global__ void column_compact_kernel(const int* __restrict__ is_long, const int* __restrict__ long_pos,
+                                      const int* __restrict__ short_pos, int N, int32_t* __restrict__ long_cols,
+                                      int32_t* __restrict__ short_cols) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= N) return;
+    if (is_long[j]) long_cols[long_pos[j]] = j;
+    else short_cols[short_pos[j]] = j;
 }
 
 // ---- candidate graph on the GPU: checks, column index (CSC) -----------------
@@ -432,6 +504,10 @@ struct hap_sparse {
     float* cval = nullptr;        // [L][N*K] max(0, rho) in CSC order
     int32_t* tmp[4] = {nullptr, nullptr, nullptr, nullptr};  // radix-sort key / value buffers
     int* cnt = nullptr;           // [N + 1] column counts
+    int* cls = nullptr;           // [4][N + 1] column-class flags and positions
+    int32_t* long_cols = nullptr; // columns with more than kShortCol entries, increasing
+    int32_t* short_cols = nullptr;
+    int n_long = 0, n_short = 0;
     int* hist = nullptr;          // radix histograms, then their offsets
     int* hoff = nullptr;
     int64_t* tsum = nullptr;      // scan tile sums
@@ -501,7 +577,10 @@ int hap_sparse_create(int64_t N, int L, int K, const float* prefs, float damping
               cudaMalloc(&h->cptr, (N + 1) * 8) == cudaSuccess && cudaMalloc(&h->cent, nk * 4) == cudaSuccess &&
               cudaMalloc(&h->e, (size_t)L * N * 4) == cudaSuccess && cudaMalloc(&h->ns, (size_t)L * 8) == cudaSuccess &&
               cudaMalloc(&h->status, 16) == cudaSuccess && cudaMalloc(&h->pos, nk * 4) == cudaSuccess &&
-              cudaMalloc(&h->cval, mat) == cudaSuccess && cudaMalloc(&h->cnt, (N + 1) * 4) == cudaSuccess;
+              cudaMalloc(&h->cval, mat) == cudaSuccess && cudaMalloc(&h->cnt, (N + 1) * 4) == cudaSuccess &&
+              cudaMalloc(&h->cls, (size_t)4 * (N + 1) * 4) == cudaSuccess &&
+              cudaMalloc(&h->long_cols, (size_t)N * 4) == cudaSuccess &&
+              cudaMalloc(&h->short_cols, (size_t)N * 4) == cudaSuccess;
     const int64_t nhist = (int64_t)kRadixBins * radix_chunks((int64_t)nk);
     const int64_t ntiles = (std::max<int64_t>(nhist, N + 1) + kScanTile - 1) / kScanTile;
     for (int q = 0; q < 4 && ok; ++q) ok = cudaMalloc(&h->tmp[q], nk * 4) == cudaSuccess;
@@ -528,6 +607,7 @@ void hap_sparse_destroy(hap_sparse* h) {
     cudaFree(h->c0); cudaFree(h->tau); cudaFree(h->phi); cudaFree(h->tpart); cudaFree(h->b); cudaFree(h->rdiag);
     cudaFree(h->cptr); cudaFree(h->cent); cudaFree(h->e); cudaFree(h->ns); cudaFree(h->status);
     cudaFree(h->pos); cudaFree(h->cval); cudaFree(h->cnt); cudaFree(h->hist); cudaFree(h->hoff); cudaFree(h->tsum);
+    cudaFree(h->cls); cudaFree(h->long_cols); cudaFree(h->short_cols);
     for (int q = 0; q < 4; ++q) cudaFree(h->tmp[q]);
     delete h;
 }
@@ -559,6 +639,17 @@ int hap_sparse_set_candidates(hap_sparse* h, const int32_t* cand, const float* X
     sparse_check_count_kernel<<<(unsigned)((N * 32 + 255) / 256), 256, 0, st>>>(h->cand, (int)N, (int)K, h->status, h->cnt);
     SCU(cudaGetLastError());
     SCU(scan_exclusive<int64_t>(h->cnt, N + 1, h->cptr, h->tsum, st));
+    // columns by length class, each list in increasing column order
+    int* is_long = h->cls;
+    int* is_short = h->cls + (N + 1);
+    int* long_pos = h->cls + 2 * (N + 1);
+    int* short_pos = h->cls + 3 * (N + 1);
+    column_class_kernel<<<(unsigned)((N + 1 + 255) / 256), 256, 0, st>>>(h->cnt, (int)N, is_long, is_short);
+    SCU(scan_exclusive<int>(is_long, N + 1, long_pos, h->tsum, st));
+    SCU(scan_exclusive<int>(is_short, N + 1, short_pos, h->tsum, st));
+    column_compact_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(is_long, long_pos, short_pos, (int)N,
+                                                                       h->long_cols, h->short_cols);
+    SCU(cudaGetLastError());
     // entries sorted by column, stable: the CSC entry order
     int passes = 1;
     while (passes * kRadixBits < 31 && ((int64_t)1 << (passes * kRadixBits)) < N) ++passes;
@@ -580,10 +671,14 @@ int hap_sparse_set_candidates(hap_sparse* h, const int32_t* cand, const float* X
     inverse_perm_kernel<<<(unsigned)((nk + 255) / 256), 256, 0, st>>>(h->cent, nk, h->pos);
     sparse_similarity_kernel<<<(unsigned)((nk + 255) / 256), 256, 0, st>>>(X, d, h->cand, (int)N, (int)K, h->s);
     SCU(cudaGetLastError());
-    h->launches += 6 + 3 * passes + 3 * passes;
+    h->launches += 6 + 3 * passes + 3 * passes + 8;  // checks, scans, sort passes, classes, inverse map, s
     unsigned stw = 0;
+    int nl = 0;
     SCU(cudaMemcpyAsync(&stw, h->status, 4, cudaMemcpyDeviceToHost, st));
+    SCU(cudaMemcpyAsync(&nl, long_pos + N, 4, cudaMemcpyDeviceToHost, st));
     SCU(cudaStreamSynchronize(st));
+    h->n_long = nl;
+    h->n_short = (int)N - nl;
     if (stw & ST_BOUNDS) {
         SCU(cudaMemset(h->status, 0, 16));
         return HAP_EINVAL;
@@ -613,11 +708,18 @@ int hap_sparse_iterate(hap_sparse* h, int n) {
         SCU(cudaMemsetAsync(h->cval, 0, (size_t)h->L * h->N * h->K * 4, h->stream));
         sparse_rowpass_kernel<<<grid, 256, 0, h->stream>>>(a);
         SCU(cudaGetLastError());
-        const int64_t tot = (int64_t)h->L * h->N * 32;
-        sparse_colstats_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, h->stream>>>(
-            h->cval, h->cptr, h->N, h->L, h->K, h->c, h->phi, h->rdiag, h->b, h->tpart);
+        if (h->n_short > 0) {
+            const int64_t tot = (int64_t)h->L * h->n_short;
+            sparse_colstats_short_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, h->stream>>>(
+                h->cval, h->cptr, h->short_cols, h->n_short, h->N, h->L, h->K, h->c, h->phi, h->rdiag, h->b, h->tpart);
+        }
+        if (h->n_long > 0) {
+            const int64_t tot = (int64_t)h->L * h->n_long * 32;
+            sparse_colstats_long_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, h->stream>>>(
+                h->cval, h->cptr, h->long_cols, h->n_long, h->N, h->L, h->K, h->c, h->phi, h->rdiag, h->b, h->tpart);
+        }
         SCU(cudaGetLastError());
-        h->launches += 2;
+        h->launches += 1 + (h->n_short > 0) + (h->n_long > 0);
         h->pending = true;
         h->iter = t;
     }

@@ -74,6 +74,7 @@ def _load():
         "hap_batch_query": (i32, [vp, i32, ctypes.POINTER(i64)]),
         "hap_batch_sync": (i32, [vp]),
         "hap_knn": (i32, [vp, i64, i64, i32, vp, vp, vp]),
+        "hap_acceptance": (i32, [vp, vp, vp]),
         "hap_knn_with": (i32, [vp, i64, i64, i32, i32, vp, vp, vp]),
         "hap_proposal_launches": (i64, []),
         "hap_knn_subset_with": (i32, [vp, i64, i64, vp, i64, i32, i32, vp, vp, vp]),
@@ -250,6 +251,15 @@ class HAP:
         ns = np.zeros(self.L, dtype=np.float64)
         check(lib.hap_net_similarity(self._h, ns.ctypes.data_as(ctypes.c_void_p)), "hap_net_similarity")
         return ns
+
+    def acceptance(self):
+        """(self-consistent points, exemplars) per level of the current assignment."""
+        import numpy as np
+        cons = np.zeros(self.L, dtype=np.int64)
+        ex = np.zeros(self.L, dtype=np.int64)
+        check(lib.hap_acceptance(self._h, cons.ctypes.data_as(ctypes.c_void_p), ex.ctypes.data_as(ctypes.c_void_p)),
+              "hap_acceptance")
+        return cons, ex
 
     def get_state(self):
         A = torch.empty((self.L, self.N, self.N), dtype=torch.float32, device=self.device)

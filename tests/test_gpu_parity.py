@@ -233,6 +233,21 @@ def test_exemplars_and_net_similarity_from_gpu_state():
     np.testing.assert_array_equal(ctx.exemplars(host).numpy(), e_gpu)
 
 
+def test_acceptance_check(report):
+    """Self-consistency and exemplar counts on the GPU equal the reference's
+    on the same assignment; a converged run is self-consistent."""
+    N, L, lam = 900, 2, 0.9
+    S32, prefs, S_ref = problem(N, L, seed=13)
+    ctx = make_ctx(N, L, prefs, lam, S32, c_mode="fixed")
+    ctx.iterate(300)
+    e = ctx.exemplars().cpu().numpy()
+    cons, ex = ctx.acceptance()
+    rc, rx = H.acceptance(e)
+    report(consistent=cons.tolist(), exemplars=ex.tolist())
+    assert np.array_equal(cons, rc) and np.array_equal(ex, rx)
+    assert cons[0] == N and ex[0] == len(np.unique(e[0]))
+
+
 def test_bitwise_determinism_and_resume():
     N, L, lam = 1200, 3, 0.5
     S32, prefs, _ = problem(N, L, seed=21)

@@ -350,3 +350,10 @@ def test_purity():
     assert H.purity(np.arange(6), truth) == 1.0
     assert H.purity(np.zeros(6), truth) == 3 / 6
     assert H.purity(np.array([5, 5, 5, 7, 7, 7]), truth) == (2 + 3) / 6
+
+
+def test_acceptance_counts():
+    """Hand examples: [1, 1, 2, 1] is self-consistent with exemplars 1 and 2;
+    in [1, 2, 2, 0] points 0 and 3 point at non-exemplars."""
+    cons, ex = H.acceptance(np.array([[1, 1, 2, 1], [1, 2, 2, 0]]))
+    assert list(cons) == [4, 2] and list(ex) == [2, 1]
