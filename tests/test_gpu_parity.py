@@ -318,6 +318,67 @@ def test_similarity_build_tensor_cores(mode, N, d, s_dtype, report):
     assert np.all(np.diagonal(S) == -5.0)
 
 
+# ----------------------------------------------------------- degenerate / max
+@pytest.mark.parametrize("c_mode", ["paper", "fixed"])
+def test_all_ties(c_mode, report):
+    """Identical points (every off-diagonal similarity 0, the preference 0 at
+    level 1): every maximum is attained many times, so the lowest-index rule
+    (reading R7) decides; the GPU follows the reference free-running."""
+    N, L, lam = 300, 2, 0.5
+    S32 = np.zeros((N, N), dtype=np.float32)
+    prefs = np.array([0.0, -1.0], dtype=np.float32)
+    S_ref = H.level_similarities(S32.astype(np.float64), prefs.astype(np.float64))
+    ctx = make_ctx(N, L, prefs, lam, S32, c_mode=c_mode)
+    st = H.init_state(L, N)
+    for t in range(1, 9):
+        ctx.iterate(1)
+        st = H.step(S_ref, st, lam, c_mode)
+    errs = assert_close(gpu_state(ctx), st)
+    e = ctx.exemplars().cpu().numpy()
+    np.testing.assert_array_equal(e, H.exemplars(st.A, st.R))
+    report(errs=errs, exemplars=[int(len(np.unique(x))) for x in e])
+
+
+def test_maximum_size(report):
+    """The largest N a context takes (65536, L = 1, S from points on the
+    tensor cores, clusters of 8 CTAs holding a 65536-column row): one
+    iteration from the GPU's own state at t = 2, rho on sampled rows against
+    Eq. 2.1 and alpha against Eqs. 2.2/2.3 with the column sums of the GPU's
+    new rho streamed to the host in row blocks."""
+    hap = hap_mod()
+    N, L, lam, chunk = 65536, 1, 0.5, 1024
+    X, _ = W.gmm_points(N, 8, 64, sigma=1.0, seed=77, means="normal", mean_scale=2.0)
+    X32 = X.astype(np.float32)
+    prefs = np.array([median_pref(X32)], dtype=np.float32)
+    ctx = hap.HAP(N, L, prefs=prefs, damping=lam, device=DEV, c_mode="fixed")
+    ctx.build_similarity(torch.from_numpy(X32).to(DEV), mode="bf16_split")
+    ctx.iterate(2)
+    rows = np.sort(np.random.default_rng(5).choice(N, 16, replace=False))
+    rows_t = torch.from_numpy(rows).to(DEV)
+    host = lambda t: t.cpu().numpy().astype(np.float64)
+    g0 = ctx.get_state()
+    A0r, R0r = host(g0["A"][0][rows_t]), host(g0["R"][0][rows_t])
+    c0 = host(g0["c"][0])
+    del g0
+    Sr = host(ctx.get_similarity(0)[rows_t])
+    Sr[np.arange(rows.size), rows] = prefs[0]
+    ctx.iterate(1)
+    g1 = ctx.get_state()
+    P1 = np.zeros(N)
+    for r0 in range(0, N, chunk):
+        blk = np.arange(r0, min(N, r0 + chunk))
+        P1 += H.row_block_column_sums(host(g1["R"][0, r0:r0 + blk.size]), blk)
+    Rd1 = host(torch.diagonal(g1["R"][0]))
+    Rn = H.responsibility_update(Sr, A0r, R0r, np.full(rows.size, np.inf), lam)
+    R1r = host(g1["R"][0][rows_t])
+    An = H.availability_update(A0r, R1r, rows, c0, np.zeros(N), Rd1, P1, lam)
+    errs = {"R": H.message_rel_error(R1r, Rn), "A": H.message_rel_error(host(g1["A"][0][rows_t]), An)}
+    report(shape=ctx.shape, errs=errs)
+    assert all(e <= TOL for e in errs.values()), errs
+    assert ctx.shape["ld"] == 65536 and ctx.shape["cluster_size"] == 8
+    ctx.close()
+
+
 # ----------------------------------------------------------------- errors
 def test_error_codes():
     hap = hap_mod()
