@@ -246,8 +246,6 @@ constexpr int KT_PEND = 32;     // per-row buffer of threshold-passing candidate
 constexpr int KT_THREADS = 192; // 4 epilogue warps, 1 producer warp, 1 MMA warp
 
 struct KnnTcArgs {
-    const float* qnorm;   // [Nq] query norms
-    const float* cnorm;   // [ncpad] candidate norms (0 beyond Nc)
     const int32_t* cid;   // candidate j's global id (null: j)
     int Nq, Nc, M2, kchunks, ring;
     int32_t* cand;        // out [Nq][M2] candidate columns, -1 where fewer
@@ -624,9 +622,8 @@ cudaError_t launch_knn_tc(const float* Q, int64_t Nq, const float* C, const int3
     const int64_t kpad = (3 * d + 2 + BK - 1) / BK * BK;
     const int64_t qpad = (Nq + BM - 1) / BM * BM, cpad = (Nc + BN - 1) / BN * BN;
     const size_t aB = (size_t)qpad * kpad * 2, bB = (size_t)cpad * kpad * 2;
-    const size_t off_b = (aB + 1023) / 1024 * 1024, off_qn = off_b + (bB + 1023) / 1024 * 1024;
-    const size_t off_cn = off_qn + ((size_t)qpad * 4 + 255) / 256 * 256;
-    const size_t off_cand = off_cn + ((size_t)cpad * 4 + 255) / 256 * 256;
+    const size_t off_b = (aB + 1023) / 1024 * 1024;
+    const size_t off_cand = off_b + (bB + 1023) / 1024 * 1024;
     const size_t off_status = off_cand + ((size_t)Nq * M2 * 4 + 255) / 256 * 256;
     const size_t total = off_status + 256 + 1024;
     char* raw = nullptr;
@@ -635,8 +632,6 @@ cudaError_t launch_knn_tc(const float* Q, int64_t Nq, const float* C, const int3
     char* base = reinterpret_cast<char*>(((uintptr_t)raw + 1023) & ~(uintptr_t)1023);
     __nv_bfloat16* A = reinterpret_cast<__nv_bfloat16*>(base);
     __nv_bfloat16* B = reinterpret_cast<__nv_bfloat16*>(base + off_b);
-    float* qn = reinterpret_cast<float*>(base + off_qn);
-    float* cn = reinterpret_cast<float*>(base + off_cn);
     int32_t* cand = reinterpret_cast<int32_t*>(base + off_cand);
     unsigned* status = reinterpret_cast<unsigned*>(base + off_status);
     do {
@@ -651,8 +646,6 @@ cudaError_t launch_knn_tc(const float* Q, int64_t Nq, const float* C, const int3
             break;
         }
         KnnTcArgs a;
-        a.qnorm = qn;
-        a.cnorm = cn;
         a.cid = cid;
         a.Nq = (int)Nq;
         a.Nc = (int)Nc;
