@@ -27,7 +27,7 @@ namespace hap {
 namespace {
 
 constexpr int BM = 128, BN = 128, BK = 64;  // tile and K-chunk (64 BF16 = 128 bytes)
-constexpr int kRing = 3;                     // K-chunk stages in shared memory
+constexpr int kRing = 2;                     // K-chunk stages in shared memory (3 CTAs per SM)
 constexpr uint32_t kChunkBytes = (BM + BN) * BK * 2;
 constexpr uint32_t kTmemCols = 128;
 
