@@ -151,3 +151,24 @@ def test_batch_many_items_per_cta(report):
         ctx.close()
     report(worst=worst, items_per_cta=bt.query(8))
     bt.close()
+
+
+def test_batch_bf16_storage():
+    """Batched instances with BF16-stored S equal single-instance runs with
+    BF16-stored S (the same rounding of s, the same arithmetic)."""
+    from paper_1403_7394_gb300 import hap
+    Ns, Ls = [700, 2300, 150], [3, 2, 4]
+    insts = _instances(Ns, Ls, seed=71)
+    bt = hap.HAPBatch(Ns, Ls, damping=0.5, device=DEV, s_dtype="bf16")
+    bt.set_preferences([x[2] for x in insts])
+    for b, (_, S32, _) in enumerate(insts):
+        bt.set_similarity(b, torch.from_numpy(S32).to(DEV))
+    bt.iterate(5)
+    for b, (_, S32, prefs) in enumerate(insts):
+        ctx = hap.HAP(Ns[b], Ls[b], prefs=prefs, damping=0.5, device=DEV, s_dtype="bf16")
+        ctx.set_similarity(torch.from_numpy(S32).to(DEV))
+        ctx.iterate(5)
+        errs = _errs(bt.get_state(b), ctx.get_state())
+        assert all(e <= TOL for e in errs.values()), (b, errs)
+        ctx.close()
+    bt.close()

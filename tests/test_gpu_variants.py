@@ -158,3 +158,35 @@ def test_variant_options_refused():
     with pytest.raises(hap.HapError) as ei:
         hap.HAPBatch([64, 100], [2, 3], device=DEV, schedule="gauss_seidel")
     assert ei.value.code == hap.HAP_EUNSUPPORTED
+
+
+def test_gauss_seidel_per_level_asymmetric_similarity(report):
+    """The sequential schedule with a separate non-metric S per level (§2)."""
+    hap = hap_mod()
+    N, L, lam = 500, 3, 0.5
+    mats = [problem(N, 1, seed=60 + l, asym=True)[0] for l in range(L)]
+    prefs = np.array([-30.0, -60.0, -90.0], dtype=np.float32)
+    S_ref = np.stack([m.astype(np.float64) for m in mats])
+    for l in range(L):
+        np.fill_diagonal(S_ref[l], prefs[l])
+    ctx = hap.HAP(N, L, prefs=prefs, damping=lam, device=DEV, s_per_level=True, schedule="gauss_seidel")
+    for l in range(L):
+        ctx.set_similarity(torch.from_numpy(mats[l]).to(DEV), level=l)
+    st = to32(H.run(S_ref, 3, lam, H.PAPER, schedule=H.GAUSS_SEIDEL))
+    st.phi = st.phi.astype(np.float32).astype(np.float64)
+    ctx.set_state(st.A, st.R, st.c, st.t, phi=st.phi)
+    ctx.iterate(2)
+    ref = H.step(S_ref, H.step(S_ref, st, lam, H.PAPER, H.GAUSS_SEIDEL), lam, H.PAPER, H.GAUSS_SEIDEL)
+    report(errs=assert_close(gpu_state(ctx), ref))
+
+
+def test_similarity_level_update_bf16_storage(report):
+    """Eq. 2.7 on a BF16-stored S (the chain runs in FP32 registers)."""
+    N, L, lam, kappa = 900, 3, 0.5, 0.5
+    S32, prefs, S_ref = problem(N, L, seed=35, s_dtype="bf16")
+    st = to32(H.run(S_ref, 3, lam, H.FIXED, kappa=kappa))
+    ctx = make_ctx(N, L, prefs, lam, S32, kappa=kappa, c_mode="fixed", s_dtype="bf16")
+    ctx.set_state(st.A, st.R, st.c, st.t)
+    ctx.iterate(2)
+    ref = H.step(S_ref, H.step(S_ref, st, lam, H.FIXED, kappa=kappa), lam, H.FIXED, kappa=kappa)
+    report(errs=assert_close(gpu_state(ctx), ref))
