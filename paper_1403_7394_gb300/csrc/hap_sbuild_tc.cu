@@ -81,25 +81,16 @@ HAP_DEV uint64_t desc_kmajor_sw128(uint32_t saddr) {
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 
 template <typename OT>
-HAP_DEV void store_row32(OT* dst, const float (&v)[32]);
+HAP_DEV void store4(OT* dst, float4 w);
 template <>
-HAP_DEV void store_row32<float>(float* dst, const float (&v)[32]) {
-#pragma unroll
-    for (int q = 0; q < 32; q += 4) *reinterpret_cast<float4*>(dst + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
-}
+HAP_DEV void store4<float>(float* dst, float4 w) { *reinterpret_cast<float4*>(dst) = w; }
 template <>
-HAP_DEV void store_row32<__nv_bfloat16>(__nv_bfloat16* dst, const float (&v)[32]) {
-#pragma unroll
-    for (int q = 0; q < 32; q += 8) {
-        uint4 u;
-        __nv_bfloat162 p0 = __floats2bfloat162_rn(v[q], v[q + 1]), p1 = __floats2bfloat162_rn(v[q + 2], v[q + 3]);
-        __nv_bfloat162 p2 = __floats2bfloat162_rn(v[q + 4], v[q + 5]), p3 = __floats2bfloat162_rn(v[q + 6], v[q + 7]);
-        u.x = *reinterpret_cast<uint32_t*>(&p0);
-        u.y = *reinterpret_cast<uint32_t*>(&p1);
-        u.z = *reinterpret_cast<uint32_t*>(&p2);
-        u.w = *reinterpret_cast<uint32_t*>(&p3);
-        *reinterpret_cast<uint4*>(dst + q) = u;
-    }
+HAP_DEV void store4<__nv_bfloat16>(__nv_bfloat16* dst, float4 w) {
+    __nv_bfloat162 p0 = __floats2bfloat162_rn(w.x, w.y), p1 = __floats2bfloat162_rn(w.z, w.w);
+    uint2 u;
+    u.x = *reinterpret_cast<uint32_t*>(&p0);
+    u.y = *reinterpret_cast<uint32_t*>(&p1);
+    *reinterpret_cast<uint2*>(dst) = u;
 }
 
 template <typename OT>
@@ -165,25 +156,42 @@ __global__ void __launch_bounds__(128, 1) sbuild_tc_kernel(const __grid_constant
     tc_fence_after();
 
     // ---- epilogue: warp w owns TMEM lanes (tile rows) 32w .. 32w+31 ---------
+    // Each 32 x 32 block goes through shared memory (the K-chunk ring is idle
+    // once every MMA has completed) so that one store instruction writes
+    // four full 128-byte row segments instead of 32 scattered 16-byte pieces.
     const int row = m0 + 32 * warp + lane;
     const float ni = row < N ? norms[row] : 0.f;
+    constexpr int kStg = 36;  // staging row stride in floats (16-byte aligned rows)
+    float* stg = reinterpret_cast<float*>(smem_raw + (base - raw)) + warp * 32 * kStg;
 #pragma unroll 1
     for (int cc = 0; cc < BN / 32; ++cc) {
         float v[32];
         tmem_ld_32x32b_x32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(32 * cc), v);
 #pragma unroll
         for (int q = 0; q < 32; ++q) v[q] = __fsub_rn(__fsub_rn(2.f * v[q], ni), col_norm[32 * cc + q]);
-        const int c0 = n0 + 32 * cc;
-        if (row < N) {
-            OT* dst = S + (int64_t)row * ld + c0;
-            if (c0 + 32 <= N) {
-                store_row32<OT>(dst, v);
-            } else {
 #pragma unroll
-                for (int q = 0; q < 32; ++q)
-                    if (c0 + q < N) dst[q] = (OT)v[q];
+        for (int q = 0; q < 32; q += 4)
+            *reinterpret_cast<float4*>(stg + lane * kStg + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+        __syncwarp();
+        const int c0 = n0 + 32 * cc;
+#pragma unroll
+        for (int rr = 0; rr < 8; ++rr) {
+            const int r = 4 * rr + (lane >> 3), col = 4 * (lane & 7);
+            const int grow = m0 + 32 * warp + r;
+            const float4 w = *reinterpret_cast<const float4*>(stg + r * kStg + col);
+            if (grow < N) {
+                OT* dst = S + (int64_t)grow * ld + c0 + col;
+                if (c0 + col + 4 <= N) {
+                    store4<OT>(dst, w);
+                } else {
+                    const float wv[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        if (c0 + col + q < N) dst[q] = (OT)wv[q];
+                }
             }
         }
+        __syncwarp();  // the staging block is rewritten by the next chunk
     }
     tc_fence_before();
     __syncthreads();
