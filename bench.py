@@ -646,9 +646,10 @@ def run_learned(args, world, rank, local):
     updates = float(N) * K * L * T
     value = world * args.steps * updates / (ms / 1e3)
     peaks, peak_src = measured_peaks()
-    # per sparse update: alpha, rho read + write (16 B), column statistics gather of rho + entry index (8 B);
-    # per row entry once per iteration: s and the candidate index (8 B / L)
-    bytes_it = float(N) * K * (L * 24 + 8)
+    # per sparse update: alpha, rho read + write (16 B); per row entry once per iteration: s, the candidate
+    # index and its column-index slot (12 B).  The column terms b (16 B per column, L2-resident), the
+    # positive responsibilities and their bitmap (a few per row) are not counted.
+    bytes_it = float(N) * K * (L * 16 + 12)
     achieved = bytes_it / (it_ms / 1e3) / 1e9
     line = {"metric": "hap_message_updates_per_s", "value": value, "unit": "updates/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,

@@ -388,6 +388,7 @@ int hap_sparse_net_similarity(hap_sparse* sp, double* ns);
 /* alpha, rho device [L][N][K] (entry q of row i is candidate cand[i][q]);
  * vecs device [3][L][N] (c, tau, phi).  Asynchronous. */
 int hap_sparse_get_state(hap_sparse* sp, float* A, float* R, float* vecs, int64_t* iter);
+/* keys HAP_Q_ITER and HAP_Q_LAUNCHES. */
 int hap_sparse_query(hap_sparse* sp, int key, int64_t* value);
 
 /* Net similarity of any assignment from the points: NS^l = sum_i

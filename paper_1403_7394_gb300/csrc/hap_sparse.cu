@@ -5,7 +5,10 @@
 // maximum and add max(0, rho) = 0 to every column sum.
 //
 // Layout: cand [N][K] int32, s [N][K] FP32 (= -||x_i - x_cand||^2, the
-// preference on the self entry), alpha and rho [L][N][K].  Row pass: one warp
+// preference on the self entry), alpha and rho [L][N][K], the column terms
+// b [N][4 ceil(L/4)] (all levels of a column in one 16-byte gather; the row
+// pass's gathers of b set its speed: one 32-byte sector per candidate per
+// gather).  Row pass: one warp
 // per row walks the L levels (alpha kept one step behind exactly as in the
 // dense row pass; the next level's alpha, rho and b are loaded while the
 // current level reduces).  The column index (CSC: for every column j the
@@ -14,7 +17,11 @@
 // positive off-diagonal responsibilities straight to their CSC slots (in a
 // buffer zeroed before the pass: most responsibilities are negative, so few
 // scattered writes), and the column statistics sum contiguous segments in a
-// fixed order.
+// fixed order.  Only the slots of positive responsibilities are ever read:
+// the row pass also sets the slot's bit in a per-level bitmap (zeroed before
+// the pass, 1/32 of the values' size), and the column statistics read the
+// bitmap and gather the values of set bits alone, so the CSC values are
+// neither zeroed nor swept.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -34,7 +41,9 @@ constexpr int SP_MAXK = 64;
 struct SparseArgs {
     const int32_t* cand;
     const int32_t* pos;    // [N][K] CSC slot of every entry
-    float* cval;           // [L][N*K] max(0, rho) in CSC order (0 on the diagonal), zeroed before the pass
+    float* cval;           // [L][N*K] max(0, rho) in CSC order, valid where the slot's bit is set
+    unsigned* cbits;       // [L][cwords] bit e of level l set iff slot e holds a positive value; zeroed before the pass
+    int64_t cwords;
     const float* s;
     float* A;
     float* R;
@@ -43,17 +52,21 @@ struct SparseArgs {
     float* tau;
     float* phi;
     const float* tpart;
-    const float* b;
+    const float* b;        // [N][Lb]: the levels of one column side by side (Lb = L rounded up to 4)
     float* rdiag;
     unsigned* status;
-    int N, L, K;
+    int N, L, K, Lb;
     float lam, oml;
     int pending, update_c, use_tau;
 };
 
 // one warp per row, all levels of the row in order; lane holds entries
-// q = lane and q = lane + 32
-__global__ void __launch_bounds__(256) sparse_rowpass_kernel(const SparseArgs p) {
+// q = lane and q = lane + 32.  The column terms b of four levels of a
+// candidate come in one 16-byte gather (levels 0-3 of the next row's
+// candidates during this row's last level, levels 4q..4q+3 four levels
+// ahead when kMultiChunk, i.e. L > 4).
+template <bool kMultiChunk>
+__global__ void __launch_bounds__(256, 4) sparse_rowpass_kernel(const SparseArgs p) {
     const int lane = threadIdx.x & 31;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -67,6 +80,9 @@ __global__ void __launch_bounds__(256) sparse_rowpass_kernel(const SparseArgs p)
     // row's levels run
     int njq[2] = {0x7fffffff, 0x7fffffff}, npq[2] = {0, 0};
     float nsq[2] = {0.f, 0.f};
+    // and so do its per-level scalars: lane t < L holds level t's
+    // preference, fixed c and tau part, broadcast by shuffles when needed
+    float nsc_pref = 0.f, nsc_c = 0.f, nsc_tp = 0.f;
     auto load_row = [&](int64_t r) {
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
@@ -77,8 +93,23 @@ __global__ void __launch_bounds__(256) sparse_rowpass_kernel(const SparseArgs p)
                 nsq[h] = p.s[r * K + q];
             }
         }
+        if (lane < L && r < N) {
+            const int64_t at = (int64_t)lane * N + r;
+            nsc_pref = __ldg(p.pref + at);
+            if (!p.update_c) nsc_c = p.c[at];
+            nsc_tp = p.tpart[at];
+        }
     };
+    auto gather_b = [&](const int (&j)[2], int chunk, float4 (&out)[2]) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+            out[h] = (has[h] && pending)
+                         ? __ldg(reinterpret_cast<const float4*>(p.b + (int64_t)j[h] * p.Lb + 4 * chunk))
+                         : f4_splat(0.f);
+    };
+    float4 bc[2] = {f4_splat(0.f), f4_splat(0.f)};
     load_row(wid);
+    if (wid < N) gather_b(njq, 0, bc);
     for (int64_t i = wid; i < N; i += nw) {
         int jq[2], pq[2];
         float sq[2];
@@ -88,21 +119,33 @@ __global__ void __launch_bounds__(256) sparse_rowpass_kernel(const SparseArgs p)
             pq[h] = npq[h];
             sq[h] = nsq[h];
         }
+        const float sc_pref = nsc_pref, sc_c = nsc_c, sc_tp = nsc_tp;
         load_row(i + nw);
         // level 0's messages; later levels are loaded one level ahead
-        float a[2], r[2], bb[2];
+        float a[2], r[2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int64_t at = i * K + lane + 32 * h;
             a[h] = has[h] ? p.A[at] : -kInf;
             r[h] = has[h] ? p.R[at] : 0.f;
-            bb[h] = (has[h] && pending) ? __ldg(p.b + jq[h]) : 0.f;
         }
+        float4 bn[2] = {f4_splat(0.f), f4_splat(0.f)};
         float c_prev = 0.f;
         for (int l = 0; l < L; ++l) {
             const int64_t base = ((int64_t)l * N + i) * K;
             const int64_t voff = (int64_t)l * N;
-            float na[2] = {-kInf, -kInf}, nr[2] = {0.f, 0.f}, nbb[2] = {0.f, 0.f};
+            if (kMultiChunk) {
+                if ((l & 3) == 0 && l > 0) {
+                    bc[0] = bn[0];
+                    bc[1] = bn[1];
+                }
+                if ((l & 3) == 0 && l + 4 < L) gather_b(jq, (l >> 2) + 1, bn);
+            }
+            const float bb[2] = {f4_get(bc[0], l & 3), f4_get(bc[1], l & 3)};
+            // bc is spent after the last level's read: the next row's gather
+            // goes out while that level runs
+            if (l == L - 1 && i + nw < N) gather_b(njq, 0, bc);
+            float na[2] = {-kInf, -kInf}, nr[2] = {0.f, 0.f};
             if (l + 1 < L) {
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
@@ -110,11 +153,10 @@ __global__ void __launch_bounds__(256) sparse_rowpass_kernel(const SparseArgs p)
                     if (has[h]) {
                         na[h] = p.A[at];
                         nr[h] = p.R[at];
-                        if (pending) nbb[h] = __ldg(p.b + voff + N + jq[h]);
                     }
                 }
             }
-            const float pref_i = __ldg(p.pref + voff + i);
+            const float pref_i = __shfl_sync(0xffffffffu, sc_pref, l);
             float x[2];
             float m1 = -kInf, m2 = -kInf, cm = -kInf;
             int k1 = 0x7fffffff;
@@ -133,8 +175,10 @@ __global__ void __launch_bounds__(256) sparse_rowpass_kernel(const SparseArgs p)
                 cm = fmaxf(cm, __fadd_rn(a[h], r[h]));
             }
             warp_top2(m1, k1, m2, cm);
-            const float cval = p.update_c ? cm : p.c[voff + i];
-            const float tauv = (p.use_tau && l > 0) ? __fadd_rn(c_prev, p.tpart[voff + i]) : kInf;
+            const float c_fixed = __shfl_sync(0xffffffffu, sc_c, l);
+            const float tp_i = __shfl_sync(0xffffffffu, sc_tp, l);
+            const float cval = p.update_c ? cm : c_fixed;
+            const float tauv = (p.use_tau && l > 0) ? __fadd_rn(c_prev, tp_i) : kInf;
             c_prev = cval;
             if (lane == 0) {
                 if (p.update_c) p.c[voff + i] = cval;
@@ -150,38 +194,45 @@ __global__ void __launch_bounds__(256) sparse_rowpass_kernel(const SparseArgs p)
                 p.R[base + q] = rn;
                 const bool diag = jq[h] == (int)i;
                 if (diag) p.rdiag[voff + i] = rn;
-                // the CSC values start at zero each iteration: only positive
-                // off-diagonal responsibilities are written (a few per row)
-                if (!diag && rn > 0.f) p.cval[(int64_t)l * NK + pq[h]] = rn;
+                // only positive off-diagonal responsibilities are written
+                // (a few per row), each with its slot's bit
+                if (!diag && rn > 0.f) {
+                    p.cval[(int64_t)l * NK + pq[h]] = rn;
+                    atomicOr(p.cbits + l * p.cwords + (pq[h] >> 5), 1u << (pq[h] & 31));
+                }
             }
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 a[h] = na[h];
                 r[h] = nr[h];
-                bb[h] = nbb[h];
             }
         }
     }
 }
 
 // P_j = sum over the column's entries (rows k != j) of max(0, rho), read from
-// the CSC-ordered values the row pass wrote.  Columns with at most
-// kShortCol entries (most of them: a point is the candidate of a few
+// the CSC-ordered values the row pass wrote; a slot whose bit is clear holds
+// a zero term and is skipped (adding +0 to a sum of non-negative terms leaves
+// it unchanged, so skipping it does not change the result).  Columns with at
+// most kShortCol entries (most of them: a point is the candidate of a few
 // neighbours) are summed in entry order by one thread; longer ones (hubs,
-// thousands of entries) by one warp: lane t sums slots t, t + 32, ... in
-// order, then a fixed xor-shuffle tree.  The split depends only on the
+// thousands of entries) by one warp: lane t sums the set slots of the
+// column's bitmap words t, t + 32, ... in slot order, then a fixed
+// xor-shuffle tree.  The split depends only on the
 // column's length, so every sum has a fixed order.
 constexpr int kShortCol = 32;
 
-HAP_DEV void colstats_finish(int64_t idx, int l, int L, int N, float P, const float* __restrict__ c,
+HAP_DEV void colstats_finish(int64_t j, int l, int L, int N, float P, const float* __restrict__ c,
                              const float* __restrict__ phi, const float* __restrict__ rdiag, float* __restrict__ b,
                              float* __restrict__ tpart) {
+    const int64_t idx = (int64_t)l * N + j;
     const float rd = rdiag[idx];
-    b[idx] = __fadd_rn(__fadd_rn(__fadd_rn(c[idx], phi[idx]), rd), P);
+    b[j * ((L + 3) & ~3) + l] = __fadd_rn(__fadd_rn(__fadd_rn(c[idx], phi[idx]), rd), P);
     if (l + 1 < L) tpart[idx + N] = __fadd_rn(rd, P);
 }
 
-__global__ void sparse_colstats_short_kernel(const float* __restrict__ cval, const int64_t* __restrict__ cptr,
+__global__ void sparse_colstats_short_kernel(const float* __restrict__ cval, const unsigned* __restrict__ cbits,
+                                             int64_t cwords, const int64_t* __restrict__ cptr,
                                              const int32_t* __restrict__ cols, int ncols, int N, int L, int K,
                                              const float* __restrict__ c, const float* __restrict__ phi,
                                              const float* __restrict__ rdiag, float* __restrict__ b,
@@ -191,12 +242,26 @@ __global__ void sparse_colstats_short_kernel(const float* __restrict__ cval, con
     const int l = (int)(t / ncols);
     const int64_t j = cols[t - (int64_t)l * ncols];
     const float* v = cval + (int64_t)l * N * K;
+    const unsigned* bits = cbits + l * cwords;
+    const int64_t e0 = cptr[j], e1 = cptr[j + 1];
     float P = 0.f;
-    for (int64_t e = cptr[j]; e < cptr[j + 1]; ++e) P = __fadd_rn(P, __ldcs(v + e));
-    colstats_finish((int64_t)l * N + j, l, L, N, P, c, phi, rdiag, b, tpart);
+    if (e0 < e1) {
+        const int64_t w0 = e0 >> 5, w1 = (e1 - 1) >> 5;
+        for (int64_t w = w0; w <= w1; ++w) {
+            unsigned m = bits[w];
+            if (w == w0) m &= ~0u << (e0 & 31);
+            if (w == w1) m &= (2u << ((e1 - 1) & 31)) - 1u;  // bits up to e1 - 1 (all 32 when it is bit 31)
+            while (m) {
+                P = __fadd_rn(P, v[w * 32 + __ffs(m) - 1]);
+                m &= m - 1u;
+            }
+        }
+    }
+    colstats_finish(j, l, L, N, P, c, phi, rdiag, b, tpart);
 }
 
-__global__ void sparse_colstats_long_kernel(const float* __restrict__ cval, const int64_t* __restrict__ cptr,
+__global__ void sparse_colstats_long_kernel(const float* __restrict__ cval, const unsigned* __restrict__ cbits,
+                                            int64_t cwords, const int64_t* __restrict__ cptr,
                                             const int32_t* __restrict__ cols, int ncols, int N, int L, int K,
                                             const float* __restrict__ c, const float* __restrict__ phi,
                                             const float* __restrict__ rdiag, float* __restrict__ b,
@@ -207,20 +272,30 @@ __global__ void sparse_colstats_long_kernel(const float* __restrict__ cval, cons
     const int l = (int)(w / ncols);
     const int64_t j = cols[w - (int64_t)l * ncols];
     const float* v = cval + (int64_t)l * N * K;
+    const unsigned* bits = cbits + l * cwords;
+    const int64_t e0 = cptr[j], e1 = cptr[j + 1];
     float P = 0.f;
-    const int64_t e1 = cptr[j + 1];
-    int64_t e = cptr[j] + lane;
-    // eight loads in flight, added in slot order
-    for (; e + 7 * 32 < e1; e += 8 * 32) {
-        float x[8];
+    // lane t takes the bitmap words t, t + 32, ... of the column and adds the
+    // values of their set bits in slot order, four loads in flight
+    const int64_t w0 = e0 >> 5, w1 = (e1 - 1) >> 5;
+    for (int64_t w = w0 + lane; e0 < e1 && w <= w1; w += 32) {
+        unsigned m = bits[w];
+        if (w == w0) m &= ~0u << (e0 & 31);
+        if (w == w1) m &= (2u << ((e1 - 1) & 31)) - 1u;
+        const float* vw = v + w * 32;
+        while (m) {
+            float x[4];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) x[u] = __ldcs(v + e + 32 * u);
+            for (int u = 0; u < 4; ++u) {
+                x[u] = m ? vw[__ffs(m) - 1] : 0.f;  // +0 leaves the sum unchanged
+                m &= m - 1u;
+            }
 #pragma unroll
-        for (int u = 0; u < 8; ++u) P = __fadd_rn(P, x[u]);
+            for (int u = 0; u < 4; ++u) P = __fadd_rn(P, x[u]);
+        }
     }
-    for (; e < e1; e += 32) P = __fadd_rn(P, __ldcs(v + e));
     for (int o = 16; o > 0; o >>= 1) P = __fadd_rn(P, __shfl_xor_sync(0xffffffffu, P, o));
-    if (lane == 0) colstats_finish((int64_t)l * N + j, l, L, N, P, c, phi, rdiag, b, tpart);
+    if (lane == 0) colstats_finish(j, l, L, N, P, c, phi, rdiag, b, tpart);
 }
 
 // Column classes: flag[j] = 1 for a long column; after the prefix sums the
@@ -436,7 +511,7 @@ __global__ void sparse_exemplars_kernel(const int32_t* __restrict__ cand, const 
         const int j = cand[i * K + q];
         const float r = R[at];
         float a = A[at];
-        if (pending) a = damp(a, avail_target(b[(int64_t)l * N + j], r, j == i), lam, oml);
+        if (pending) a = damp(a, avail_target(b[(int64_t)j * ((L + 3) & ~3) + l], r, j == i), lam, oml);
         if (A_out) A_out[at] = a;
         const float v = __fadd_rn(a, r);
         if (v > best || (v == best && j < bj)) { best = v; bj = j; }
@@ -502,6 +577,8 @@ struct hap_sparse {
     int32_t* cent = nullptr;
     int32_t* pos = nullptr;       // [N*K] CSC slot of every entry
     float* cval = nullptr;        // [L][N*K] max(0, rho) in CSC order
+    unsigned* cbits = nullptr;    // [L][cwords] bitmap of the positive slots
+    int64_t cwords = 0;
     int32_t* tmp[4] = {nullptr, nullptr, nullptr, nullptr};  // radix-sort key / value buffers
     int* cnt = nullptr;           // [N + 1] column counts
     int* cls = nullptr;           // [4][N + 1] column-class flags and positions
@@ -542,7 +619,7 @@ int sparse_reset(hap_sparse* h) {
     SCU(cudaMemcpyAsync(h->c, h->c0, vec, cudaMemcpyDeviceToDevice, h->stream));
     SCU(cudaMemsetAsync(h->phi, 0, vec, h->stream));
     SCU(cudaMemsetAsync(h->tpart, 0, vec, h->stream));
-    SCU(cudaMemsetAsync(h->b, 0, vec, h->stream));
+    SCU(cudaMemsetAsync(h->b, 0, (size_t)h->N * ((h->L + 3) & ~3) * 4, h->stream));
     SCU(cudaMemsetAsync(h->rdiag, 0, vec, h->stream));
     std::vector<float> inf((size_t)h->L * h->N, __builtin_inff());
     SCU(cudaMemcpyAsync(h->tau, inf.data(), vec, cudaMemcpyHostToDevice, h->stream));
@@ -567,17 +644,20 @@ int hap_sparse_create(int64_t N, int L, int K, const float* prefs, float damping
     h->K = K;
     h->lam = damping;
     h->c_mode = c_mode;
+    h->cwords = (int64_t)((N * K + 31) / 32);
     const size_t nk = (size_t)N * K, mat = nk * L * 4, vec = (size_t)L * N * 4;
     bool ok = cudaMalloc(&h->cand, nk * 4) == cudaSuccess && cudaMalloc(&h->s, nk * 4) == cudaSuccess &&
               cudaMalloc(&h->A, mat) == cudaSuccess && cudaMalloc(&h->R, mat) == cudaSuccess &&
               cudaMalloc(&h->pref, vec) == cudaSuccess && cudaMalloc(&h->c, vec) == cudaSuccess &&
               cudaMalloc(&h->c0, vec) == cudaSuccess && cudaMalloc(&h->tau, vec) == cudaSuccess &&
               cudaMalloc(&h->phi, vec) == cudaSuccess && cudaMalloc(&h->tpart, vec) == cudaSuccess &&
-              cudaMalloc(&h->b, vec) == cudaSuccess && cudaMalloc(&h->rdiag, vec) == cudaSuccess &&
+              cudaMalloc(&h->b, (size_t)N * ((L + 3) & ~3) * 4) == cudaSuccess &&
+              cudaMalloc(&h->rdiag, vec) == cudaSuccess &&
               cudaMalloc(&h->cptr, (N + 1) * 8) == cudaSuccess && cudaMalloc(&h->cent, nk * 4) == cudaSuccess &&
               cudaMalloc(&h->e, (size_t)L * N * 4) == cudaSuccess && cudaMalloc(&h->ns, (size_t)L * 8) == cudaSuccess &&
               cudaMalloc(&h->status, 16) == cudaSuccess && cudaMalloc(&h->pos, nk * 4) == cudaSuccess &&
               cudaMalloc(&h->cval, mat) == cudaSuccess && cudaMalloc(&h->cnt, (N + 1) * 4) == cudaSuccess &&
+              cudaMalloc(&h->cbits, (size_t)L * ((nk + 31) / 32) * 4) == cudaSuccess &&
               cudaMalloc(&h->cls, (size_t)4 * (N + 1) * 4) == cudaSuccess &&
               cudaMalloc(&h->long_cols, (size_t)N * 4) == cudaSuccess &&
               cudaMalloc(&h->short_cols, (size_t)N * 4) == cudaSuccess;
@@ -606,7 +686,7 @@ void hap_sparse_destroy(hap_sparse* h) {
     cudaFree(h->cand); cudaFree(h->s); cudaFree(h->A); cudaFree(h->R); cudaFree(h->pref); cudaFree(h->c);
     cudaFree(h->c0); cudaFree(h->tau); cudaFree(h->phi); cudaFree(h->tpart); cudaFree(h->b); cudaFree(h->rdiag);
     cudaFree(h->cptr); cudaFree(h->cent); cudaFree(h->e); cudaFree(h->ns); cudaFree(h->status);
-    cudaFree(h->pos); cudaFree(h->cval); cudaFree(h->cnt); cudaFree(h->hist); cudaFree(h->hoff); cudaFree(h->tsum);
+    cudaFree(h->pos); cudaFree(h->cval); cudaFree(h->cbits); cudaFree(h->cnt); cudaFree(h->hist); cudaFree(h->hoff); cudaFree(h->tsum);
     cudaFree(h->cls); cudaFree(h->long_cols); cudaFree(h->short_cols);
     for (int q = 0; q < 4; ++q) cudaFree(h->tmp[q]);
     delete h;
@@ -691,10 +771,10 @@ int hap_sparse_set_candidates(hap_sparse* h, const int32_t* cand, const float* X
 int hap_sparse_iterate(hap_sparse* h, int n) {
     if (!h || n < 0) return HAP_EINVAL;
     SparseArgs a;
-    a.cand = h->cand; a.pos = h->pos; a.cval = h->cval;
+    a.cand = h->cand; a.pos = h->pos; a.cval = h->cval; a.cbits = h->cbits; a.cwords = h->cwords;
     a.s = h->s; a.A = h->A; a.R = h->R; a.pref = h->pref; a.c = h->c; a.tau = h->tau;
     a.phi = h->phi; a.tpart = h->tpart; a.b = h->b; a.rdiag = h->rdiag; a.status = h->status;
-    a.N = h->N; a.L = h->L; a.K = h->K; a.lam = h->lam; a.oml = 1.0f - h->lam;
+    a.N = h->N; a.L = h->L; a.K = h->K; a.Lb = (h->L + 3) & ~3; a.lam = h->lam; a.oml = 1.0f - h->lam;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -705,18 +785,21 @@ int hap_sparse_iterate(hap_sparse* h, int n) {
         a.pending = h->pending ? 1 : 0;
         a.update_c = (h->c_mode == HAP_C_PAPER && t >= 2) ? 1 : 0;
         a.use_tau = t >= 2 ? 1 : 0;
-        SCU(cudaMemsetAsync(h->cval, 0, (size_t)h->L * h->N * h->K * 4, h->stream));
-        sparse_rowpass_kernel<<<grid, 256, 0, h->stream>>>(a);
+        SCU(cudaMemsetAsync(h->cbits, 0, (size_t)h->L * h->cwords * 4, h->stream));
+        if (h->L > 4)
+            sparse_rowpass_kernel<true><<<grid, 256, 0, h->stream>>>(a);
+        else
+            sparse_rowpass_kernel<false><<<grid, 256, 0, h->stream>>>(a);
         SCU(cudaGetLastError());
         if (h->n_short > 0) {
             const int64_t tot = (int64_t)h->L * h->n_short;
             sparse_colstats_short_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, h->stream>>>(
-                h->cval, h->cptr, h->short_cols, h->n_short, h->N, h->L, h->K, h->c, h->phi, h->rdiag, h->b, h->tpart);
+                h->cval, h->cbits, h->cwords, h->cptr, h->short_cols, h->n_short, h->N, h->L, h->K, h->c, h->phi, h->rdiag, h->b, h->tpart);
         }
         if (h->n_long > 0) {
             const int64_t tot = (int64_t)h->L * h->n_long * 32;
             sparse_colstats_long_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, h->stream>>>(
-                h->cval, h->cptr, h->long_cols, h->n_long, h->N, h->L, h->K, h->c, h->phi, h->rdiag, h->b, h->tpart);
+                h->cval, h->cbits, h->cwords, h->cptr, h->long_cols, h->n_long, h->N, h->L, h->K, h->c, h->phi, h->rdiag, h->b, h->tpart);
         }
         SCU(cudaGetLastError());
         h->launches += 1 + (h->n_short > 0) + (h->n_long > 0);

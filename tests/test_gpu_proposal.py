@@ -166,9 +166,12 @@ def _sparse_problem(N, L, K, seed, K_near=None, score=None):
 
 
 @pytest.mark.parametrize("c_mode", ["paper", "fixed"])
-def test_sparse_hap_equals_masked_dense_reference(c_mode, report):
+@pytest.mark.parametrize("N,K,L", [(600, 32, 3), (602, 30, 3), (601, 31, 6)])
+def test_sparse_hap_equals_masked_dense_reference(c_mode, N, K, L, report):
+    """Even and odd row and candidate counts; L = 6 takes the column terms b
+    of levels 4 and 5 from a second 16-byte gather per candidate."""
     hap = hapm()
-    N, L, K, T = 600, 3, 32, 4
+    T = 4
     Xt, cand, cn, prefs, S_mask = _sparse_problem(N, L, K, seed=4)
     sp = hap.HAPSparse(N, L, K, prefs=prefs, damping=0.5, c_mode=c_mode, device=DEV)
     sp.set_candidates(cand, Xt)
