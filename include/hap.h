@@ -305,7 +305,8 @@ int hap_knn(const float* X, int64_t N, int64_t d, int M, int32_t* idx, float* di
 int hap_knn_with(const float* X, int64_t N, int64_t d, int M, int method, int32_t* idx, float* dist, void* stream);
 
 /* M nearest members of a subset for every point: candidates are the points
- * subset[0..Ns) (device int32 global indices), a point never takes itself;
+ * subset[0..Ns) (device int32 global indices, distinct), a point never takes
+ * itself;
  * idx holds global indices.  Uses a temporary device buffer of Ns*d floats
  * (stream-ordered allocation).  Otherwise as hap_knn. */
 int hap_knn_subset(const float* X, int64_t N, int64_t d, const int32_t* subset, int64_t Ns, int M, int32_t* idx,

@@ -64,9 +64,10 @@ cudaError_t launch_colstats(const float* partials, int G, int L, int64_t N, int6
 // and an exact FP32 re-rank of the M2 >= M best candidates per query row.
 // Queries Q [Nq][d], candidates C [Nc][d] (global ids cid, null = index);
 // a query never takes its own id.  d <= 64, M2 <= knn_tc_max_candidates().
+// launches (may be null) is increased by the number of kernels launched.
 int knn_tc_max_candidates();
 cudaError_t launch_knn_tc(const float* Q, int64_t Nq, const float* C, const int32_t* cid, int64_t Nc, int64_t d, int M,
-                          int M2, int32_t* idx, float* dist, cudaStream_t st);
+                          int M2, int32_t* idx, float* dist, cudaStream_t st, int64_t* launches = nullptr);
 
 // One level of the sequential (Gauss-Seidel) schedule after its rho pass and
 // column statistics: alpha^l (Eqs. 2.2-2.3, damped), then c^l (Eq. 2.6, when
@@ -112,5 +113,23 @@ cudaError_t launch_sbuild_f32(const float* X, int64_t N, int64_t d, void* S, int
 size_t sbuild_tc_scratch_bytes(int64_t N, int64_t d, int split);
 cudaError_t launch_sbuild_tc(const float* X, int64_t N, int64_t d, int split, void* S, int s_bf16,
                              int64_t ld, void* scratch, unsigned* status, cudaStream_t st, int* kernels);
+
+// ---- exclusive prefix sums and stable radix sort (hap_sort.cu) ----------
+constexpr int kRadixBits = 9;  // digit of one radix pass
+// tile sums scan_exclusive needs for n inputs
+int64_t scan_tiles(int64_t n);
+// out[i] = in[0] + ... + in[i-1]; tsum holds scan_tiles(n) values of scratch
+cudaError_t scan_exclusive(const int* in, int64_t n, int* out, int64_t* tsum, cudaStream_t st);
+cudaError_t scan_exclusive(const int* in, int64_t n, int64_t* out, int64_t* tsum, cudaStream_t st);
+// histogram entries of one radix pass over n keys (hist and hoff each)
+int64_t radix_hist_size(int64_t n);
+// one stable pass on the 9-bit digit at `shift`: (key_in, val_in; null =
+// position) -> (key_out, val_out); tsum holds scan_tiles(radix_hist_size(n))
+cudaError_t radix_pass(const int32_t* key_in, const int32_t* val_in, int64_t n, int shift, int* hist, int* hoff,
+                       int64_t* tsum, int32_t* key_out, int32_t* val_out, cudaStream_t st);
+// stable sort of n keys in [0, 2^bits): key_out the sorted keys, perm[r] the
+// input position of the r-th; scratch allocated and freed on the stream
+cudaError_t stable_sort_keys(const int32_t* key, int64_t n, int bits, int32_t* key_out, int32_t* perm,
+                             cudaStream_t st);
 
 }  // namespace hap

@@ -563,10 +563,11 @@ static int knn_launch(const float* Q, int64_t Nq, const float* C, const int32_t*
     // tensor cores once the N_q x N_c distances dominate (the first pass keeps
     // M + 16 candidates per query for the exact re-rank)
     if (method == HAP_KNN_TENSOR_CORES || (method == HAP_KNN_AUTO && tc_ok && (double)Nq * (double)Nc >= 16e6)) {
-        cudaError_t err = launch_knn_tc(Q, Nq, C, cid, Nc, d, M, M2, idx, dist, st);
+        int64_t nl = 0;
+        cudaError_t err = launch_knn_tc(Q, Nq, C, cid, Nc, d, M, M2, idx, dist, st, &nl);
         if (err == cudaErrorNotSupported) { cudaGetLastError(); return HAP_EUNSUPPORTED; }
         PCU(err);
-        g_launches += 4;  // two operand packs, the tensor-core pass, the re-rank
+        g_launches += nl;
         return HAP_OK;
     }
     const int D = d <= 4 ? 4 : d <= 8 ? 8 : d <= 16 ? 16 : d <= 32 ? 32 : 64;

@@ -53,6 +53,50 @@ HAP_DEV void mbar_arrive(uint32_t bar) {
 }
 // 32 lanes x 32 consecutive FP32 columns: thread t of the warp receives row
 // (lane base + t), columns col .. col+31.
+// The same load without the wait: several may be in flight before one
+// tcgen05.wait::ld; the registers are valid only after that wait.
+HAP_DEV void tmem_ld_32x32b_x32_nowait(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                 "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+                 "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+                   "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+                   "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                 : "r"(taddr));
+}
+
+// tcgen05.wait::ld that also marks r as written by it, so no use of the
+// loaded registers can be scheduled before the wait; `tie` does only the
+// latter for further registers of loads the same wait covered.
+HAP_DEV void tmem_wait_ld(uint32_t (&r)[32]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]),
+                   "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]),
+                   "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+                 :: "memory");
+}
+HAP_DEV void tmem_tie(uint32_t (&r)[32]) {
+    asm volatile(""
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]),
+                   "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]),
+                   "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31]));
+}
+
+// Maximum of 32 values by a pairwise tree (5 dependent steps, exact).
+HAP_DEV float max32(const uint32_t (&r)[32]) {
+    float m[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) m[q] = fmaxf(__uint_as_float(r[2 * q]), __uint_as_float(r[2 * q + 1]));
+#pragma unroll
+    for (int w = 8; w > 0; w >>= 1)
+#pragma unroll
+        for (int q = 0; q < w; ++q) m[q] = fmaxf(m[q], m[q + w]);
+    return m[0];
+}
+
 HAP_DEV void tmem_ld_32x32b_x32(uint32_t taddr, float (&v)[32]) {
     uint32_t r[32];
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
@@ -254,9 +298,15 @@ constexpr int KT_PEND = 32;     // per-row buffer of threshold-passing candidate
 constexpr int KT_THREADS = 192; // 4 epilogue warps, 1 producer warp, 1 MMA warp
 
 struct KnnTcArgs {
-    const int32_t* cid;   // candidate j's global id (null: j)
+    const int32_t* cid;   // candidate c's global id (null: c)
+    const int32_t* qperm; // operand row r holds query qperm[r] (null: r)
+    const int32_t* cperm; // operand column j holds candidate cperm[j] (null: j)
+    const int32_t* qkey;  // [Nq] spatial bucket of operand row r, increasing (null: no rotation)
+    const int32_t* ckey;  // [Nc] spatial bucket of operand column j, increasing
+    const int32_t* self_col;  // [Nq] operand column holding query r's own point, -1 none (null: see exclude_self)
     int Nq, Nc, M2, kchunks, ring;
-    int32_t* cand;        // out [Nq][M2] candidate columns, -1 where fewer
+    int exclude_self;     // without self_col: drop column r for row r (queries and candidates in the same order)
+    int32_t* cand;        // out [Nq][M2] candidate indices per query, -1 where fewer
     unsigned* status;
 };
 
@@ -289,6 +339,22 @@ __global__ void __launch_bounds__(KT_THREADS, 1) knn_tc_kernel(const __grid_cons
     const uint32_t acc_full = b_empty + 8 * KT_RING_MAX, acc_empty = acc_full + 16;
     const int m0 = blockIdx.x * BM;
     const int ntiles = (p.Nc + BN - 1) / BN;
+    // With queries and candidates sorted by spatial bucket, candidate tiles
+    // are visited from the one holding the first candidate of this query
+    // tile's first bucket (wrapping), so the nearest candidates come first
+    // and the row thresholds tighten at once (the bucket before it in the
+    // sorted order is no nearer in space than any other).  Without buckets every CTA
+    // scans from tile 0, in step with the others, sharing tiles in L2.
+    int t0 = 0;
+    if (p.qkey) {
+        const int key = p.qkey[m0 < p.Nq ? m0 : p.Nq - 1];
+        int lo = 0, hi = p.Nc;  // first column whose bucket is >= key
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (p.ckey[mid] < key) lo = mid + 1; else hi = mid;
+        }
+        t0 = (lo < p.Nc ? lo : p.Nc - 1) / BN;
+    }
     if (tid == 0) {
         mbar_init(a_full, 1);
         for (int q = 0; q < R; ++q) {
@@ -321,8 +387,9 @@ __global__ void __launch_bounds__(KT_THREADS, 1) knn_tc_kernel(const __grid_cons
                     break;
                 }
                 const int t = g / p.kchunks, kc = g - t * p.kchunks;
+                const int tt = t0 + t < ntiles ? t0 + t : t0 + t - ntiles;
                 mbar_arrive_expect_tx(b_full + 8 * st, BN * BK * 2);
-                tma_load_2d(sB + (uint32_t)st * BN * BK * 2, &tmB, kc * BK, t * BN, b_full + 8 * st);
+                tma_load_2d(sB + (uint32_t)st * BN * BK * 2, &tmB, kc * BK, tt * BN, b_full + 8 * st);
             }
         }
     } else if (warp == 5) {
@@ -350,6 +417,10 @@ __global__ void __launch_bounds__(KT_THREADS, 1) knn_tc_kernel(const __grid_cons
         }
     } else {  // ---- epilogue: warps 0-3, thread = query row = TMEM lane
         const int row = m0 + tid;
+        const int qrow = row < p.Nq ? (p.qperm ? p.qperm[row] : row) : -1;
+        // the column never taken by this row (its own point), -1 none; the
+        // heap keeps operand columns, mapped to candidates on output
+        const int skip = p.self_col ? (row < p.Nq ? p.self_col[row] : -1) : (p.exclude_self ? row : -1);
         // the M2 smallest first-pass keys ||c||^2 - 2 q.c of this row as a
         // max-heap in shared memory (root = current threshold); columns below
         // the threshold are first appended to a short buffer (cheap even when
@@ -402,38 +473,51 @@ __global__ void __launch_bounds__(KT_THREADS, 1) knn_tc_kernel(const __grid_cons
                 break;
             }
             tc_fence_after();
-            const bool full_tile = (t + 1) * BN <= p.Nc;
+            const int tt = t0 + t < ntiles ? t0 + t : t0 + t - ntiles;
+            const bool full_tile = (tt + 1) * BN <= p.Nc;
+            // 64 columns per round: two TMEM loads in flight, one wait; the
+            // accumulator goes back to the MMA warp as soon as the last
+            // round's values are in registers
 #pragma unroll 1
-            for (int cc = 0; cc < BN / 32; ++cc) {
-                float v[32];
+            for (int hh = 0; hh < BN / 64; ++hh) {
+                uint32_t r[2][32];
                 __syncwarp();
-                tmem_ld_32x32b_x32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(buf * BN + 32 * cc), v);
-                const int jb = t * BN + 32 * cc;
-                float vm = v[0];
+                const uint32_t ta = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(buf * BN + 64 * hh);
+                tmem_ld_32x32b_x32_nowait(ta, r[0]);
+                tmem_ld_32x32b_x32_nowait(ta + 32, r[1]);
+                tmem_wait_ld(r[0]);
+                tmem_tie(r[1]);
+                if (hh == BN / 64 - 1) {
+                    tc_fence_before();
+                    mbar_arrive(acc_empty + 8 * buf);
+                }
 #pragma unroll
-                for (int q = 1; q < 32; ++q) vm = fmaxf(vm, v[q]);
-                int np = 0;
-                if (vm > vthr) {
+                for (int b = 0; b < 2; ++b) {
+                    const int jb = tt * BN + 64 * hh + 32 * b;
+                    int np = 0;
+                    if (max32(r[b]) > vthr) {
 #pragma unroll
-                    for (int q = 0; q < 32; ++q) {
-                        if (v[q] > vthr && (full_tile || jb + q < p.Nc)) {
-                            pdist[np * BM + tid] = -2.f * v[q];
-                            pidx[np * BM + tid] = jb + q;
-                            ++np;
+                        for (int q = 0; q < 32; ++q) {
+                            const float v = __uint_as_float(r[b][q]);
+                            if (v > vthr && (full_tile || jb + q < p.Nc)) {
+                                pdist[np * BM + tid] = -2.f * v;
+                                pidx[np * BM + tid] = jb + q;
+                                ++np;
+                            }
                         }
                     }
-                }
-                for (int k = 0; k < np; ++k) {
-                    const int j = pidx[k * BM + tid];
-                    const int gid = p.cid ? p.cid[j] : j;
-                    if (gid != row) heap_push(pdist[k * BM + tid], j);
+                    for (int k = 0; k < np; ++k) {
+                        const int j = pidx[k * BM + tid];
+                        if (j != skip) heap_push(pdist[k * BM + tid], j);
+                    }
                 }
             }
-            tc_fence_before();
-            mbar_arrive(acc_empty + 8 * buf);
         }
-        if (row < p.Nq)
-            for (int m = 0; m < M2; ++m) p.cand[(int64_t)row * M2 + m] = m < cnt ? tidx[m * BM + tid] : -1;
+        if (qrow >= 0)
+            for (int m = 0; m < M2; ++m) {
+                const int j = m < cnt ? tidx[m * BM + tid] : -1;
+                p.cand[(int64_t)qrow * M2 + m] = (j >= 0 && p.cperm) ? p.cperm[j] : j;
+            }
     }
     tc_fence_before();
     __syncthreads();
@@ -505,13 +589,14 @@ __global__ void knn_rerank_kernel(const float* __restrict__ Q, const float* __re
 // Operands of the nearest-neighbour contraction (zero-padded to [npad][kpad]
 // BF16): queries A = [hi, hi, lo, 1, 1], candidates B = [hi, lo, hi, h, l]
 // with h + l = -||c||^2 / 2 (BF16 hi and lo; the norm accumulated in FP64).
-__global__ void pack_knn_kernel(const float* __restrict__ X, int N, int d, int kpad, int is_b,
-                                __nv_bfloat16* __restrict__ out) {
+__global__ void pack_knn_kernel(const float* __restrict__ X, const int32_t* __restrict__ perm, int N, int d,
+                                int kpad, int is_b, __nv_bfloat16* __restrict__ out) {
     const int i = blockIdx.x;
+    const int64_t src = perm ? perm[i] : i;
     __nv_bfloat16* o = out + (int64_t)i * kpad;
     double acc = 0.0;
     for (int k = threadIdx.x; k < d; k += blockDim.x) {
-        const float x = X[(int64_t)i * d + k];
+        const float x = X[src * d + k];
         acc += (double)x * (double)x;
         const __nv_bfloat16 hi = __float2bfloat16_rn(x);
         const __nv_bfloat16 lo = __float2bfloat16_rn(x - __bfloat162float(hi));
@@ -624,8 +709,17 @@ cudaError_t launch_sbuild_tc(const float* X, int64_t N, int64_t d, int split, vo
 
 int knn_tc_max_candidates() { return KT_MAXM2; }
 
-cudaError_t launch_knn_tc(const float* Q, int64_t Nq, const float* C, const int32_t* cid, int64_t Nc, int64_t d, int M,
-                          int M2, int32_t* idx, float* dist, cudaStream_t st) {
+// Spatial order of one kNN problem: operand row r / column j hold query
+// qperm[r] / candidate cperm[j], with bucket keys qkey / ckey increasing.
+struct KnnOrder {
+    const int32_t *qperm = nullptr, *cperm = nullptr, *qkey = nullptr, *ckey = nullptr;
+};
+
+// rerank 0: the first pass alone, its M2 candidates per query straight into
+// idx [Nq][M2] (unordered, BF16-split keys; dist unused)
+static cudaError_t knn_tc_core(const float* Q, int64_t Nq, const float* C, const int32_t* cid, int64_t Nc, int64_t d,
+                               int M, int M2, int32_t* idx, float* dist, const KnnOrder& ord, int exclude_self,
+                               const int32_t* self_col, int rerank, cudaStream_t st) {
     if (M2 > KT_MAXM2 || M2 < M || d > 64) return cudaErrorInvalidValue;
     const int64_t kpad = (3 * d + 2 + BK - 1) / BK * BK;
     const int64_t qpad = (Nq + BM - 1) / BM * BM, cpad = (Nc + BN - 1) / BN * BN;
@@ -645,8 +739,8 @@ cudaError_t launch_knn_tc(const float* Q, int64_t Nq, const float* C, const int3
     do {
         if ((err = cudaMemsetAsync(base, 0, off_cand, st)) != cudaSuccess) break;
         if ((err = cudaMemsetAsync(status, 0, 16, st)) != cudaSuccess) break;
-        pack_knn_kernel<<<(unsigned)Nq, 64, 0, st>>>(Q, (int)Nq, (int)d, (int)kpad, 0, A);
-        pack_knn_kernel<<<(unsigned)Nc, 64, 0, st>>>(C, (int)Nc, (int)d, (int)kpad, 1, B);
+        pack_knn_kernel<<<(unsigned)Nq, 64, 0, st>>>(Q, ord.qperm, (int)Nq, (int)d, (int)kpad, 0, A);
+        pack_knn_kernel<<<(unsigned)Nc, 64, 0, st>>>(C, ord.cperm, (int)Nc, (int)d, (int)kpad, 1, B);
         if ((err = cudaGetLastError()) != cudaSuccess) break;
         CUtensorMap mA, mB;
         if (!encode_operand_map(&mA, A, qpad, kpad) || !encode_operand_map(&mB, B, cpad, kpad)) {
@@ -655,11 +749,17 @@ cudaError_t launch_knn_tc(const float* Q, int64_t Nq, const float* C, const int3
         }
         KnnTcArgs a;
         a.cid = cid;
+        a.qperm = ord.qperm;
+        a.cperm = ord.cperm;
+        a.qkey = ord.qkey;
+        a.ckey = ord.ckey;
+        a.exclude_self = exclude_self;
+        a.self_col = self_col;
         a.Nq = (int)Nq;
         a.Nc = (int)Nc;
         a.M2 = M2;
         a.kchunks = (int)(kpad / BK);
-        a.cand = cand;
+        a.cand = rerank ? cand : idx;
         a.status = status;
         int dev = 0, smem_limit = 0;
         cudaGetDevice(&dev);
@@ -675,10 +775,92 @@ cudaError_t launch_knn_tc(const float* Q, int64_t Nq, const float* C, const int3
             cudaSuccess)
             break;
         knn_tc_kernel<<<(unsigned)(qpad / BM), KT_THREADS, smem, st>>>(mA, mB, a);
-        if ((err = cudaGetLastError()) != cudaSuccess) break;
+        if ((err = cudaGetLastError()) != cudaSuccess || !rerank) break;
         knn_rerank_kernel<<<(unsigned)((Nq * 32 + 255) / 256), 256, 0, st>>>(Q, C, cid, (int)Nq, (int)d, M2, M, cand,
                                                                             status, idx, dist);
         err = cudaGetLastError();
+    } while (0);
+    cudaError_t e2 = cudaFreeAsync(raw, st);
+    return err != cudaSuccess ? err : e2;
+}
+
+// inv[cid[j]] = j for the candidates whose global id is a query index
+__global__ void inverse_subset_kernel(const int32_t* __restrict__ cid, int64_t Nc, int64_t Nq,
+                                      int32_t* __restrict__ inv) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < Nc && cid[j] >= 0 && cid[j] < Nq) inv[cid[j]] = (int32_t)j;
+}
+
+__global__ void pivot_rows_kernel(const float* __restrict__ C, int64_t d, int64_t step, float* __restrict__ out) {
+    const int64_t i = blockIdx.x;
+    for (int64_t k = threadIdx.x; k < d; k += blockDim.x) out[i * d + k] = C[i * step * d + k];
+}
+
+// The first pass prunes a 32-column batch unless it beats a row's current
+// threshold, which is cheap only once the threshold is close to its final
+// value.  So for the kNN of a point set among itself the points are first
+// sorted by their nearest of P pivots (every 128th point: buckets of about
+// one tile; the bucket search is the first pass alone with one candidate),
+// and each query tile scans the candidates from its own bucket on.  The
+// result does not depend on the order: the re-rank sorts by (distance,
+// index).  Queries against another set (hubs) keep the input order: with
+// buckets barely larger than the M2 kept candidates, a query's nearest
+// candidates span buckets that are not adjacent, and the CTAs scanning in
+// step share candidate tiles in L2 (measured faster).
+cudaError_t launch_knn_tc(const float* Q, int64_t Nq, const float* C, const int32_t* cid, int64_t Nc, int64_t d, int M,
+                          int M2, int32_t* idx, float* dist, cudaStream_t st, int64_t* launches) {
+    if (M2 > KT_MAXM2 || M2 < M || d > 64) return cudaErrorInvalidValue;
+    const bool self = Q == C && cid == nullptr && Nq == Nc;
+    const int64_t P = Nc / 128;
+    if (!self) {
+        // queries Q are the N points, candidates their subset cid: the
+        // column holding a query's own point comes from the inverse of cid
+        int32_t* inv = nullptr;
+        cudaError_t err = cudaMallocAsync(reinterpret_cast<void**>(&inv), (size_t)Nq * 4, st);
+        if (err != cudaSuccess) return err;
+        do {
+            if ((err = cudaMemsetAsync(inv, 0xff, (size_t)Nq * 4, st)) != cudaSuccess) break;
+            if (cid) {
+                inverse_subset_kernel<<<(unsigned)((Nc + 255) / 256), 256, 0, st>>>(cid, Nc, Nq, inv);
+                if ((err = cudaGetLastError()) != cudaSuccess) break;
+            }
+            err = knn_tc_core(Q, Nq, C, cid, Nc, d, M, M2, idx, dist, KnnOrder{}, 0, inv, 1, st);
+        } while (0);
+        if (launches) *launches += (cid ? 1 : 0) + 4;  // inverse map; two operand packs, first pass, re-rank
+        cudaError_t e2 = cudaFreeAsync(inv, st);
+        return err != cudaSuccess ? err : e2;
+    }
+    if (P < 8) {
+        if (launches) *launches += 4;  // two operand packs, the first pass, the re-rank
+        return knn_tc_core(Q, Nq, C, cid, Nc, d, M, M2, idx, dist, KnnOrder{}, 1, nullptr, 1, st);
+    }
+    int bits = 1;
+    while (((int64_t)1 << bits) < P) ++bits;
+    // pivots; the bucket search (two packs and a first pass); the sort (5
+    // kernels per 9-bit pass); the ordered search
+    if (launches) *launches += 1 + 3 + 5 * ((bits + kRadixBits - 1) / kRadixBits) + 4;
+    // scratch: pivots, and per point its bucket, the sorted buckets and the
+    // permutation
+    const size_t bytes = (size_t)P * d * 4 + (size_t)Nq * 12 + 1024;
+    char* raw = nullptr;
+    cudaError_t err = cudaMallocAsync(reinterpret_cast<void**>(&raw), bytes, st);
+    if (err != cudaSuccess) return err;
+    float* piv = reinterpret_cast<float*>(raw);
+    int32_t* bkt = reinterpret_cast<int32_t*>(piv + P * d);
+    int32_t* key = bkt + Nq;
+    int32_t* perm = key + Nq;
+    do {
+        pivot_rows_kernel<<<(unsigned)P, 64, 0, st>>>(C, d, Nc / P, piv);
+        if ((err = cudaGetLastError()) != cudaSuccess) break;
+        // the approximately nearest pivot (first-pass keys) is bucket enough
+        if ((err = knn_tc_core(Q, Nq, piv, nullptr, P, d, 1, 1, bkt, nullptr, KnnOrder{}, 0, nullptr, 0, st)) !=
+            cudaSuccess)
+            break;
+        if ((err = stable_sort_keys(bkt, Nq, bits, key, perm, st)) != cudaSuccess) break;
+        KnnOrder ord;
+        ord.qperm = ord.cperm = perm;
+        ord.qkey = ord.ckey = key;
+        err = knn_tc_core(Q, Nq, C, cid, Nc, d, M, M2, idx, dist, ord, 1, nullptr, 1, st);
     } while (0);
     cudaError_t e2 = cudaFreeAsync(raw, st);
     return err != cudaSuccess ? err : e2;

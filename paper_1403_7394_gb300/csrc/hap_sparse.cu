@@ -343,137 +343,6 @@ __global__ void sparse_check_count_kernel(const int32_t* __restrict__ cand, int 
 
 // Exclusive prefix sums of int counts (3 launches: tile sums, one-CTA scan of
 // the tile sums, tile-local scans plus offsets).
-constexpr int kScanT = 256, kScanPer = 8, kScanTile = kScanT * kScanPer;
-
-HAP_DEV int64_t block_exclusive_scan(int64_t v, int64_t* warp_sums, int64_t* total) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int64_t x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) warp_sums[warp] = x;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int64_t run = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-            const int64_t t = warp_sums[w];
-            warp_sums[w] = run;
-            run += t;
-        }
-        *total = run;
-    }
-    __syncthreads();
-    const int64_t out = x - v + warp_sums[warp];
-    __syncthreads();
-    return out;
-}
-
-__global__ void scan_tile_sums_kernel(const int* __restrict__ in, int64_t n, int64_t* __restrict__ tsum) {
-    __shared__ int64_t ws[kScanT / 32];
-    __shared__ int64_t tot;
-    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanPer;
-    int64_t v = 0;
-    for (int u = 0; u < kScanPer; ++u) v += (base + u < n) ? in[base + u] : 0;
-    block_exclusive_scan(v, ws, &tot);
-    if (threadIdx.x == 0) tsum[blockIdx.x] = tot;
-}
-
-__global__ void scan_tile_offsets_kernel(int64_t* __restrict__ tsum, int64_t ntiles) {
-    __shared__ int64_t ws[kScanT / 32];
-    __shared__ int64_t tot;
-    int64_t carry = 0;
-    for (int64_t b0 = 0; b0 < ntiles; b0 += kScanT) {
-        const int64_t k = b0 + threadIdx.x;
-        const int64_t v = k < ntiles ? tsum[k] : 0;
-        const int64_t ex = block_exclusive_scan(v, ws, &tot);
-        if (k < ntiles) tsum[k] = carry + ex;
-        carry += tot;
-        __syncthreads();
-    }
-}
-
-template <typename OT>
-__global__ void scan_apply_kernel(const int* __restrict__ in, int64_t n, const int64_t* __restrict__ toff,
-                                  OT* __restrict__ out) {
-    __shared__ int64_t ws[kScanT / 32];
-    __shared__ int64_t tot;
-    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanPer;
-    int64_t v = 0;
-    for (int u = 0; u < kScanPer; ++u) v += (base + u < n) ? in[base + u] : 0;
-    int64_t run = block_exclusive_scan(v, ws, &tot) + toff[blockIdx.x];
-    for (int u = 0; u < kScanPer; ++u) {
-        if (base + u < n) {
-            out[base + u] = (OT)run;
-            run += in[base + u];
-        }
-    }
-}
-
-// Stable least-significant-digit radix sort of (column, entry) pairs, 9-bit
-// digits, chunks of kRadixChunk consecutive elements per CTA.  Pass p orders
-// by digit p with ties kept in their current order, so after the last pass
-// the entries of every column are in increasing entry order.
-constexpr int kRadixBits = 9, kRadixBins = 1 << kRadixBits, kRadixT = 256, kRadixRounds = 16;
-constexpr int kRadixChunk = kRadixT * kRadixRounds;
-
-__global__ void radix_hist_kernel(const int32_t* __restrict__ key, int64_t n, int shift, int nchunks,
-                                  int* __restrict__ hist) {
-    __shared__ int h[kRadixBins];
-    for (int d = threadIdx.x; d < kRadixBins; d += kRadixT) h[d] = 0;
-    __syncthreads();
-    const int64_t base = (int64_t)blockIdx.x * kRadixChunk;
-    for (int r = 0; r < kRadixRounds; ++r) {
-        const int64_t idx = base + (int64_t)r * kRadixT + threadIdx.x;
-        if (idx < n) atomicAdd(&h[(key[idx] >> shift) & (kRadixBins - 1)], 1);
-    }
-    __syncthreads();
-    for (int d = threadIdx.x; d < kRadixBins; d += kRadixT) hist[(int64_t)d * nchunks + blockIdx.x] = h[d];
-}
-
-__global__ void __launch_bounds__(kRadixT) radix_scatter_kernel(
-    const int32_t* __restrict__ key, const int32_t* __restrict__ val, int64_t n, int shift, int nchunks,
-    const int* __restrict__ off, int32_t* __restrict__ okey, int32_t* __restrict__ oval) {
-    __shared__ int running[kRadixBins];
-    __shared__ int wcnt[kRadixT / 32][kRadixBins];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int d = tid; d < kRadixBins; d += kRadixT) {
-        running[d] = 0;
-        for (int w = 0; w < kRadixT / 32; ++w) wcnt[w][d] = 0;
-    }
-    __syncthreads();
-    const int64_t base = (int64_t)blockIdx.x * kRadixChunk;
-    for (int r = 0; r < kRadixRounds; ++r) {
-        const int64_t idx = base + (int64_t)r * kRadixT + tid;
-        const bool valid = idx < n;
-        const int32_t k = valid ? key[idx] : 0;
-        const int32_t v = valid ? (val ? val[idx] : (int32_t)idx) : 0;
-        const int d = valid ? ((k >> shift) & (kRadixBins - 1)) : kRadixBins;  // invalid: own class
-        const unsigned peers = __match_any_sync(0xffffffffu, d);
-        const int rank = __popc(peers & ((1u << lane) - 1u));
-        if (valid && rank == 0) wcnt[warp][d] = __popc(peers);
-        __syncthreads();
-        if (valid) {
-            int before = running[d] + rank;
-            for (int w = 0; w < warp; ++w) before += wcnt[w][d];
-            const int64_t pos = (int64_t)off[(int64_t)d * nchunks + blockIdx.x] + before;
-            okey[pos] = k;
-            oval[pos] = v;
-        }
-        __syncthreads();
-        for (int d2 = tid; d2 < kRadixBins; d2 += kRadixT) {
-            int sum = 0;
-            for (int w = 0; w < kRadixT / 32; ++w) {
-                sum += wcnt[w][d2];
-                wcnt[w][d2] = 0;
-            }
-            running[d2] += sum;
-        }
-        __syncthreads();
-    }
-}
-
 // pos[cent[x]] = x: the CSC slot of every entry
 __global__ void inverse_perm_kernel(const int32_t* __restrict__ cent, int64_t n, int32_t* __restrict__ pos) {
     const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -600,18 +469,6 @@ struct hap_sparse {
 
 namespace {
 
-int64_t radix_chunks(int64_t nk) { return (nk + kRadixChunk - 1) / kRadixChunk; }
-
-// exclusive prefix sums of n ints into out (int or int64)
-template <typename OT>
-cudaError_t scan_exclusive(const int* in, int64_t n, OT* out, int64_t* tsum, cudaStream_t st) {
-    const int64_t tiles = (n + kScanTile - 1) / kScanTile;
-    scan_tile_sums_kernel<<<(unsigned)tiles, kScanT, 0, st>>>(in, n, tsum);
-    scan_tile_offsets_kernel<<<1, kScanT, 0, st>>>(tsum, tiles);
-    scan_apply_kernel<OT><<<(unsigned)tiles, kScanT, 0, st>>>(in, n, tsum, out);
-    return cudaGetLastError();
-}
-
 int sparse_reset(hap_sparse* h) {
     const size_t mat = (size_t)h->L * h->N * h->K * 4, vec = (size_t)h->L * h->N * 4;
     SCU(cudaMemsetAsync(h->A, 0, mat, h->stream));
@@ -661,8 +518,8 @@ int hap_sparse_create(int64_t N, int L, int K, const float* prefs, float damping
               cudaMalloc(&h->cls, (size_t)4 * (N + 1) * 4) == cudaSuccess &&
               cudaMalloc(&h->long_cols, (size_t)N * 4) == cudaSuccess &&
               cudaMalloc(&h->short_cols, (size_t)N * 4) == cudaSuccess;
-    const int64_t nhist = (int64_t)kRadixBins * radix_chunks((int64_t)nk);
-    const int64_t ntiles = (std::max<int64_t>(nhist, N + 1) + kScanTile - 1) / kScanTile;
+    const int64_t nhist = radix_hist_size((int64_t)nk);
+    const int64_t ntiles = scan_tiles(std::max<int64_t>(nhist, N + 1));
     for (int q = 0; q < 4 && ok; ++q) ok = cudaMalloc(&h->tmp[q], nk * 4) == cudaSuccess;
     ok = ok && cudaMalloc(&h->hist, nhist * 4) == cudaSuccess && cudaMalloc(&h->hoff, nhist * 4) == cudaSuccess &&
          cudaMalloc(&h->tsum, ntiles * 8) == cudaSuccess;
@@ -718,33 +575,28 @@ int hap_sparse_set_candidates(hap_sparse* h, const int32_t* cand, const float* X
     SCU(cudaMemsetAsync(h->status, 0, 16, st));
     sparse_check_count_kernel<<<(unsigned)((N * 32 + 255) / 256), 256, 0, st>>>(h->cand, (int)N, (int)K, h->status, h->cnt);
     SCU(cudaGetLastError());
-    SCU(scan_exclusive<int64_t>(h->cnt, N + 1, h->cptr, h->tsum, st));
+    SCU(scan_exclusive(h->cnt, N + 1, h->cptr, h->tsum, st));
     // columns by length class, each list in increasing column order
     int* is_long = h->cls;
     int* is_short = h->cls + (N + 1);
     int* long_pos = h->cls + 2 * (N + 1);
     int* short_pos = h->cls + 3 * (N + 1);
     column_class_kernel<<<(unsigned)((N + 1 + 255) / 256), 256, 0, st>>>(h->cnt, (int)N, is_long, is_short);
-    SCU(scan_exclusive<int>(is_long, N + 1, long_pos, h->tsum, st));
-    SCU(scan_exclusive<int>(is_short, N + 1, short_pos, h->tsum, st));
+    SCU(scan_exclusive(is_long, N + 1, long_pos, h->tsum, st));
+    SCU(scan_exclusive(is_short, N + 1, short_pos, h->tsum, st));
     column_compact_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(is_long, long_pos, short_pos, (int)N,
                                                                        h->long_cols, h->short_cols);
     SCU(cudaGetLastError());
     // entries sorted by column, stable: the CSC entry order
     int passes = 1;
     while (passes * kRadixBits < 31 && ((int64_t)1 << (passes * kRadixBits)) < N) ++passes;
-    const int nchunks = (int)radix_chunks(nk);
     const int32_t* kin = h->cand;
     const int32_t* vin = nullptr;  // first pass: value = entry index
     for (int p = 0; p < passes; ++p) {
         const bool last = p + 1 == passes;
         int32_t* ko = (kin == h->tmp[0]) ? h->tmp[2] : h->tmp[0];
         int32_t* vo = last ? h->cent : ((vin == h->tmp[1]) ? h->tmp[3] : h->tmp[1]);
-        radix_hist_kernel<<<nchunks, kRadixT, 0, st>>>(kin, nk, p * kRadixBits, nchunks, h->hist);
-        SCU(cudaGetLastError());
-        SCU(scan_exclusive<int>(h->hist, (int64_t)kRadixBins * nchunks, h->hoff, h->tsum, st));
-        radix_scatter_kernel<<<nchunks, kRadixT, 0, st>>>(kin, vin, nk, p * kRadixBits, nchunks, h->hoff, ko, vo);
-        SCU(cudaGetLastError());
+        SCU(radix_pass(kin, vin, nk, p * kRadixBits, h->hist, h->hoff, h->tsum, ko, vo, st));
         kin = ko;
         vin = vo;
     }

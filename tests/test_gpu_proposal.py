@@ -58,10 +58,11 @@ def test_knn_exact(N, d, M, method):
 
 
 def test_knn_tensor_cores_match_cuda_cores(report):
-    """At a size where the tensor-core path is the automatic choice, its
-    re-ranked result equals the CUDA-core kNN (same FP32 distance arithmetic)
-    row for row; hub kNN (a subset of candidates) likewise up to the order of
-    exactly equal distances."""
+    """At a size where the tensor-core path is the automatic choice (and the
+    points are first sorted by nearest pivot), its re-ranked result equals
+    the CUDA-core kNN (same FP32 distance arithmetic) row for row; hub kNN (a
+    subset of candidates) likewise up to the order of exactly equal
+    distances."""
     hap = hapm()
     X, _ = W.gmm_points(20000, 32, 64, sigma=1.0, seed=8, means="normal", mean_scale=2.0)
     Xt = torch.from_numpy(X.astype(np.float32)).to(DEV)
@@ -70,11 +71,15 @@ def test_knn_tensor_cores_match_cuda_cores(report):
     same = (i_tc == i_cc).all(dim=1).float().mean().item()
     report(rows_identical=same)
     assert same == 1.0 and torch.equal(d_tc, d_cc)
-    sub = torch.from_numpy(np.sort(np.random.default_rng(1).choice(20000, 700, replace=False)).astype(np.int32)).to(DEV)
-    s_tc, e_tc = hap.knn_subset(Xt, sub, 48, method="tensor_cores")
-    s_cc, e_cc = hap.knn_subset(Xt, sub, 48, method="cuda_cores")
-    assert torch.equal(e_tc, e_cc)
-    assert torch.equal(torch.sort(s_tc, dim=1).values, torch.sort(s_cc, dim=1).values)
+    # 700 candidates: one pass in input order; 2500: queries and candidates
+    # sorted by their nearest of 19 pivots first (different orders for the
+    # two sets), which must not change the result
+    for ns in (700, 2500):
+        sub = torch.from_numpy(np.sort(np.random.default_rng(1).choice(20000, ns, replace=False)).astype(np.int32)).to(DEV)
+        s_tc, e_tc = hap.knn_subset(Xt, sub, 48, method="tensor_cores")
+        s_cc, e_cc = hap.knn_subset(Xt, sub, 48, method="cuda_cores")
+        assert torch.equal(e_tc, e_cc), ns
+        assert torch.equal(torch.sort(s_tc, dim=1).values, torch.sort(s_cc, dim=1).values), ns
 
 
 def test_features_match_reference():
