@@ -628,6 +628,15 @@ def run_learned(args, world, rank, local):
         step(eh)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
+    # judging at full N: the learned candidates against the K - 1 exact
+    # nearest neighbours as candidates (untimed)
+    e_l = e_out.cpu().numpy()
+    e_k, ns_k = sparse_solve(Xt, prefs, None, K - 1, T)
+    e_k = e_k.cpu().numpy()
+    full_n = {"n": N, "ns_learned": [float(x) for x in ns], "ns_knn": [float(x) for x in ns_k],
+              "ns_gain_over_knn_level1": float((ns[0] - ns_k[0]) / abs(ns_k[0])),
+              "ari_learned_vs_knn_level1": ari(e_l[0], e_k[0]),
+              "exemplars_level1": {"learned": int(len(np.unique(e_l[0]))), "knn": int(len(np.unique(e_k[0])))}}
     # the sparse iterations alone
     sp.iterate(2)
     a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -656,7 +665,8 @@ def run_learned(args, world, rank, local):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": args.workload, "desc": desc, "N": N, "K": K, "L": L, "iters": T,
                        "updates_counted": "sparse N*K*L per iteration", "knn_ms": knn_ms,
-                       "sparse_iteration_ms": it_ms, "train_s": t_train, "train_loss": loss, "judge": judge},
+                       "sparse_iteration_ms": it_ms, "train_s": t_train, "train_loss": loss, "judge": judge,
+                       "judge_full_n": full_n},
             "e2e": {"value": world * max(1, args.e2e_steps) * updates / e2e_s, "unit": "updates/s",
                     "h2d_bytes_per_step": int(X32.nbytes), "d2h_bytes_per_step": int(eh.numel() * 4 + L * 8)},
             "gpu_launches": int(launches),
