@@ -6,22 +6,19 @@
 //
 // Layout: cand [N][K] int32, s [N][K] FP32 (= -||x_i - x_cand||^2, the
 // preference on the self entry), alpha and rho [L][N][K], the column terms
-// b [N][4 ceil(L/4)] (all levels of a column in one 16-byte gather; the row
-// pass's gathers of b set its speed: one 32-byte sector per candidate per
-// gather).  Row pass: one warp
-// per row walks the L levels (alpha kept one step behind exactly as in the
-// dense row pass; the next level's alpha, rho and b are loaded while the
-// current level reduces).  The column index (CSC: for every column j the
-// entries (k, q) with cand[k][q] = j, in entry order) is built on the GPU by
-// a stable radix sort of the entries by column; the row pass writes the
-// positive off-diagonal responsibilities straight to their CSC slots (in a
-// buffer zeroed before the pass: most responsibilities are negative, so few
-// scattered writes), and the column statistics sum contiguous segments in a
-// fixed order.  Only the slots of positive responsibilities are ever read:
-// the row pass also sets the slot's bit in a per-level bitmap (zeroed before
-// the pass, 1/32 of the values' size), and the column statistics read the
-// bitmap and gather the values of set bits alone, so the CSC values are
-// neither zeroed nor swept.
+// b [N][4 ceil(L/4)] (all levels of a column side by side, so one 16-byte
+// gather per candidate brings them).  Row pass: one warp per row walks the L
+// levels (alpha kept one step behind exactly as in the dense row pass); the
+// next level's alpha and rho load while the current level reduces, and the
+// next row's candidates, CSC slots, similarities, per-level scalars and b
+// load while the current row runs.  The column index (CSC: for every column
+// j the entries (k, q) with cand[k][q] = j, in entry order) is built on the
+// GPU by a stable radix sort of the entries by column.  The row pass writes
+// each positive off-diagonal responsibility straight to its CSC slot and
+// sets the slot's bit in a per-level bitmap zeroed before the pass (most
+// responsibilities are negative, so a few scattered writes per row); the
+// column statistics read the bitmap and gather the values of set bits alone,
+// in a fixed order, so the CSC values are neither zeroed nor swept.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
