@@ -803,10 +803,9 @@ __global__ void pivot_rows_kernel(const float* __restrict__ C, int64_t d, int64_
 // one tile; the bucket search is the first pass alone with one candidate),
 // and each query tile scans the candidates from its own bucket on.  The
 // result does not depend on the order: the re-rank sorts by (distance,
-// index).  Queries against another set (hubs) keep the input order: with
-// buckets barely larger than the M2 kept candidates, a query's nearest
-// candidates span buckets that are not adjacent, and the CTAs scanning in
-// step share candidate tiles in L2 (measured faster).
+// index).  Queries against another set (hubs) keep the input order: there
+// the heap inserts of the first tiles dominate (M2 = 80 for M = 64), and
+// buckets of one or four tiles of hubs measured no faster.
 cudaError_t launch_knn_tc(const float* Q, int64_t Nq, const float* C, const int32_t* cid, int64_t Nc, int64_t d, int M,
                           int M2, int32_t* idx, float* dist, cudaStream_t st, int64_t* launches) {
     if (M2 > KT_MAXM2 || M2 < M || d > 64) return cudaErrorInvalidValue;

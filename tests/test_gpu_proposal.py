@@ -71,10 +71,8 @@ def test_knn_tensor_cores_match_cuda_cores(report):
     same = (i_tc == i_cc).all(dim=1).float().mean().item()
     report(rows_identical=same)
     assert same == 1.0 and torch.equal(d_tc, d_cc)
-    # 700 candidates: one pass in input order; 2500: queries and candidates
-    # sorted by their nearest of 19 pivots first (different orders for the
-    # two sets), which must not change the result
-    for ns in (700, 2500):
+    # subsets of several sizes (queries never take their own point)
+    for ns in (700, 2500, 5000):
         sub = torch.from_numpy(np.sort(np.random.default_rng(1).choice(20000, ns, replace=False)).astype(np.int32)).to(DEV)
         s_tc, e_tc = hap.knn_subset(Xt, sub, 48, method="tensor_cores")
         s_cc, e_cc = hap.knn_subset(Xt, sub, 48, method="cuda_cores")
