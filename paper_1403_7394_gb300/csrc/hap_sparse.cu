@@ -395,20 +395,31 @@ __global__ void sparse_exemplars_kernel(const int32_t* __restrict__ cand, const 
 
 // NS^l = sum_i s(i, e_i) with s = -||x_i - x_e||^2 in FP64 from the points
 // (preference on self-assignments); one CTA per level, fixed-order tree
-__global__ void netsim_points_kernel(const float* __restrict__ X, int64_t d, const int32_t* __restrict__ e,
-                                     const float* __restrict__ pref, int N, double* __restrict__ ns) {
+// NS^l = sum_i -||x_i - x_{e_i}||^2 (the preference where e_i = i) in FP64
+// from the points: kNsChunks fixed chunks of the points per level, each
+// summed by a fixed tree in one CTA, then the chunks in order by one thread
+// per level, so the value does not depend on the launch.  ns holds
+// L * (kNsChunks + 1) doubles: the chunk sums, then NS^0 .. NS^{L-1}.
+constexpr int kNsChunks = 128;
+
+__global__ void __launch_bounds__(256) netsim_points_kernel(const float* __restrict__ X, int64_t d,
+                                                            const int32_t* __restrict__ e,
+                                                            const float* __restrict__ pref, int N,
+                                                            double* __restrict__ ns) {
     __shared__ double part[256];
-    const int l = blockIdx.x;
+    const int c = blockIdx.x, l = blockIdx.y;
+    const int64_t per = ((int64_t)N + kNsChunks - 1) / kNsChunks;
+    const int64_t i0 = (int64_t)c * per, i1 = i0 + per < N ? i0 + per : N;
     double acc = 0.0;
-    for (int64_t i = threadIdx.x; i < N; i += blockDim.x) {
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
         const int64_t j = e[(int64_t)l * N + i];
         if (j == i) { acc += (double)pref[(int64_t)l * N + i]; continue; }
-        double s = 0.0;
+        double sq = 0.0;
         for (int64_t k = 0; k < d; ++k) {
             const double df = (double)X[i * d + k] - (double)X[j * d + k];
-            s += df * df;
+            sq += df * df;
         }
-        acc -= s;
+        acc -= sq;
     }
     part[threadIdx.x] = acc;
     __syncthreads();
@@ -416,7 +427,22 @@ __global__ void netsim_points_kernel(const float* __restrict__ X, int64_t d, con
         if ((int)threadIdx.x < o) part[threadIdx.x] += part[threadIdx.x + o];
         __syncthreads();
     }
-    if (threadIdx.x == 0) ns[l] = part[0];
+    if (threadIdx.x == 0) ns[(int64_t)l * kNsChunks + c] = part[0];
+}
+
+__global__ void netsim_finish_kernel(double* __restrict__ ns, int L) {
+    const int l = threadIdx.x;
+    if (l >= L) return;
+    double t = 0.0;
+    for (int c = 0; c < kNsChunks; ++c) t += ns[(int64_t)l * kNsChunks + c];
+    ns[(int64_t)L * kNsChunks + l] = t;
+}
+
+cudaError_t launch_netsim_points(const float* X, int64_t d, const int32_t* e, const float* pref, int N, int L,
+                                 double* ns, cudaStream_t st) {
+    netsim_points_kernel<<<dim3(kNsChunks, (unsigned)L), 256, 0, st>>>(X, d, e, pref, N, ns);
+    netsim_finish_kernel<<<1, 32 * ((L + 31) / 32), 0, st>>>(ns, L);
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -458,7 +484,7 @@ struct hap_sparse {
     int* hoff = nullptr;
     int64_t* tsum = nullptr;      // scan tile sums
     int32_t* e = nullptr;
-    double* ns = nullptr;
+    double* ns = nullptr;         // [L][kNsChunks] chunk sums of the net similarity, then [L] totals
     unsigned* status = nullptr;
     const float* X = nullptr;  // points of the last hap_sparse_set_candidates (borrowed for NS)
     int64_t d = 0;
@@ -511,7 +537,7 @@ int hap_sparse_create(int64_t N, int L, int K, const float* prefs, float damping
               cudaMalloc(&h->b, (size_t)N * ((L + 3) & ~3) * 4) == cudaSuccess &&
               cudaMalloc(&h->rdiag, vec) == cudaSuccess &&
               cudaMalloc(&h->cptr, (N + 1) * 8) == cudaSuccess && cudaMalloc(&h->cent, nk * 4) == cudaSuccess &&
-              cudaMalloc(&h->e, (size_t)L * N * 4) == cudaSuccess && cudaMalloc(&h->ns, (size_t)L * 8) == cudaSuccess &&
+              cudaMalloc(&h->e, (size_t)L * N * 4) == cudaSuccess && cudaMalloc(&h->ns, (size_t)L * (kNsChunks + 1) * 8) == cudaSuccess &&
               cudaMalloc(&h->status, 16) == cudaSuccess && cudaMalloc(&h->pos, nk * 4) == cudaSuccess &&
               cudaMalloc(&h->cval, mat) == cudaSuccess && cudaMalloc(&h->cnt, (N + 1) * 4) == cudaSuccess &&
               cudaMalloc(&h->cbits, (size_t)L * ((nk + 31) / 32) * 4) == cudaSuccess &&
@@ -680,10 +706,9 @@ int hap_net_similarity_points(const float* X, int64_t N, int64_t d, int L, const
     if (!X || !e || !pref || !ns_host || N < 1 || L < 1) return HAP_EINVAL;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     double* dns = nullptr;
-    SCU(cudaMallocAsync(&dns, (size_t)L * 8, st));
-    netsim_points_kernel<<<L, 256, 0, st>>>(X, d, e, pref, (int)N, dns);
-    SCU(cudaGetLastError());
-    SCU(cudaMemcpyAsync(ns_host, dns, (size_t)L * 8, cudaMemcpyDeviceToHost, st));
+    SCU(cudaMallocAsync(&dns, (size_t)L * (kNsChunks + 1) * 8, st));
+    SCU(launch_netsim_points(X, d, e, pref, (int)N, L, dns, st));
+    SCU(cudaMemcpyAsync(ns_host, dns + (size_t)L * kNsChunks, (size_t)L * 8, cudaMemcpyDeviceToHost, st));
     SCU(cudaFreeAsync(dns, st));
     SCU(cudaStreamSynchronize(st));
     return HAP_OK;
@@ -695,10 +720,9 @@ int hap_sparse_net_similarity(hap_sparse* h, double* ns) {
     sparse_exemplars_kernel<<<(unsigned)((rows * 32 + 255) / 256), 256, 0, h->stream>>>(
         h->cand, h->A, h->R, h->b, h->N, h->L, h->K, h->pending, h->lam, 1.0f - h->lam, h->e, nullptr);
     SCU(cudaGetLastError());
-    netsim_points_kernel<<<h->L, 256, 0, h->stream>>>(h->X, h->d, h->e, h->pref, h->N, h->ns);
-    SCU(cudaGetLastError());
-    h->launches += 2;
-    SCU(cudaMemcpyAsync(ns, h->ns, (size_t)h->L * 8, cudaMemcpyDeviceToHost, h->stream));
+    SCU(launch_netsim_points(h->X, h->d, h->e, h->pref, h->N, h->L, h->ns, h->stream));
+    h->launches += 3;
+    SCU(cudaMemcpyAsync(ns, h->ns + (size_t)h->L * kNsChunks, (size_t)h->L * 8, cudaMemcpyDeviceToHost, h->stream));
     SCU(cudaStreamSynchronize(h->stream));
     return HAP_OK;
 }

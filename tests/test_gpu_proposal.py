@@ -272,6 +272,28 @@ def test_sparse_hub_columns_against_reference(report):
     assert all(v <= 1e-4 for v in errs.values()), errs
 
 
+def test_net_similarity_points_matches_fp64():
+    """NS^l = sum_i -||x_i - x_{e_i}||^2 (preference where e_i = i) from the
+    points, in FP64 on the GPU (chunked, fixed order), against numpy FP64;
+    N not a multiple of the chunk count, exemplars mixing self and others."""
+    hap = hapm()
+    rng = np.random.default_rng(12)
+    N, d, L = 5003, 7, 3
+    X32 = rng.normal(size=(N, d)).astype(np.float32)
+    e = rng.integers(0, N, size=(L, N)).astype(np.int32)
+    e[:, ::5] = np.arange(N, dtype=np.int32)[::5]
+    pref = (-rng.uniform(1, 5, size=(L, N))).astype(np.float32)
+    got = hap.net_similarity_points(torch.from_numpy(X32).to(DEV), torch.from_numpy(e).to(DEV),
+                                    torch.from_numpy(pref).to(DEV))
+    X64 = X32.astype(np.float64)
+    want = np.empty(L)
+    for l in range(L):
+        dd = ((X64 - X64[e[l]]) ** 2).sum(axis=1)
+        self_ = e[l] == np.arange(N)
+        want[l] = np.where(self_, pref[l].astype(np.float64), -dd).sum()
+    np.testing.assert_allclose(got, want, rtol=1e-12)
+
+
 def test_sparse_candidates_rejected():
     hap = hapm()
     N, K = 50, 4
