@@ -296,6 +296,7 @@ constexpr int KT_RING_MAX = 4;  // candidate K-chunk stages (fewer when shared m
 constexpr int KT_MAXM2 = 80;    // candidates kept per row by the first pass
 constexpr int KT_PEND = 32;     // per-row buffer of threshold-passing candidates of one 32-column batch
 constexpr int KT_THREADS = 192; // 4 epilogue warps, 1 producer warp, 1 MMA warp
+constexpr int KT_HEAP_D = 4;    // arity of the per-row candidate heap
 
 struct KnnTcArgs {
     const int32_t* cid;   // candidate c's global id (null: c)
@@ -422,7 +423,7 @@ __global__ void __launch_bounds__(KT_THREADS, 1) knn_tc_kernel(const __grid_cons
         // heap keeps operand columns, mapped to candidates on output
         const int skip = p.self_col ? (row < p.Nq ? p.self_col[row] : -1) : (p.exclude_self ? row : -1);
         // the M2 smallest first-pass keys ||c||^2 - 2 q.c of this row as a
-        // max-heap in shared memory (root = current threshold); columns below
+        // KT_HEAP_D-ary max-heap in shared memory (root = current threshold); columns below
         // the threshold are first appended to a short buffer (cheap even when
         // few lanes of the warp take the branch) and then pushed into the
         // heap by all lanes with pending candidates together
@@ -430,10 +431,13 @@ __global__ void __launch_bounds__(KT_THREADS, 1) knn_tc_kernel(const __grid_cons
         float thr = kInf, vthr = -kInf;  // key < thr  <=>  v > vthr = -thr / 2
         const int M2 = p.M2;
         auto heap_push = [&](float dv, int j) {
+            // KT_HEAP_D-ary max-heap: children of node c are D c + 1 .. D c + D,
+            // so a sift passes fewer levels than in a binary heap and the
+            // child loads of a level are independent
             if (cnt < M2) {  // sift up
                 int c = cnt++;
                 while (c > 0) {
-                    const int par = (c - 1) >> 1;
+                    const int par = (c - 1) / KT_HEAP_D;
                     const float pd = tdist[par * BM + tid];
                     if (pd >= dv) break;
                     tdist[c * BM + tid] = pd;
@@ -445,12 +449,16 @@ __global__ void __launch_bounds__(KT_THREADS, 1) knn_tc_kernel(const __grid_cons
             } else if (dv < tdist[tid]) {  // replace the root, sift down
                 int c = 0;
                 for (;;) {
-                    int ch = 2 * c + 1;
-                    if (ch >= M2) break;
-                    float cd = tdist[ch * BM + tid];
-                    if (ch + 1 < M2) {
-                        const float cd2 = tdist[(ch + 1) * BM + tid];
-                        if (cd2 > cd) { cd = cd2; ++ch; }
+                    const int ch0 = KT_HEAP_D * c + 1;
+                    if (ch0 >= M2) break;
+                    float cd = tdist[ch0 * BM + tid];
+                    int ch = ch0;
+#pragma unroll
+                    for (int u = 1; u < KT_HEAP_D; ++u) {
+                        if (ch0 + u < M2) {
+                            const float x = tdist[(ch0 + u) * BM + tid];
+                            if (x > cd) { cd = x; ch = ch0 + u; }
+                        }
                     }
                     if (cd <= dv) break;
                     tdist[c * BM + tid] = cd;
