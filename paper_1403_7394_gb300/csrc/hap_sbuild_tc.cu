@@ -294,9 +294,16 @@ __global__ void pack_operands_kernel(const float* __restrict__ X, int N, int d, 
 // the first pass.
 constexpr int KT_RING_MAX = 4;  // candidate K-chunk stages (fewer when shared memory is short)
 constexpr int KT_MAXM2 = 80;    // candidates kept per row by the first pass
-constexpr int KT_PEND = 32;     // per-row buffer of threshold-passing candidates of one 32-column batch
+// per-row buffer of threshold-passing candidates of one 32-column batch (128-wide
+// tiles) or of one 16-column half batch (256-wide tiles, where shared memory is short)
+__host__ __device__ constexpr int knn_pend(int kbn) { return kbn == 256 ? 16 : 32; }
 constexpr int KT_THREADS = 192; // 4 epilogue warps, 1 producer warp, 1 MMA warp
 constexpr int KT_HEAP_D = 4;    // arity of the per-row candidate heap
+// candidates per tile KBN: 256 (one M = 128, N = 256 MMA per K step) where
+// shared memory allows, else 128
+__host__ __device__ constexpr uint32_t knn_idesc(int kbn) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kbn >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
 
 struct KnnTcArgs {
     const int32_t* cid;   // candidate c's global id (null: c)
@@ -311,13 +318,14 @@ struct KnnTcArgs {
     unsigned* status;
 };
 
-// at least 116 KB: one CTA per SM, so its 256-column TMEM allocation never waits
-size_t knn_tc_smem_bytes(int kchunks, int ring, int M2) {
-    const size_t b = 1024 + (size_t)kchunks * BM * BK * 2 + (size_t)ring * BN * BK * 2 + (size_t)M2 * BM * 8 +
-                     (size_t)KT_PEND * BM * 8;
+// at least 116 KB: one CTA per SM, so its 2 KBN-column TMEM allocation never waits
+size_t knn_tc_smem_bytes(int kchunks, int ring, int M2, int kbn) {
+    const size_t b = 1024 + (size_t)kchunks * BM * BK * 2 + (size_t)ring * kbn * BK * 2 + (size_t)M2 * BM * 8 +
+                     (size_t)knn_pend(kbn) * BM * 8;
     return b < 116 * 1024 ? 116 * 1024 : b;
 }
 
+template <int KBN>
 __global__ void __launch_bounds__(KT_THREADS, 1) knn_tc_kernel(const __grid_constant__ CUtensorMap tmA,
                                                               const __grid_constant__ CUtensorMap tmB,
                                                               const KnnTcArgs p) {
@@ -325,12 +333,13 @@ __global__ void __launch_bounds__(KT_THREADS, 1) knn_tc_kernel(const __grid_cons
     const uint32_t raw = smem_addr(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
     const uint32_t sA = base;                                          // kchunks x [128][64] BF16
-    const uint32_t sB = sA + (uint32_t)p.kchunks * BM * BK * 2;        // ring x [128][64] BF16
+    const uint32_t sB = sA + (uint32_t)p.kchunks * BM * BK * 2;        // ring x [256][64] BF16
     const int R = p.ring;
-    float* tdist = reinterpret_cast<float*>(smem_raw + (sB + R * BN * BK * 2 - raw));  // heap [M2][128]
+    float* tdist = reinterpret_cast<float*>(smem_raw + (sB + R * KBN * BK * 2 - raw));  // heap [M2][128]
     int* tidx = reinterpret_cast<int*>(tdist + p.M2 * BM);                                   // [M2][128]
-    float* pdist = reinterpret_cast<float*>(tidx + p.M2 * BM);                               // [KT_PEND][128]
-    int* pidx = reinterpret_cast<int*>(pdist + KT_PEND * BM);                                // [KT_PEND][128]
+    constexpr int PEND = knn_pend(KBN);
+    float* pdist = reinterpret_cast<float*>(tidx + p.M2 * BM);  // [PEND][128]
+    int* pidx = reinterpret_cast<int*>(pdist + PEND * BM);      // [PEND][128]
     __shared__ uint64_t bars[1 + 2 * KT_RING_MAX + 4];  // a_full, b_full[R], b_empty[R], acc_full[2], acc_empty[2]
     __shared__ uint32_t tmem_slot;
     __shared__ int s_abort;
@@ -339,7 +348,7 @@ __global__ void __launch_bounds__(KT_THREADS, 1) knn_tc_kernel(const __grid_cons
     const uint32_t b_full = a_full + 8, b_empty = b_full + 8 * KT_RING_MAX;
     const uint32_t acc_full = b_empty + 8 * KT_RING_MAX, acc_empty = acc_full + 16;
     const int m0 = blockIdx.x * BM;
-    const int ntiles = (p.Nc + BN - 1) / BN;
+    const int ntiles = (p.Nc + KBN - 1) / KBN;
     // With queries and candidates sorted by spatial bucket, candidate tiles
     // are visited from the one holding the first candidate of this query
     // tile's first bucket (wrapping), so the nearest candidates come first
@@ -354,7 +363,7 @@ __global__ void __launch_bounds__(KT_THREADS, 1) knn_tc_kernel(const __grid_cons
             const int mid = (lo + hi) >> 1;
             if (p.ckey[mid] < key) lo = mid + 1; else hi = mid;
         }
-        t0 = (lo < p.Nc ? lo : p.Nc - 1) / BN;
+        t0 = (lo < p.Nc ? lo : p.Nc - 1) / KBN;
     }
     if (tid == 0) {
         mbar_init(a_full, 1);
@@ -369,7 +378,7 @@ __global__ void __launch_bounds__(KT_THREADS, 1) knn_tc_kernel(const __grid_cons
         s_abort = 0;
         fence_mbarrier_init();
     }
-    if (warp == 0) tmem_alloc(smem_addr(&tmem_slot), 256);
+    if (warp == 0) tmem_alloc(smem_addr(&tmem_slot), 2 * KBN);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -389,8 +398,8 @@ __global__ void __launch_bounds__(KT_THREADS, 1) knn_tc_kernel(const __grid_cons
                 }
                 const int t = g / p.kchunks, kc = g - t * p.kchunks;
                 const int tt = t0 + t < ntiles ? t0 + t : t0 + t - ntiles;
-                mbar_arrive_expect_tx(b_full + 8 * st, BN * BK * 2);
-                tma_load_2d(sB + (uint32_t)st * BN * BK * 2, &tmB, kc * BK, tt * BN, b_full + 8 * st);
+                mbar_arrive_expect_tx(b_full + 8 * st, KBN * BK * 2);
+                tma_load_2d(sB + (uint32_t)st * KBN * BK * 2, &tmB, kc * BK, tt * KBN, b_full + 8 * st);
             }
         }
     } else if (warp == 5) {
@@ -404,11 +413,11 @@ __global__ void __launch_bounds__(KT_THREADS, 1) knn_tc_kernel(const __grid_cons
                     const int g = t * p.kchunks + kc, st = g % R;
                     if (!(ok = mbar_wait(b_full + 8 * st, (uint32_t)((g / R) & 1), p.status))) break;
                     tc_fence_after();
-                    const uint32_t a_s = sA + (uint32_t)kc * BM * BK * 2, b_s = sB + (uint32_t)st * BN * BK * 2;
+                    const uint32_t a_s = sA + (uint32_t)kc * BM * BK * 2, b_s = sB + (uint32_t)st * KBN * BK * 2;
 #pragma unroll
                     for (int kk = 0; kk < BK / 16; ++kk)
-                        umma_bf16(tmem + (uint32_t)(buf * BN), desc_kmajor_sw128(a_s + 32 * kk),
-                                  desc_kmajor_sw128(b_s + 32 * kk), kIdesc, (kc > 0 || kk > 0) ? 1u : 0u);
+                        umma_bf16(tmem + (uint32_t)(buf * KBN), desc_kmajor_sw128(a_s + 32 * kk),
+                                  desc_kmajor_sw128(b_s + 32 * kk), knn_idesc(KBN), (kc > 0 || kk > 0) ? 1u : 0u);
                     umma_commit(b_empty + 8 * st);
                 }
                 if (!ok) break;
@@ -482,41 +491,46 @@ __global__ void __launch_bounds__(KT_THREADS, 1) knn_tc_kernel(const __grid_cons
             }
             tc_fence_after();
             const int tt = t0 + t < ntiles ? t0 + t : t0 + t - ntiles;
-            const bool full_tile = (tt + 1) * BN <= p.Nc;
+            const bool full_tile = (tt + 1) * KBN <= p.Nc;
             // 64 columns per round: two TMEM loads in flight, one wait; the
             // accumulator goes back to the MMA warp as soon as the last
             // round's values are in registers
 #pragma unroll 1
-            for (int hh = 0; hh < BN / 64; ++hh) {
+            for (int hh = 0; hh < KBN / 64; ++hh) {
                 uint32_t r[2][32];
                 __syncwarp();
-                const uint32_t ta = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(buf * BN + 64 * hh);
+                const uint32_t ta = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(buf * KBN + 64 * hh);
                 tmem_ld_32x32b_x32_nowait(ta, r[0]);
                 tmem_ld_32x32b_x32_nowait(ta + 32, r[1]);
                 tmem_wait_ld(r[0]);
                 tmem_tie(r[1]);
-                if (hh == BN / 64 - 1) {
+                if (hh == KBN / 64 - 1) {
                     tc_fence_before();
                     mbar_arrive(acc_empty + 8 * buf);
                 }
 #pragma unroll
                 for (int b = 0; b < 2; ++b) {
-                    const int jb = tt * BN + 64 * hh + 32 * b;
-                    int np = 0;
+                    const int jb = tt * KBN + 64 * hh + 32 * b;
                     if (max32(r[b]) > vthr) {
+                        // PEND columns at a time, each part buffered then
+                        // pushed (a later part sees the tightened threshold)
 #pragma unroll
-                        for (int q = 0; q < 32; ++q) {
-                            const float v = __uint_as_float(r[b][q]);
-                            if (v > vthr && (full_tile || jb + q < p.Nc)) {
-                                pdist[np * BM + tid] = -2.f * v;
-                                pidx[np * BM + tid] = jb + q;
-                                ++np;
+                        for (int hq = 0; hq < 32 / PEND; ++hq) {
+                            int np = 0;
+#pragma unroll
+                            for (int q = PEND * hq; q < PEND * hq + PEND; ++q) {
+                                const float v = __uint_as_float(r[b][q]);
+                                if (v > vthr && (full_tile || jb + q < p.Nc)) {
+                                    pdist[np * BM + tid] = -2.f * v;
+                                    pidx[np * BM + tid] = jb + q;
+                                    ++np;
+                                }
+                            }
+                            for (int k = 0; k < np; ++k) {
+                                const int j = pidx[k * BM + tid];
+                                if (j != skip) heap_push(pdist[k * BM + tid], j);
                             }
                         }
-                    }
-                    for (int k = 0; k < np; ++k) {
-                        const int j = pidx[k * BM + tid];
-                        if (j != skip) heap_push(pdist[k * BM + tid], j);
                     }
                 }
             }
@@ -529,7 +543,7 @@ __global__ void __launch_bounds__(KT_THREADS, 1) knn_tc_kernel(const __grid_cons
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, 256);
+    if (warp == 0) tmem_dealloc(tmem, 2 * KBN);
 }
 
 // Exact re-rank of the first pass's candidates: one warp per query row,
@@ -645,12 +659,12 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
     return fn;
 }
 
-bool encode_operand_map(CUtensorMap* map, void* ptr, int64_t rows, int64_t kpad) {
+bool encode_operand_map(CUtensorMap* map, void* ptr, int64_t rows, int64_t kpad, int box_rows = BM) {
     auto enc = get_encode();
     if (!enc) return false;
     const cuuint64_t dims[2] = {(cuuint64_t)kpad, (cuuint64_t)rows};
     const cuuint64_t strides[1] = {(cuuint64_t)kpad * 2};
-    const cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)BM};
+    const cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
     const cuuint32_t estr[2] = {1, 1};
     return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ptr, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
@@ -725,12 +739,33 @@ struct KnnOrder {
 
 // rerank 0: the first pass alone, its M2 candidates per query straight into
 // idx [Nq][M2] (unordered, BF16-split keys; dist unused)
+// wide: 256 candidates per tile where they fit (the MMA stream bounds the
+// kNN of a set among itself); else 128 (a subset search is bound by the heap
+// inserts of its first tiles, which wider tiles only make longer)
 static cudaError_t knn_tc_core(const float* Q, int64_t Nq, const float* C, const int32_t* cid, int64_t Nc, int64_t d,
                                int M, int M2, int32_t* idx, float* dist, const KnnOrder& ord, int exclude_self,
-                               const int32_t* self_col, int rerank, cudaStream_t st) {
+                               const int32_t* self_col, int rerank, bool wide, cudaStream_t st) {
     if (M2 > KT_MAXM2 || M2 < M || d > 64) return cudaErrorInvalidValue;
     const int64_t kpad = (3 * d + 2 + BK - 1) / BK * BK;
-    const int64_t qpad = (Nq + BM - 1) / BM * BM, cpad = (Nc + BN - 1) / BN * BN;
+    // tile width and ring: 256 candidates per tile when at least three
+    // K-chunk stages fit beside the query operand and the heaps, else 128
+    int dev = 0, smem_limit = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&smem_limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const int kchunks = (int)(kpad / BK);
+    auto ring_for = [&](int kbn) {
+        int r = KT_RING_MAX;
+        while (r > 2 && knn_tc_smem_bytes(kchunks, r, M2, kbn) > (size_t)smem_limit) --r;
+        return r;
+    };
+    int KBN = 256, ring = ring_for(256);
+    if (!wide || ring < 3 || knn_tc_smem_bytes(kchunks, ring, M2, 256) > (size_t)smem_limit) {
+        KBN = 128;
+        ring = ring_for(128);
+    }
+    const size_t smem = knn_tc_smem_bytes(kchunks, ring, M2, KBN);
+    if (smem > (size_t)smem_limit) return cudaErrorNotSupported;
+    const int64_t qpad = (Nq + BM - 1) / BM * BM, cpad = (Nc + KBN - 1) / KBN * KBN;
     const size_t aB = (size_t)qpad * kpad * 2, bB = (size_t)cpad * kpad * 2;
     const size_t off_b = (aB + 1023) / 1024 * 1024;
     const size_t off_cand = off_b + (bB + 1023) / 1024 * 1024;
@@ -751,7 +786,7 @@ static cudaError_t knn_tc_core(const float* Q, int64_t Nq, const float* C, const
         pack_knn_kernel<<<(unsigned)Nc, 64, 0, st>>>(C, ord.cperm, (int)Nc, (int)d, (int)kpad, 1, B);
         if ((err = cudaGetLastError()) != cudaSuccess) break;
         CUtensorMap mA, mB;
-        if (!encode_operand_map(&mA, A, qpad, kpad) || !encode_operand_map(&mB, B, cpad, kpad)) {
+        if (!encode_operand_map(&mA, A, qpad, kpad) || !encode_operand_map(&mB, B, cpad, kpad, KBN)) {
             err = cudaErrorNotSupported;
             break;
         }
@@ -769,20 +804,11 @@ static cudaError_t knn_tc_core(const float* Q, int64_t Nq, const float* C, const
         a.kchunks = (int)(kpad / BK);
         a.cand = rerank ? cand : idx;
         a.status = status;
-        int dev = 0, smem_limit = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&smem_limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-        a.ring = KT_RING_MAX;
-        while (a.ring > 2 && knn_tc_smem_bytes(a.kchunks, a.ring, M2) > (size_t)smem_limit) --a.ring;
-        const size_t smem = knn_tc_smem_bytes(a.kchunks, a.ring, M2);
-        if (smem > (size_t)smem_limit) {
-            err = cudaErrorNotSupported;
+        a.ring = ring;
+        auto kern = KBN == 256 ? knn_tc_kernel<256> : knn_tc_kernel<128>;
+        if ((err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
             break;
-        }
-        if ((err = cudaFuncSetAttribute(knn_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
-            cudaSuccess)
-            break;
-        knn_tc_kernel<<<(unsigned)(qpad / BM), KT_THREADS, smem, st>>>(mA, mB, a);
+        kern<<<(unsigned)(qpad / BM), KT_THREADS, smem, st>>>(mA, mB, a);
         if ((err = cudaGetLastError()) != cudaSuccess || !rerank) break;
         knn_rerank_kernel<<<(unsigned)((Nq * 32 + 255) / 256), 256, 0, st>>>(Q, C, cid, (int)Nq, (int)d, M2, M, cand,
                                                                             status, idx, dist);
@@ -831,7 +857,7 @@ cudaError_t launch_knn_tc(const float* Q, int64_t Nq, const float* C, const int3
                 inverse_subset_kernel<<<(unsigned)((Nc + 255) / 256), 256, 0, st>>>(cid, Nc, Nq, inv);
                 if ((err = cudaGetLastError()) != cudaSuccess) break;
             }
-            err = knn_tc_core(Q, Nq, C, cid, Nc, d, M, M2, idx, dist, KnnOrder{}, 0, inv, 1, st);
+            err = knn_tc_core(Q, Nq, C, cid, Nc, d, M, M2, idx, dist, KnnOrder{}, 0, inv, 1, false, st);
         } while (0);
         if (launches) *launches += (cid ? 1 : 0) + 4;  // inverse map; two operand packs, first pass, re-rank
         cudaError_t e2 = cudaFreeAsync(inv, st);
@@ -839,7 +865,7 @@ cudaError_t launch_knn_tc(const float* Q, int64_t Nq, const float* C, const int3
     }
     if (P < 8) {
         if (launches) *launches += 4;  // two operand packs, the first pass, the re-rank
-        return knn_tc_core(Q, Nq, C, cid, Nc, d, M, M2, idx, dist, KnnOrder{}, 1, nullptr, 1, st);
+        return knn_tc_core(Q, Nq, C, cid, Nc, d, M, M2, idx, dist, KnnOrder{}, 1, nullptr, 1, true, st);
     }
     int bits = 1;
     while (((int64_t)1 << bits) < P) ++bits;
@@ -860,14 +886,14 @@ cudaError_t launch_knn_tc(const float* Q, int64_t Nq, const float* C, const int3
         pivot_rows_kernel<<<(unsigned)P, 64, 0, st>>>(C, d, Nc / P, piv);
         if ((err = cudaGetLastError()) != cudaSuccess) break;
         // the approximately nearest pivot (first-pass keys) is bucket enough
-        if ((err = knn_tc_core(Q, Nq, piv, nullptr, P, d, 1, 1, bkt, nullptr, KnnOrder{}, 0, nullptr, 0, st)) !=
+        if ((err = knn_tc_core(Q, Nq, piv, nullptr, P, d, 1, 1, bkt, nullptr, KnnOrder{}, 0, nullptr, 0, true, st)) !=
             cudaSuccess)
             break;
         if ((err = stable_sort_keys(bkt, Nq, bits, key, perm, st)) != cudaSuccess) break;
         KnnOrder ord;
         ord.qperm = ord.cperm = perm;
         ord.qkey = ord.ckey = key;
-        err = knn_tc_core(Q, Nq, C, cid, Nc, d, M, M2, idx, dist, ord, 1, nullptr, 1, st);
+        err = knn_tc_core(Q, Nq, C, cid, Nc, d, M, M2, idx, dist, ord, 1, nullptr, 1, true, st);
     } while (0);
     cudaError_t e2 = cudaFreeAsync(raw, st);
     return err != cudaSuccess ? err : e2;
