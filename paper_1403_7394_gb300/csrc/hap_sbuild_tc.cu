@@ -276,12 +276,13 @@ __global__ void pack_operands_kernel(const float* __restrict__ X, int N, int d, 
 }
 
 // ---- nearest neighbours with tensor-core candidate distances ----------------
-// One CTA per 128 query rows streams every 128-column tile of candidates:
-// warp 4 loads the query operand once and the candidate K-chunks through a
-// TMA ring, warp 5 issues the tcgen05.mma contractions into one of two TMEM
-// accumulators (128 columns each) so that the next tile's products overlap
-// the epilogue of this one, and warps 0-3 (one query row per thread, its
-// TMEM lane) turn dot products into squared distances
+// One CTA per 128 query rows streams every KBN-column tile of candidates
+// (KBN = 256 or 128): warp 4 loads the query operand once and the candidate
+// K-chunks through a TMA ring, warp 5 issues the tcgen05.mma contractions
+// into one of two TMEM accumulators (KBN columns each) so that the next
+// tile's products overlap the epilogue of this one, and warps 0-3 (one
+// query row per thread, its TMEM lane) turn dot products into squared
+// distances
 // ||q||^2 + ||c||^2 - 2 q.c and keep the M2 smallest per row in shared
 // memory.  The candidate norm enters the contraction as two extra K columns
 // (A: 1, 1; B: -||c||^2/2 split into BF16 hi and lo), so the accumulator
