@@ -186,20 +186,30 @@ __global__ void __launch_bounds__(256, 4) sparse_rowpass_kernel(const SparseArgs
                 p.tau[vo + i] = tauv;
                 if (l > 0) p.phi[vo - N + i] = m1;
             }
+            float rnv[2];
+            bool wpos[2];
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
+                wpos[h] = false;
                 if (!has[h]) continue;
                 const float mx = jq[h] == k1 ? m2 : m1;
                 const float rn = damp(r[h], __fadd_rn(x[h], fminf(tauv, -mx)), p.lam, p.oml);
                 Rl[32 * h] = rn;
                 const bool diag = jq[h] == (int)i;
                 if (diag) p.rdiag[vo + i] = rn;
-                // only positive off-diagonal responsibilities are written
-                // (a few per row), each with its slot's bit
-                if (!diag && rn > 0.f) {
-                    cv[pq[h]] = rn;
-                    atomicOr(cb + (pq[h] >> 5), 1u << (pq[h] & 31));
-                }
+                rnv[h] = rn;
+                wpos[h] = !diag && rn > 0.f;
+            }
+            // only positive off-diagonal responsibilities are written (a few
+            // per row), each with its slot's bit; one warp vote skips the
+            // common case where no lane has one
+            if (__any_sync(0xffffffffu, wpos[0] || wpos[1])) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h)
+                    if (wpos[h]) {
+                        cv[pq[h]] = rnv[h];
+                        atomicOr(cb + (pq[h] >> 5), 1u << (pq[h] & 31));
+                    }
             }
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
