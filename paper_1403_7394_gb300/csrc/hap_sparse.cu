@@ -125,8 +125,6 @@ __global__ void __launch_bounds__(256, 4) sparse_rowpass_kernel(const SparseArgs
         // vo is level l's offset in the [L][N] vectors
         float* Al = p.A + i * K + lane;
         float* Rl = p.R + i * K + lane;
-        float* cv = p.cval;
-        unsigned* cb = p.cbits;
         int64_t vo = 0;
         float a[2], r[2];
 #pragma unroll
@@ -136,7 +134,7 @@ __global__ void __launch_bounds__(256, 4) sparse_rowpass_kernel(const SparseArgs
         }
         float4 bn[2] = {f4_splat(0.f), f4_splat(0.f)};
         float c_prev = 0.f;
-        for (int l = 0; l < L; ++l, Al += NK, Rl += NK, cv += NK, cb += p.cwords, vo += N) {
+        for (int l = 0; l < L; ++l, Al += NK, Rl += NK, vo += N) {
             if (kMultiChunk) {
                 if ((l & 3) == 0 && l > 0) {
                     bc[0] = bn[0];
@@ -204,6 +202,8 @@ __global__ void __launch_bounds__(256, 4) sparse_rowpass_kernel(const SparseArgs
             // per row), each with its slot's bit; one warp vote skips the
             // common case where no lane has one
             if (__any_sync(0xffffffffu, wpos[0] || wpos[1])) {
+                float* cv = p.cval + l * NK;
+                unsigned* cb = p.cbits + l * p.cwords;
 #pragma unroll
                 for (int h = 0; h < 2; ++h)
                     if (wpos[h]) {
