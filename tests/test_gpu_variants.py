@@ -8,7 +8,7 @@ import torch
 
 from oracle import hap_oracle as H
 from paper_1403_7394_gb300 import workloads as W
-from test_gpu_parity import DEV, TOL, assert_close, gpu_state, hap_mod, make_ctx, problem, to32
+from test_gpu_parity import DEV, assert_close, gpu_state, hap_mod, make_ctx, problem, to32
 
 pytestmark = pytest.mark.gpu
 

@@ -2,7 +2,6 @@
 difference gradients, special cases of candidate selection, and the masked
 (-inf) similarity reading of sparse HAP."""
 import numpy as np
-import pytest
 
 from oracle import hap_oracle as H
 from oracle import proposal_oracle as P
