@@ -550,6 +550,72 @@ __global__ void __launch_bounds__(KT_THREADS, 1) knn_tc_kernel(const __grid_cons
 // Exact re-rank of the first pass's candidates: one warp per query row,
 // FP32 direct-difference distances accumulated in dimension order (the
 // CUDA-core kNN's arithmetic), the M nearest by (distance, global index).
+// (distance, global index) lexicographic order of two candidates
+HAP_DEV bool cand_less(float da, int ga, float db, int gb) { return da < db || (da == db && ga < gb); }
+
+// Bitonic sort of the warp's 32 R candidates into ascending order, element
+// e = R * lane + r in register r of lane e / R: partners R or more elements
+// apart are exchanged by shuffles, nearer ones within the lane.  Then the
+// first M elements go out (index -1 and an infinite distance past the last
+// valid candidate).
+template <int R, int PER>
+HAP_DEV void rerank_emit(const float (&dv)[PER], const int (&gv)[PER], int64_t i, int M,
+                         int32_t* __restrict__ out_idx, float* __restrict__ out_dist) {
+    const int lane = threadIdx.x & 31;
+    float d[R];
+    int g[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        d[r] = r < PER ? dv[r] : kInf;
+        g[r] = r < PER ? gv[r] : 0x7fffffff;
+    }
+#pragma unroll
+    for (int k = 2; k <= 32 * R; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j >= R) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const int e = R * lane + r;
+                    const float od = __shfl_xor_sync(0xffffffffu, d[r], j / R);
+                    const int og = __shfl_xor_sync(0xffffffffu, g[r], j / R);
+                    const bool keep_small = ((e & j) == 0) == ((e & k) == 0);
+                    const bool other_less = cand_less(od, og, d[r], g[r]);
+                    if (keep_small == other_less) {
+                        d[r] = od;
+                        g[r] = og;
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const int r2 = r ^ j;
+                    if (r2 > r) {
+                        const int e = R * lane + r;
+                        const bool ascending = (e & k) == 0;
+                        if (cand_less(d[r2], g[r2], d[r], g[r]) == ascending) {
+                            const float td = d[r];
+                            const int tg = g[r];
+                            d[r] = d[r2];
+                            g[r] = g[r2];
+                            d[r2] = td;
+                            g[r2] = tg;
+                        }
+                    }
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int m = R * lane + r;
+        if (m < M) {
+            out_idx[i * M + m] = g[r] == 0x7fffffff ? -1 : g[r];
+            out_dist[i * M + m] = d[r];
+        }
+    }
+}
+
 __global__ void knn_rerank_kernel(const float* __restrict__ Q, const float* __restrict__ C,
                                   const int32_t* __restrict__ cid, int Nq, int d, int M2, int M,
                                   const int32_t* __restrict__ cand, const unsigned* __restrict__ status,
@@ -583,30 +649,11 @@ __global__ void knn_rerank_kernel(const float* __restrict__ Q, const float* __re
             gv[u] = cid ? cid[j] : j;
         }
     }
-    for (int m = 0; m < M; ++m) {
-        // lane-local best, then a warp argmin by (distance, global index)
-        float bd = kInf;
-        int bg = 0x7fffffff, bu = -1;
-#pragma unroll
-        for (int u = 0; u < PER; ++u)
-            if (dv[u] < bd || (dv[u] == bd && gv[u] < bg)) { bd = dv[u]; bg = gv[u]; bu = u; }
-        float wd = bd;
-        int wg = bg;
-        for (int o = 16; o > 0; o >>= 1) {
-            const float od = __shfl_xor_sync(0xffffffffu, wd, o);
-            const int og = __shfl_xor_sync(0xffffffffu, wg, o);
-            if (od < wd || (od == wd && og < wg)) { wd = od; wg = og; }
-        }
-        if (bu >= 0 && bd == wd && bg == wg) {  // the unique owner removes it
-#pragma unroll
-            for (int u = 0; u < PER; ++u)
-                if (u == bu) { dv[u] = kInf; gv[u] = 0x7fffffff; }
-        }
-        if (lane == 0) {
-            out_idx[i * M + m] = wg == 0x7fffffff ? -1 : wg;
-            out_dist[i * M + m] = wd;
-        }
-    }
+    // ascending (distance, global index) order of all candidates by one
+    // warp-wide bitonic sort; element m is then the m-th nearest
+    if (M2 <= 32) rerank_emit<1>(dv, gv, i, M, out_idx, out_dist);
+    else if (M2 <= 64) rerank_emit<2>(dv, gv, i, M, out_idx, out_dist);
+    else rerank_emit<4>(dv, gv, i, M, out_idx, out_dist);
 }
 
 // Operands of the nearest-neighbour contraction (zero-padded to [npad][kpad]
