@@ -297,7 +297,10 @@ int hap_knn(const float* X, int64_t N, int64_t d, int M, int32_t* idx, float* di
  *                         CUDA-core result whenever the true M nearest are among
  *                         the M + 16 first-pass candidates.  M <= 64; allocates
  *                         stream-ordered scratch; if its bounded waits give up
- *                         (a stalled GPU) every output index is -1.
+ *                         (a stalled GPU) every output index is -1.  From N =
+ *                         1024 the points are first put in a spatial order
+ *                         (nearest of N/128 pivots) so that near candidates are
+ *                         scanned first; that changes the speed, not the result.
  *   HAP_KNN_AUTO          tensor cores when N*N >= 16e6 and M <= 64. */
 #define HAP_KNN_AUTO          0
 #define HAP_KNN_CUDA_CORES    1
