@@ -73,6 +73,17 @@ def dist_env():
     return world, rank, local
 
 
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The largest x over the ranks (x itself with one rank): timed regions are
+    reported by the slowest rank."""
+    if world == 1:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
 def make_inputs(workload: str, seed: int):
     from paper_1403_7394_gb300 import workloads as W
     N, d, L, T, gen, _ = WORKLOADS[workload]
@@ -269,10 +280,7 @@ def main():
     ms = ev0.elapsed_time(ev1)
     launches = ctx.launches - launches0
     rp_ms, rp_n = ctx.row_pass_time(reset=True)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world, dev)
     updates = float(N) * N * L * T
     value = world * args.steps * updates / (ms / 1e3)
 
@@ -290,11 +298,7 @@ def main():
         ctx.exemplars(eh)
         ns = ctx.net_similarity()
     torch.cuda.synchronize()
-    e2e_s = max(time.perf_counter() - t0, 1e-9)
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(max(time.perf_counter() - t0, 1e-9), world, dev)
     e2e_value = world * args.e2e_steps * updates / e2e_s if args.e2e_steps else None
 
     # ---- roofline of the dominant kernel (fused row pass) ----------------------
@@ -438,10 +442,7 @@ def run_batched(args, world, rank, local):
     ms = ev0.elapsed_time(ev1)
     it_ms = float(np.mean([a.elapsed_time(b) for a, b in ev_it])) / T
     launches = bt.query(7) - l0
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world, dev)
     updates = float(sum(n * n * l for n, l in zip(Ns, Ls))) * T
     value = world * args.steps * updates / (ms / 1e3)
     # e2e: host X in, exemplars + NS out
@@ -458,7 +459,7 @@ def run_batched(args, world, rank, local):
         bt.exemplars(eh)
         bt.net_similarity()
     torch.cuda.synchronize()
-    e2e = max(1, args.e2e_steps) * updates * world / (time.perf_counter() - t0)
+    e2e = max(1, args.e2e_steps) * updates * world / max_over_ranks(time.perf_counter() - t0, world, dev)
     peaks, peak_src = measured_peaks()
     s_bytes = 2 if args.s_dtype == "bf16" else 4
     bytes_it = float(sum(n * n * (16 * l + s_bytes) for n, l in zip(Ns, Ls)))
@@ -599,6 +600,10 @@ def run_learned(args, world, rank, local):
         sp.exemplars(e_buf)
         return sp.net_similarity()
 
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
     for _ in range(args.warmup):
         step(e_out)
     torch.cuda.synchronize()
@@ -607,6 +612,8 @@ def run_learned(args, world, rank, local):
     if gpu_id and not gpu_id.startswith("GPU-") and len(gpu_id) == 36:
         gpu_id = "GPU-" + gpu_id
     l0 = hap.proposal_launches() + sp.launches
+    barrier()
+    torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(gpu_id) as clk:
         ev0.record(stream)
@@ -614,19 +621,21 @@ def run_learned(args, world, rank, local):
             ns = step(e_out)
         ev1.record(stream)
         torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1)
+    barrier()
+    ms = max_over_ranks(ev0.elapsed_time(ev1), world, dev)
     launches = hap.proposal_launches() + sp.launches - l0
     # end to end through the public API: points from pinned host memory in,
     # exemplars (host) and the FP64 net similarity out
     Xh = torch.from_numpy(X32).pin_memory()
     eh = torch.empty((L, N), dtype=torch.int32).pin_memory()
+    barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(max(1, args.e2e_steps)):
         Xt.copy_(Xh, non_blocking=True)
         step(eh)
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
     # judging at full N: the learned candidates against the K - 1 exact
     # nearest neighbours as candidates (untimed)
     e_l = e_out.cpu().numpy()
