@@ -8,10 +8,17 @@ net similarity.  The metric counts N^2 * L message updates per iteration.
 
     python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 
-Default workload: 8192 points in 64-D from a 64-component Gaussian mixture
-(means ~ N(0, 4I), sigma = 1), L = 4 levels, 300 iterations, lambda = 0.5,
-preferences = median similarity.  Under torchrun every rank solves its own
-instance (a different seed): weak scaling with no collective on the data path.
+Default workload: the large dense instance, 32768 8x8x3 texture patches
+(d = 192, 256 procedural prototypes plus noise), L = 3 levels, 100 iterations,
+lambda = 0.5, preferences = median similarity (``--workload c1``: 8192 points
+in 64-D from a 64-component Gaussian mixture, L = 4, 300 iterations).  Under
+torchrun every rank solves its own instance (a different seed): weak scaling
+with no collective on the data path.
+
+The CPU baseline is the FP64 reference run row-sharded over every host core
+the process may use (one gloo rank per core, one all-reduce per iteration, the
+multi-GPU design) on a bounded sample of the workload family; the
+single-threaded figure is kept beside it.
 """
 from __future__ import annotations
 
@@ -43,7 +50,9 @@ LEARNED = {"c4": (262144, 32, 3, 64, 400,
                   "dense HAP labels of two N=8192 instances), sparse HAP 400 iterations, c fixed, lambda 0.9")}
 HUB_DIV, K_NEAR = 16, 4  # hubs = N / HUB_DIV; nearest neighbours kept besides the hubs
 CPU_SAMPLE_N = 4096
-CPU_SAMPLE_ITERS = 8  # about 10 s of reference work for the default benchmark's cpu_baseline
+CPU_SAMPLE_ITERS = 8  # about 10 s of single-threaded reference work
+CPU_CORES_N = 8192    # points of the all-cores reference sample
+CPU_CORES_ITERS = 10  # timed iterations of the all-cores reference sample
 
 
 def parse():
@@ -52,7 +61,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="c1", choices=sorted(WORKLOADS) + sorted(BATCHED) + sorted(LEARNED))
+    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS) + sorted(BATCHED) + sorted(LEARNED))
+    ap.add_argument("--c-mode", default="paper", choices=["paper", "fixed"],
+                    help="Eq. 2.6 applied every iteration (paper) or c held at 0 (fixed)")
     ap.add_argument("--judge-n", type=int, default=32768, help="dense-vs-sparse judging size (learned workload)")
     ap.add_argument("--sbuild", default="bf16_split", choices=["bf16_split", "bf16", "f32"])
     ap.add_argument("--s-dtype", default="f32", choices=["f32", "bf16"])
@@ -100,18 +111,25 @@ def make_inputs(workload: str, seed: int):
 
 def ari(a, b) -> float:
     """Adjusted Rand index of two labelings (Hubert and Arabie), used to judge
-    one solution against another."""
-    a = np.unique(np.asarray(a), return_inverse=True)[1]
-    b = np.unique(np.asarray(b), return_inverse=True)[1]
+    one solution against another.  The contingency table is kept sparse
+    (counts of label pairs), so all-singleton labelings cost O(n log n)."""
+    a = np.unique(np.asarray(a), return_inverse=True)[1].astype(np.int64)
+    b = np.unique(np.asarray(b), return_inverse=True)[1].astype(np.int64)
     n = a.size
-    cont = np.zeros((a.max() + 1, b.max() + 1), dtype=np.int64)
-    np.add.at(cont, (a, b), 1)
+    _, cont = np.unique(a * (int(b.max()) + 1) + b, return_counts=True)
     comb = lambda x: x * (x - 1) / 2.0
-    sij = comb(cont).sum()
-    sa, sb = comb(cont.sum(axis=1)).sum(), comb(cont.sum(axis=0)).sum()
-    expected = sa * sb / comb(n)
+    sij = comb(cont.astype(np.float64)).sum()
+    sa = comb(np.bincount(a).astype(np.float64)).sum()
+    sb = comb(np.bincount(b).astype(np.float64)).sum()
+    expected = sa * sb / comb(float(n))
     top = 0.5 * (sa + sb) - expected
     return 1.0 if top == 0 else float((sij - expected) / top)
+
+
+def exemplar_counts(e) -> list:
+    """Distinct exemplars per level (N at a level means every point chose
+    itself: a degenerate clustering)."""
+    return [int(np.unique(x).size) for x in np.asarray(e)]
 
 
 def cpu_count():
@@ -121,19 +139,127 @@ def cpu_count():
         return os.cpu_count() or 1
 
 
-def oracle_sample(workload: str, seed: int, iters: int = 1):
-    """FP64 reference iterations t = 2 .. iters + 1 on a CPU_SAMPLE_N-point
-    instance of the workload family (same d, L and distribution); returns
-    (updates/s, seconds per iteration, points)."""
-    from oracle import hap_oracle as H
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=20).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def sample_points(workload: str, n: int, seed: int):
+    """n points of the workload family (same d and distribution)."""
     from paper_1403_7394_gb300 import workloads as W
     N, d, L, T, gen, _ = WORKLOADS[workload]
-    n = min(CPU_SAMPLE_N, N)
     if gen == "config1":
         X, _ = W.gmm_points(n, d, 64, sigma=1.0, seed=seed, means="normal", mean_scale=2.0)
     else:
         X, _ = W.texture_patches(n, 256, 8, 0.05, seed=seed)
-    S = H.neg_sq_euclidean(X.astype(np.float32)).astype(np.float32).astype(np.float64)
+    return X.astype(np.float32)
+
+
+def _oracle_rank(rank, world, init_file, workload, seed, n, pref, warm, iters, out_file):
+    """One gloo rank of the all-cores reference sample: the FP64 reference's
+    row-sharded step on a contiguous band of rows, one all-reduce per
+    iteration.  Rank 0 writes the per-iteration times, each the slowest
+    rank's."""
+    import torch
+    import torch.distributed as dist
+    from oracle import hap_oracle as H
+    torch.set_num_threads(1)
+    dist.init_process_group("gloo", init_method=f"file://{init_file}", rank=rank, world_size=world)
+
+    def allreduce(x):
+        t = torch.from_numpy(np.ascontiguousarray(x))
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return t.numpy()
+
+    L = WORKLOADS[workload][2]
+    X = sample_points(workload, n, seed)
+    rows = np.array_split(np.arange(n), world)[rank]
+    S_rows = H.level_similarity_rows(H.neg_sq_euclidean(X, rows), rows, np.full(L, pref))
+    st, carry = H.init_shard_state(L, n, rows), None
+    for _ in range(warm):  # iteration 1 has no tau / c updates
+        st, carry = H.step_sharded(S_rows, st, rows, 0.5, H.PAPER, allreduce, carry)
+    times = []
+    dist.barrier()
+    for _ in range(iters):
+        t0 = time.perf_counter()
+        st, carry = H.step_sharded(S_rows, st, rows, 0.5, H.PAPER, allreduce, carry)
+        times.append(time.perf_counter() - t0)
+    tt = torch.tensor(times, dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    if rank == 0:
+        json.dump(tt.tolist(), open(out_file, "w"))
+    dist.destroy_process_group()
+
+
+def oracle_all_cores(workload: str, seed: int, n: int, iters: int, warm: int = 1):
+    """The FP64 reference on every host core this process may use: one gloo
+    rank per core (spawned), each owning a band of rows of an n-point
+    instance of the workload family.  Returns (per-iteration seconds, ranks,
+    points)."""
+    import tempfile
+    import torch.multiprocessing as mp
+    from oracle import hap_oracle as H
+    N = WORKLOADS[workload][0]
+    n = min(n, N)
+    procs = cpu_count()
+    X = sample_points(workload, n, seed)
+    pref = H.median_preference(H.neg_sq_euclidean(X[:512], np.arange(512))[:, :512])
+    old = os.environ.get("OMP_NUM_THREADS")
+    os.environ["OMP_NUM_THREADS"] = "1"
+    try:
+        with tempfile.TemporaryDirectory() as d:
+            out = os.path.join(d, "times.json")
+            mp.start_processes(_oracle_rank, args=(procs, os.path.join(d, "init"), workload, seed, n, pref, warm,
+                                                   iters, out), nprocs=procs, join=True, start_method="spawn")
+            times = json.load(open(out))
+    finally:
+        if old is None:
+            os.environ.pop("OMP_NUM_THREADS", None)
+        else:
+            os.environ["OMP_NUM_THREADS"] = old
+    return times, procs, n
+
+
+def cpu_baseline(workload: str, seed: int = 0):
+    """The oracle timed on this host: on all cores (the reported value) and on
+    one core (kept for continuity), both in updates/s of the workload family."""
+    L = WORKLOADS[workload][2]
+    times, procs, n = oracle_all_cores(workload, seed, CPU_CORES_N, CPU_CORES_ITERS)
+    per = float(np.median(times))
+    ups1, dt1, n1 = oracle_sample(workload, seed=seed, iters=CPU_SAMPLE_ITERS)
+    return {"value": n * n * L / per, "unit": "updates/s", "cores": procs, "kind": "oracle",
+            "cpu_model": cpu_model(),
+            "sample": f"FP64 reference row-sharded over {procs} gloo ranks (one per core, one all-reduce per "
+                      f"iteration) on a {n}-point L={L} instance of the workload family: median of "
+                      f"{len(times)} iterations (t >= 2), {per:.2f} s each",
+            "single_core": {"value": ups1, "unit": "updates/s", "cores": 1,
+                            "sample": f"{CPU_SAMPLE_ITERS} FP64 reference iterations (t = 2..{CPU_SAMPLE_ITERS + 1}) "
+                                      f"on a {n1}-point L={L} instance, {dt1 * CPU_SAMPLE_ITERS:.1f} s, numpy "
+                                      f"single-threaded"}}
+
+
+def oracle_sample(workload: str, seed: int, iters: int = 1):
+    """FP64 reference iterations t = 2 .. iters + 1 on a CPU_SAMPLE_N-point
+    instance of the workload family (same d, L and distribution), on one
+    core; returns (updates/s, seconds per iteration, points)."""
+    from oracle import hap_oracle as H
+    N, d, L, T, gen, _ = WORKLOADS[workload]
+    n = min(CPU_SAMPLE_N, N)
+    X = sample_points(workload, n, seed)
+    S = H.neg_sq_euclidean(X).astype(np.float32).astype(np.float64)
     pref = H.median_preference(S[:512, :512])
     S = H.level_similarities(S, np.full(L, pref))
     st = H.step(S, H.init_state(L, n), 0.5, H.PAPER)  # iteration 1 (no tau/c updates)
@@ -195,25 +321,24 @@ def measured_peaks():
 
 def run_reference(args, world, rank):
     """The FP64 reference timed on this machine's CPU cores: each step is one
-    reference iteration on a sample of the workload family."""
+    reference iteration, row-sharded over every host core, on a sample of the
+    workload family.  Under torchrun only rank 0 runs it."""
     if rank != 0:
         return
-    N, d, L, T, gen, desc = WORKLOADS[args.workload]
-    for _ in range(args.warmup):
-        oracle_sample(args.workload, seed=0)
-    times, n = [], 0
-    for _ in range(args.steps):
-        ups, dt, n = oracle_sample(args.workload, seed=0)
-        times.append(dt)
+    wl = args.workload if args.workload in WORKLOADS else "c2"
+    N, d, L, T, gen, desc = WORKLOADS[wl]
+    times, procs, n = oracle_all_cores(wl, 0, CPU_CORES_N, args.steps, warm=max(1, args.warmup))
     per = float(np.mean(times))
     value = n * n * L / per
-    sample = f"one FP64 reference iteration (t>=2) of a {n}-point, L={L} instance of the workload family per step"
+    sample = (f"one FP64 reference iteration (t >= 2) of a {n}-point, L={L} instance of the workload family per "
+              f"step, row-sharded over {procs} gloo ranks (one per core)")
     line = {"metric": "hap_message_updates_per_s", "value": value, "unit": "updates/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "desc": desc, "sample_points": n},
+            "config": {"workload": wl, "desc": desc, "sample_points": n},
             "impl": "reference",
-            "cpu_baseline": {"value": value, "unit": "updates/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "updates/s", "cores": procs, "kind": "oracle",
+                             "cpu_model": cpu_model(), "sample": sample},
             "e2e": {"value": value, "unit": "updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -246,7 +371,8 @@ def main():
         desc = f"first {N} points of: {desc}"
     shape_opts = {k: getattr(args, k) for k in ("block_threads", "cluster_size", "grid_clusters", "elems_per_thread",
                                                  "col_sums")}
-    ctx = hap.HAP(N, L, prefs=prefs, damping=0.5, device=dev, s_dtype=args.s_dtype, profile=True, **shape_opts)
+    ctx = hap.HAP(N, L, prefs=prefs, damping=0.5, device=dev, s_dtype=args.s_dtype, c_mode=args.c_mode, profile=True,
+                  **shape_opts)
     stream = ctx.stream
     Xd = torch.from_numpy(X).to(dev)
     e_dev = torch.empty((L, N), dtype=torch.int32, device=dev)
@@ -322,20 +448,22 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": args.workload, "desc": desc, "N": N, "d": d, "L": L, "iters": T,
-                       "sbuild": args.sbuild, "s_dtype": args.s_dtype, "damping": 0.5, "c_mode": "paper",
+                       "sbuild": args.sbuild, "s_dtype": args.s_dtype, "damping": 0.5, "c_mode": args.c_mode,
                        "l2": "inputs larger than L2 (A, R, S = %.2f GB)" % ((2 * L * N * N * 4 + N * N * s_bytes) / 1e9),
                        "launch_shape": ctx.shape, "parallelism": f"independent instance per GPU x{world}"},
             "e2e": {"value": e2e_value, "unit": "updates/s", "h2d_bytes_per_step": int(X.nbytes),
                     "d2h_bytes_per_step": int(eh.numel() * 4 + L * 8), "steps": args.e2e_steps},
             "gpu_launches": int(launches), "roofline": roof, "clocks": clk.summary(),
-            "net_similarity": [float(x) for x in ns]}
+            "net_similarity": [float(x) for x in ns], "exemplars_per_level": exemplar_counts(e_dev.cpu().numpy())}
     if args.s_dtype == "bf16":
         # the precision form against plain FP32 S on the same GPU: speedup of
         # the whole solve and the accuracy of its result (NS from the points
-        # in FP64 for both, ARI per level)
+        # in FP64 for both, ARI per level), in the benchmark's c mode and, when
+        # that is Eq. 2.6 as printed (whose c feedback can end with every point
+        # its own exemplar), also with c fixed
         e_bf = e_dev.clone()
         ctx.close()
-        ctx32 = hap.HAP(N, L, prefs=prefs, damping=0.5, device=dev, s_dtype="f32", **shape_opts)
+        ctx32 = hap.HAP(N, L, prefs=prefs, damping=0.5, device=dev, s_dtype="f32", c_mode=args.c_mode, **shape_opts)
         e32 = torch.empty((L, N), dtype=torch.int32, device=dev)
 
         def step32():
@@ -352,21 +480,32 @@ def main():
         f1.record(ctx32.stream)
         torch.cuda.synchronize()
         ms32 = f0.elapsed_time(f1)
-        pt = torch.from_numpy(np.repeat(prefs[:, None], N, axis=1)).to(dev)
-        ns_bf = hap.net_similarity_points(Xd, e_bf, pt)
-        ns_32 = hap.net_similarity_points(Xd, e32, pt)
-        eb, ef = e_bf.cpu().numpy(), e32.cpu().numpy()
-        line["config"]["vs_f32_s"] = {
-            "speedup": ms32 / ms, "f32_ms_per_step": ms32 / args.steps,
-            "ns_gap": [float((ns_32[l] - ns_bf[l]) / abs(ns_32[l])) for l in range(L)],
-            "ari": [ari(eb[l], ef[l]) for l in range(L)]}
         ctx32.close()
+        pt = torch.from_numpy(np.repeat(prefs[:, None], N, axis=1)).to(dev)
+
+        def judge(eb_dev, ef_dev):
+            ns_bf = hap.net_similarity_points(Xd, eb_dev, pt)
+            ns_32 = hap.net_similarity_points(Xd, ef_dev, pt)
+            eb, ef = eb_dev.cpu().numpy(), ef_dev.cpu().numpy()
+            nb, nf = exemplar_counts(eb), exemplar_counts(ef)
+            degen = [nb[l] == N and nf[l] == N for l in range(L)]
+            return {"ns_gap": [None if degen[l] else float((ns_32[l] - ns_bf[l]) / abs(ns_32[l])) for l in range(L)],
+                    "ari": [None if degen[l] else ari(eb[l], ef[l]) for l in range(L)],
+                    "exemplars_bf16_s": nb, "exemplars_f32_s": nf, "degenerate": degen}
+
+        acc = {args.c_mode: judge(e_bf, e32)}
+        if args.c_mode == "paper":
+            outs = {}
+            for sd in ("bf16", "f32"):
+                cx = hap.HAP(N, L, prefs=prefs, damping=0.5, device=dev, s_dtype=sd, c_mode="fixed", **shape_opts)
+                cx.build_similarity(Xd, mode=args.sbuild)
+                cx.iterate(T)
+                outs[sd] = cx.exemplars().clone()
+                cx.close()
+            acc["fixed"] = judge(outs["bf16"], outs["f32"])
+        line["config"]["vs_f32_s"] = {"speedup": ms32 / ms, "f32_ms_per_step": ms32 / args.steps, "accuracy": acc}
     if rank == 0 and world == 1 and args.cpu_baseline:
-        its = CPU_SAMPLE_ITERS
-        ups, dt, n = oracle_sample(args.workload, seed=0, iters=its)
-        line["cpu_baseline"] = {"value": ups, "unit": "updates/s", "cores": 1, "kind": "oracle",
-                                "sample": f"{its} FP64 reference iterations (t = 2..{its + 1}) on a {n}-point L={L} "
-                                          f"instance of the workload family, {dt * its:.1f} s, numpy single-threaded"}
+        line["cpu_baseline"] = cpu_baseline(args.workload, seed=0)
     if rank == 0:
         print(json.dumps(line))
     ctx.close()

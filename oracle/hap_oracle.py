@@ -79,16 +79,38 @@ GAUSS_SEIDEL = "gauss_seidel"
 # ---------------------------------------------------------------------------
 # Inputs: similarities and preferences (§2)
 # ---------------------------------------------------------------------------
-def neg_sq_euclidean(X) -> np.ndarray:
+def neg_sq_euclidean(X, rows=None) -> np.ndarray:
     """s_ij = -||x_i - x_j||^2 in float64, straight from the definition (§2:
     the negative squared Euclidean distance is the usual similarity).  The
-    diagonal is 0 here; preferences are placed on it separately."""
+    diagonal is 0 here; preferences are placed on it separately.  ``rows``
+    selects the rows i to compute (all by default)."""
     X = np.asarray(X, dtype=np.float64)
     n = X.shape[0]
-    S = np.empty((n, n), dtype=np.float64)
-    for i in range(n):
+    rows = np.arange(n) if rows is None else np.asarray(rows)
+    S = np.empty((rows.size, n), dtype=np.float64)
+    for r, i in enumerate(rows):
         d = X - X[i]
-        S[i] = -np.einsum("kd,kd->k", d, d)
+        S[r] = -np.einsum("kd,kd->k", d, d)
+    return S
+
+
+def neg_sq_euclidean_fixed_order(X, block: int = 512) -> np.ndarray:
+    """The same similarity as ``neg_sq_euclidean`` (§2), with the sum over the
+    coordinates taken in order k = 0, 1, ..., d-1, one correctly rounded
+    float64 subtraction, multiplication and addition at a time.  Every
+    IEEE-754 machine then produces the same bits, so a similarity built on
+    one host can be rebuilt bit for bit on another (a library reduction may
+    change its summation order between builds)."""
+    X = np.asarray(X, dtype=np.float64)
+    n, d = X.shape
+    S = np.empty((n, n), dtype=np.float64)
+    for r0 in range(0, n, block):
+        r1 = min(n, r0 + block)
+        acc = np.zeros((r1 - r0, n), dtype=np.float64)
+        for k in range(d):
+            diff = np.subtract.outer(X[r0:r1, k], X[:, k])
+            acc += diff * diff
+        S[r0:r1] = -acc
     return S
 
 
@@ -145,9 +167,20 @@ def responsibility_update(S_rows, A_rows, R_rows, tau_rows, lam):
     return damp(R_rows, R_hat, lam)
 
 
-def positive_column_sums(R_l) -> np.ndarray:
+def positive_column_sums(R_l, partition=None) -> np.ndarray:
     """P_j = sum_{k != j} max(0, rho_kj): the evidence sum shared by Eqs. 2.2,
-    2.3 and 2.4, for one level."""
+    2.3 and 2.4, for one level.
+
+    ``partition`` (a list of row-index arrays covering every row once) only
+    fixes the order of the float64 sum: each part's rows are summed by
+    ``row_block_column_sums`` and the part sums are added in list order -
+    the order in which a row-sharded run combines its shards."""
+    if partition is not None:
+        P = None
+        for rows in partition:
+            part = row_block_column_sums(R_l[np.asarray(rows)], rows)
+            P = part if P is None else P + part
+        return P
     Rp = np.maximum(R_l, 0.0)
     n = R_l.shape[0]
     Rp[np.arange(n), np.arange(n)] = 0.0
@@ -182,13 +215,13 @@ def availability_update(A_rows, R_rows, rows, c_l, phi_l, R_diag, P, lam):
     return damp(A_rows, A_hat, lam)
 
 
-def tau_update(c, R) -> np.ndarray:
+def tau_update(c, R, partition=None) -> np.ndarray:
     """Eq. 2.4: tau_j^{l+1} = c_j^l + rho_jj^l + sum_{k != j} max(0, rho_kj^l);
     the lowest level has tau = +inf (reading R3)."""
     L, n, _ = R.shape
     tau = np.full((L, n), np.inf)
     for l in range(1, L):
-        tau[l] = c[l - 1] + np.diagonal(R[l - 1]) + positive_column_sums(R[l - 1])
+        tau[l] = c[l - 1] + np.diagonal(R[l - 1]) + positive_column_sums(R[l - 1], partition)
     return tau
 
 
@@ -244,13 +277,14 @@ def similarity_level_update(S_l, A_l, R_l, pref_next, kappa):
 
 
 def step(S, st: HAPState, lam: float, c_mode: str = PAPER, schedule: str = JACOBI,
-         kappa: float = 0.0) -> HAPState:
+         kappa: float = 0.0, partition=None) -> HAPState:
     """One HAP iteration (number st.t + 1) on the (L, N, N) similarity tensor S.
 
     Order (readings R4-R6): inter-level quantities from the start-of-iteration
     state, then rho at every level (Eq. 2.1), then alpha at every level from
     the new rho (Eqs. 2.2-2.3).  schedule="gauss_seidel" runs Algorithm 1's
-    level loop instead (R11); kappa > 0 applies Eq. 2.7 (R10)."""
+    level loop instead (R11); kappa > 0 applies Eq. 2.7 (R10).  ``partition``
+    fixes the summation order of the column sums (positive_column_sums)."""
     if schedule == GAUSS_SEIDEL:
         return step_gauss_seidel(S, st, lam, c_mode, kappa)
     if schedule != JACOBI:
@@ -266,7 +300,7 @@ def step(S, st: HAPState, lam: float, c_mode: str = PAPER, schedule: str = JACOB
     if t >= 2:
         if c_mode == PAPER:
             c = cluster_preference_update(st.A, st.R)          # Eq. 2.6
-        tau = tau_update(c, st.R)                              # Eq. 2.4
+        tau = tau_update(c, st.R, partition)                   # Eq. 2.4
     else:
         tau = np.full((L, n), np.inf)
     phi = phi_update(st.A, S)                                  # Eq. 2.5
@@ -278,7 +312,7 @@ def step(S, st: HAPState, lam: float, c_mode: str = PAPER, schedule: str = JACOB
     A_new = np.empty_like(st.A)
     rows = np.arange(n)
     for l in range(L):                                         # Eqs. 2.2, 2.3
-        P = positive_column_sums(R_new[l])
+        P = positive_column_sums(R_new[l], partition)
         A_new[l] = availability_update(st.A[l], R_new[l], rows, c[l], phi[l],
                                        np.diagonal(R_new[l]).copy(), P, lam)
     return HAPState(A=A_new, R=R_new, c=c, tau=tau, phi=phi, t=t)
@@ -312,68 +346,99 @@ def step_gauss_seidel(S, st: HAPState, lam: float, c_mode: str = PAPER, kappa: f
 
 def run(S, iterations: int, lam: float, c_mode: str = PAPER, c0=None,
         state: HAPState | None = None, callback=None, schedule: str = JACOBI,
-        kappa: float = 0.0) -> HAPState:
+        kappa: float = 0.0, partition=None) -> HAPState:
     """Algorithm 1's iteration loop for a fixed number of iterations."""
     S = np.asarray(S, dtype=np.float64)
     L, n, _ = S.shape
     st = init_state(L, n, c0) if state is None else state
     for _ in range(iterations):
-        st = step(S, st, lam, c_mode, schedule, kappa)
+        st = step(S, st, lam, c_mode, schedule, kappa, partition)
         if callback is not None:
             callback(st)
     return st
 
 
-def step_sharded(S, st: HAPState, rows, lam: float, c_mode: str, allreduce,
+def level_similarity_rows(S_rows, rows, prefs) -> np.ndarray:
+    """The whole rows ``rows`` of the (L, N, N) similarity tensor of
+    ``level_similarities``: S_rows (len(rows), N) are rows of the shared
+    off-diagonal similarities; level l puts prefs[l] on the diagonal entries
+    (i, i) of its owned rows i."""
+    S_rows = np.asarray(S_rows, dtype=np.float64)
+    rows = np.asarray(rows)
+    prefs = np.asarray(prefs, dtype=np.float64)
+    L = prefs.shape[0]
+    out = np.empty((L,) + S_rows.shape, dtype=np.float64)
+    loc = np.arange(rows.size)
+    for l in range(L):
+        out[l] = S_rows
+        out[l, loc, rows] = prefs[l] if prefs.ndim == 1 else prefs[l, rows]
+    return out
+
+
+def init_shard_state(L: int, N: int, rows, c0=None) -> HAPState:
+    """Algorithm 1's initial values for the shard that owns ``rows``: alpha
+    and rho (L, len(rows), N) zero; the vectors c, tau, phi keep all N
+    nodes."""
+    nr = np.asarray(rows).size
+    c = np.zeros((L, N)) if c0 is None else np.array(c0, dtype=np.float64).reshape(L, N)
+    return HAPState(A=np.zeros((L, nr, N)), R=np.zeros((L, nr, N)), c=c,
+                    tau=np.full((L, N), np.inf), phi=np.zeros((L, N)), t=0)
+
+
+def step_sharded(S_rows, st: HAPState, rows, lam: float, c_mode: str, allreduce,
                  carry: dict | None = None):
-    """One iteration of ``step`` computed by the shard that owns ``rows`` of a
-    row-partitioned problem: every row quantity (rho, alpha, c, tau, phi of
-    node i) is computed for owned rows only, and everything another shard
-    needs - the positive column sums and the owned diagonal, c and phi values
-    (zero elsewhere) - crosses shards through ONE sum all-reduce per
-    iteration (``allreduce(x)`` returns the element-wise sum of x over all
-    shards).  Only the owned rows of st.A / st.R are read or written.
+    """One iteration of ``step`` computed by the shard that owns the whole rows
+    ``rows`` of a row-partitioned problem (MR-HAP, §3, keys its messages by
+    node; here a shard is a band of nodes).  The shard holds only its rows:
+    S_rows, st.A and st.R are (L, len(rows), N); the vectors c, tau and phi
+    are (L, N).  Every row quantity (rho, alpha, c, tau, phi of node i) is
+    computed for owned rows only, and everything another shard needs - the
+    positive column sums and the owned diagonal, c and phi values (zero
+    elsewhere) - crosses shards through ONE sum all-reduce per iteration
+    (``allreduce(x)`` returns the element-wise sum of x over all shards).
 
     ``carry`` holds the previous iteration's reduced column statistics of rho
     ({"P": (L, N), "Rdiag": (L, N)}); None at the first iteration of a run
-    (or after a restart, when they are recomputed with one extra reduction)."""
-    S = np.asarray(S, dtype=np.float64)
-    L, n, _ = S.shape
+    (or after a restart, when they are recomputed with one extra reduction).
+    With the shards' partial sums added in shard order, the result has the
+    bits of ``step(..., partition=<the shards' rows in order>)``."""
+    S_rows = np.asarray(S_rows, dtype=np.float64)
+    L, nr, n = S_rows.shape
     rows = np.asarray(rows)
+    loc = np.arange(nr)
     t = st.t + 1
     A, R = st.A, st.R
     if carry is None:  # column statistics of the current rho (Eqs. 2.2-2.4 sums)
         part = np.zeros((2, L, n))
         for l in range(L):
-            part[0, l] = row_block_column_sums(R[l][rows], rows)
-            part[1, l, rows] = R[l][rows, rows]
+            part[0, l] = row_block_column_sums(R[l], rows)
+            part[1, l, rows] = R[l][loc, rows]
         part = allreduce(part)
         carry = {"P": part[0], "Rdiag": part[1]}
     c = st.c.copy()
     if t >= 2 and c_mode == PAPER:                              # Eq. 2.6, owned rows
-        c[:, rows] = np.max(A[:, rows] + R[:, rows], axis=2)
+        c[:, rows] = np.max(A + R, axis=2)
     tau = np.full((L, n), np.inf)
     if t >= 2:                                                  # Eq. 2.4, owned rows
         for l in range(1, L):
             tau[l, rows] = c[l - 1, rows] + carry["Rdiag"][l - 1, rows] + carry["P"][l - 1, rows]
     phi = np.zeros((L, n))
     for l in range(L - 1):                                      # Eq. 2.5, owned rows
-        phi[l, rows] = np.max(A[l + 1][rows] + S[l + 1][rows], axis=1)
-    R_new = R.copy()
+        phi[l, rows] = np.max(A[l + 1] + S_rows[l + 1], axis=1)
+    R_new = np.empty_like(R)
     for l in range(L):                                          # Eq. 2.1, owned rows
-        R_new[l][rows] = responsibility_update(S[l][rows], A[l][rows], R[l][rows], tau[l, rows], lam)
+        R_new[l] = responsibility_update(S_rows[l], A[l], R[l], tau[l, rows], lam)
     # the one exchange: column sums of the new rho, and the owned c, phi, rho_jj
     part = np.zeros((4, L, n))
     for l in range(L):
-        part[0, l] = row_block_column_sums(R_new[l][rows], rows)
-        part[1, l, rows] = R_new[l][rows, rows]
+        part[0, l] = row_block_column_sums(R_new[l], rows)
+        part[1, l, rows] = R_new[l][loc, rows]
         part[2, l, rows] = c[l, rows]
         part[3, l, rows] = phi[l, rows]
     part = allreduce(part)
-    A_new = A.copy()
+    A_new = np.empty_like(A)
     for l in range(L):                                          # Eqs. 2.2, 2.3, owned rows
-        A_new[l][rows] = availability_update(A[l][rows], R_new[l][rows], rows, part[2, l], part[3, l],
-                                             part[1, l], part[0, l], lam)
+        A_new[l] = availability_update(A[l], R_new[l], rows, part[2, l], part[3, l], part[1, l], part[0, l], lam)
     out = HAPState(A=A_new, R=R_new, c=part[2], tau=tau, phi=part[3], t=t)
     return out, {"P": part[0], "Rdiag": part[1]}
 

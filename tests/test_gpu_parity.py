@@ -207,12 +207,17 @@ def test_config0_paper_c_free_running(lam, T, report):
     c grows without bound and FP32 rounding is amplified from step to step:
     free-running messages drift past 1e-4 of FP64 (single steps from the same
     state stay near 1e-7, see the teacher-forced tests) while the exemplars
-    stay identical.  The bound below only catches gross errors."""
+    stay identical.  Measured on GB300: 4.1e-4 (lambda = 0.5, 30 iterations)
+    and 1.3e-4 (lambda = 0.9, 200); a forward-error estimate of the undamped
+    c recursion (FP32 unit roundoff 6e-8 amplified by the growth of c over
+    the run) gives 2.5e-4 to 3.1e-4 for the first.  The bound 1e-3 leaves a
+    factor of 2.4 over the larger measurement, so a kernel error of the size
+    of a dropped or misplaced term (1e-2 and above) still fails."""
     g, e_gpu, ref, _ = _free_run("paper", lam, T)
     errs = {f: H.message_rel_error(g[f], getattr(ref, f)) for f in ("A", "R", "c", "tau", "phi")}
     report(errs=errs, exemplars_equal=bool(np.array_equal(e_gpu, H.exemplars(ref.A, ref.R))))
     np.testing.assert_array_equal(e_gpu, H.exemplars(ref.A, ref.R))
-    assert max(errs.values()) <= 1e-2, errs
+    assert max(errs.values()) <= 1e-3, errs
 
 
 # ----------------------------------------------------------------- outputs

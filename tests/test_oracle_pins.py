@@ -252,6 +252,21 @@ def test_similarity_matches_scipy():
     from scipy.spatial.distance import cdist
     X, _ = W.gmm_points(50, 7, 3, sigma=1.0, seed=2)
     np.testing.assert_allclose(H.neg_sq_euclidean(X), -cdist(X, X, "sqeuclidean"), rtol=1e-13, atol=1e-12)
+    np.testing.assert_allclose(H.neg_sq_euclidean_fixed_order(X, block=16), -cdist(X, X, "sqeuclidean"),
+                               rtol=1e-13, atol=1e-12)
+
+
+def test_fixed_order_similarity_is_exact_on_integers():
+    """Small integer coordinates make every float64 operation exact, so the
+    fixed-order sum must equal the integer definition -sum_k (x_ik - x_jk)^2
+    computed with Python integers."""
+    rng = np.random.default_rng(4)
+    Xi = rng.integers(-50, 51, size=(37, 5))
+    want = np.array([[-sum(int(a - b) ** 2 for a, b in zip(xi, xj)) for xj in Xi] for xi in Xi], dtype=np.float64)
+    np.testing.assert_array_equal(H.neg_sq_euclidean_fixed_order(Xi.astype(np.float64), block=8), want)
+    # the coordinate order is part of the definition: reversing it is a different rounding
+    # sequence, but on exact inputs the same value
+    np.testing.assert_array_equal(H.neg_sq_euclidean_fixed_order(Xi[:, ::-1].astype(np.float64)), want)
 
 
 def test_adjusted_rand_index():
