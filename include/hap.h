@@ -117,6 +117,21 @@ typedef struct hap_options {
                           (the paper's range); 0 (default) = off.  Needs the JACOBI
                           schedule and one S shared by all levels; the net
                           similarity keeps using the given S.                         */
+    int64_t wait_limit_ns; /* limit of every bounded device-side wait of the row pass
+                          (TMA ring stages, the cluster's row exchange), in
+                          nanoseconds; 0 (default) = 2 s.  A wait that runs out
+                          makes the kernel stop, let its own copies land and
+                          return; the next synchronising call reports
+                          HAP_ETIMEOUT.  Minimum 1.                                  */
+    int debug_bounds;  /* 1: checks for debugging, all reported as HAP_EDEVICE by
+                          the next synchronising call (hap_set_similarity and
+                          hap_build_similarity: HAP_EINVAL for a non-finite S):
+                          every off-diagonal similarity must be finite (§2 admits
+                          s_ij = -inf; this library requires finite values); every
+                          bulk copy of the row pass must lie inside the messages;
+                          the row maximum of Eq. 2.1 must sit in a real column.
+                          Failed checks skip the access and never trap.  0 (default)
+                          = no checks.                                               */
 } hap_options;
 
 typedef struct hap_ctx hap_ctx;
@@ -164,7 +179,8 @@ int hap_set_cluster_preferences(hap_ctx* ctx, const float* c0);
  *          (requires s_per_level = 1).
  *   S      device, N rows of ld elements (ld >= N), row i = node i, column j =
  *          candidate exemplar j; the diagonal is ignored (the preferences are
- *          used instead).  Values must be finite.
+ *          used instead).  Values must be finite (checked, HAP_EINVAL, with
+ *          hap_options.debug_bounds = 1).
  *   dtype  HAP_S_F32 or HAP_S_BF16 (the type of the caller's S); it is
  *          converted to the context's s_dtype (BF16 storage rounds to nearest). */
 int hap_set_similarity(hap_ctx* ctx, int level, const void* S, int64_t ld, int dtype);
@@ -219,8 +235,16 @@ int hap_get_state(hap_ctx* ctx, float* A, float* R, float* vecs, int64_t* iter);
  * uninterrupted run would. */
 int hap_set_state(hap_ctx* ctx, const float* A, const float* R, const float* vecs, int64_t iter);
 
-/* Waits for the bound stream and checks the device status word. */
+/* Waits for the bound stream and checks the device status word.
+ * After HAP_ETIMEOUT or HAP_EDEVICE the messages are undefined; the error
+ * stays reported until hap_set_state, hap_set_similarity,
+ * hap_build_similarity or hap_set_cluster_preferences gives the context a
+ * new state (they clear it). */
 int hap_sync(hap_ctx* ctx);
+
+/* Changes hap_options.wait_limit_ns of a context (ns >= 1; 0 = 2 s) for the
+ * following iterations.  Host call. */
+int hap_set_wait_limit(hap_ctx* ctx, int64_t ns);
 
 /* Launch shape and counters (HAP_Q_* keys).  Host call. */
 int hap_query(hap_ctx* ctx, int key, int64_t* value);
@@ -432,6 +456,9 @@ int hap_net_similarity_points(const float* X, int64_t N, int64_t d, int L, const
  * The call is synchronising and calls no allocating routine.  The first call
  * on each device looks up the array's device address (once per device, with
  * that device current); make that first call before any stream capture.
+ * With CUDA's lazy module loading, that first call may also be what loads
+ * this library's device code onto the device, which allocates the array
+ * there once; later calls allocate nothing.
  * Every call shares the one array and leaves its contents behind; the call
  * clears what must start at zero.  Calls that overlap on the GPU (other host
  * threads or streams, the same device) race on the array. */

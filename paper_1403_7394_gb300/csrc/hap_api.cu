@@ -203,7 +203,12 @@ int check_opts(const hap_options& o) {
     if (o.kappa != 0.f && (o.schedule != HAP_SCHED_JACOBI || o.s_per_level)) return HAP_EUNSUPPORTED;
     if (o.s_dtype != HAP_S_F32 && o.s_dtype != HAP_S_BF16) return HAP_EINVAL;
     if (o.s_per_level != 0 && o.s_per_level != 1) return HAP_EINVAL;
+    if (o.wait_limit_ns < 0 || (o.debug_bounds != 0 && o.debug_bounds != 1)) return HAP_EINVAL;
     return HAP_OK;
+}
+
+uint64_t wait_limit(const hap_options& o) {
+    return o.wait_limit_ns > 0 ? (uint64_t)o.wait_limit_ns : 2000000000ull;
 }
 
 int plan(int64_t N, int L, const hap_options& o, LaunchShape* sh, Layout* y) {
@@ -229,10 +234,11 @@ int plan(int64_t N, int L, const hap_options& o, LaunchShape* sh, Layout* y) {
     } while (0)
 
 // Messages back to Algorithm 1's initial values: alpha = rho = 0, tau = +inf,
-// phi = 0, c = c0.
+// phi = 0, c = c0; clears a reported device error.
 int reset_messages(hap_ctx* h) {
     const size_t mat = (size_t)h->L * h->N * h->ld * sizeof(float);
     const size_t vec = (size_t)h->L * h->ld * sizeof(float);
+    CU(cudaMemsetAsync(h->status, 0, 4 * sizeof(unsigned), h->stream));
     CU(cudaMemsetAsync(h->A, 0, mat, h->stream));
     CU(launch_fill_alpha_padding(h->A, (int64_t)h->L * h->N, h->N, h->ld, h->stream));
     CU(cudaMemsetAsync(h->R, 0, mat, h->stream));
@@ -246,6 +252,23 @@ int reset_messages(hap_ctx* h) {
     CU(cudaStreamSynchronize(h->stream));
     h->iter = 0;
     h->pending = false;
+    return HAP_OK;
+}
+
+// debug_bounds: every off-diagonal similarity finite, else HAP_EINVAL (the
+// status word is cleared again; the messages are reset by the caller).
+int check_similarity(hap_ctx* h) {
+    if (!h->opt.debug_bounds) return HAP_OK;
+    CU(launch_check_finite(h->S, h->opt.s_dtype == HAP_S_BF16, h->s_levels, h->N, h->ld, h->status, h->stream));
+    h->launches += 1;
+    unsigned st[4] = {0, 0, 0, 0};
+    CU(cudaMemcpyAsync(st, h->status, sizeof(st), cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    if (st[0] & ST_BOUNDS) {
+        CU(cudaMemsetAsync(h->status, 0, 4 * sizeof(unsigned), h->stream));
+        CU(cudaStreamSynchronize(h->stream));
+        return HAP_EINVAL;
+    }
     return HAP_OK;
 }
 
@@ -412,7 +435,8 @@ int hap_set_similarity(hap_ctx* h, int level, const void* S, int64_t ld, int dty
         CU(launch_copy_similarity(dst, h->opt.s_dtype == HAP_S_BF16, h->ld, S, dtype == HAP_S_BF16, ld, h->N, h->stream));
         h->launches += 1;
     }
-    return reset_messages(h);
+    const int rc = reset_messages(h);
+    return rc ? rc : check_similarity(h);
 }
 
 int hap_build_similarity(hap_ctx* h, const float* X, int64_t d, int mode) {
@@ -441,6 +465,8 @@ int hap_build_similarity(hap_ctx* h, const float* X, int64_t d, int mode) {
         CU(cudaMemcpyAsync(static_cast<char*>(h->S) + (size_t)l * h->N * h->ld * es, h->S,
                            (size_t)h->N * h->ld * es, cudaMemcpyDeviceToDevice, h->stream));
     int rc = reset_messages(h);
+    if (rc) return rc;
+    rc = check_similarity(h);
     if (rc) return rc;
     return check_status(h);
 }
@@ -542,6 +568,8 @@ int hap_iterate(hap_ctx* h, int n) {
     a.lam = h->lam;
     a.oml = 1.0f - h->lam;
     a.kappa = h->opt.kappa;
+    a.wait_ns = wait_limit(h->opt);
+    a.debug = h->opt.debug_bounds;
     const int s_bf16 = h->opt.s_dtype == HAP_S_BF16;
     if (h->opt.schedule == HAP_SCHED_GAUSS_SEIDEL) return iterate_gauss_seidel(h, a, n);
     for (int it = 0; it < n; ++it) {
@@ -636,9 +664,16 @@ int hap_set_state(hap_ctx* h, const float* A, const float* R, const float* vecs,
         CU(cudaMemcpy2DAsync(dst[q], ld * sizeof(float), vecs + (size_t)q * L * N, N * sizeof(float),
                              N * sizeof(float), (size_t)L, cudaMemcpyDeviceToDevice, h->stream));
     CU(launch_prepare_from_R(h->R, h->sh.G, (int)L, N, ld, h->rdiag, h->tpart, h->stream));
+    CU(cudaMemsetAsync(h->status, 0, 4 * sizeof(unsigned), h->stream));
     h->launches += 1;
     h->iter = iter;
     h->pending = false;
+    return HAP_OK;
+}
+
+int hap_set_wait_limit(hap_ctx* h, int64_t ns) {
+    if (!h || ns < 0) return HAP_EINVAL;
+    h->opt.wait_limit_ns = ns;
     return HAP_OK;
 }
 

@@ -107,20 +107,35 @@ HAP_DEV bool mbar_try_wait(uint32_t bar, uint32_t parity) {
                  : "=r"(done) : "r"(bar), "r"(parity) : "memory");
     return done != 0;
 }
+// Non-blocking test of the phase with the given parity.
+HAP_DEV bool mbar_test_wait(uint32_t bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile("{\n\t.reg .pred p;\n\t"
+                 "mbarrier.test_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+    return done != 0;
+}
 HAP_DEV uint64_t global_timer_ns() {
     uint64_t t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
+// Default limit of a bounded wait.
+constexpr uint64_t kWaitNs = 2000000000ull;
 // Waits for the phase with the given parity to complete, for at most about
-// two seconds; on expiry records ST_TIMEOUT in the status word and returns
-// false so the caller can skip the rest of its waits and leave.
-HAP_DEV bool mbar_wait(uint32_t bar, uint32_t parity, unsigned* status) {
-    if (mbar_try_wait(bar, parity)) return true;
+// limit_ns nanoseconds; on expiry records ST_TIMEOUT in the status word and
+// returns false so the caller can stop waiting and leave.  Limits of a
+// millisecond or more wait with try_wait (the thread may be suspended while
+// it waits); shorter ones poll with test_wait, so that the clock is read
+// within a few nanoseconds of the limit.
+HAP_DEV bool mbar_wait(uint32_t bar, uint32_t parity, unsigned* status, uint64_t limit_ns = kWaitNs) {
+    if (mbar_test_wait(bar, parity)) return true;
     const uint64_t t0 = global_timer_ns();
-    for (uint32_t it = 1;; ++it) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 255u) == 0u && global_timer_ns() - t0 > 2000000000ull) {
+    const bool poll = limit_ns < 1000000ull;
+    for (;;) {
+        if (poll ? mbar_test_wait(bar, parity) : mbar_try_wait(bar, parity)) return true;
+        if (global_timer_ns() - t0 > limit_ns) {
             atomicOr(status, ST_TIMEOUT);
             return false;
         }

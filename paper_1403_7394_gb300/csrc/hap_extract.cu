@@ -128,6 +128,22 @@ __global__ void copy_similarity_kernel(DT* __restrict__ dst, int64_t ld, const S
     }
 }
 
+// Precondition check of the similarity (§2 admits s_ij down to -inf; the
+// library requires finite values): one block per row of one level, the
+// off-diagonal entries j < N tested, ST_BOUNDS recorded once per row that
+// holds a NaN or an infinity.
+template <typename ST>
+__global__ void check_finite_kernel(const ST* __restrict__ S, int64_t N, int64_t ld, unsigned* status) {
+    const int64_t i = blockIdx.x, l = blockIdx.y;
+    const ST* row = S + (l * N + i) * ld;
+    bool bad = false;
+    for (int64_t j = threadIdx.x; j < N; j += blockDim.x) {
+        const float v = (float)row[j];
+        bad |= (j != i) && !(fabsf(v) <= 3.402823466e38f);
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, ST_BOUNDS);
+}
+
 // Dense FP32 copy of one level's similarity with the preferences on the diagonal.
 template <typename ST>
 __global__ void read_similarity_kernel(float* __restrict__ dst, const ST* __restrict__ S,
@@ -227,6 +243,16 @@ cudaError_t launch_copy_similarity(void* dst, int dst_bf16, int64_t ld, const vo
         copy_similarity_kernel<<<grid, 256, 0, st>>>(static_cast<float*>(dst), ld, static_cast<const __nv_bfloat16*>(src), ld_src, N);
     else
         copy_similarity_kernel<<<grid, 256, 0, st>>>(static_cast<float*>(dst), ld, static_cast<const float*>(src), ld_src, N);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_finite(const void* S, int s_bf16, int levels, int64_t N, int64_t ld, unsigned* status,
+                                cudaStream_t st) {
+    const dim3 grid((unsigned)N, (unsigned)levels);
+    if (s_bf16)
+        check_finite_kernel<<<grid, 256, 0, st>>>(static_cast<const __nv_bfloat16*>(S), N, ld, status);
+    else
+        check_finite_kernel<<<grid, 256, 0, st>>>(static_cast<const float*>(S), N, ld, status);
     return cudaGetLastError();
 }
 

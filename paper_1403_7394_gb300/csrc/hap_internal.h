@@ -37,6 +37,8 @@ struct RowPassArgs {
     int use_tau;           // tau from Eq. 2.4 this iteration (else +inf)
     const float* tau_in = nullptr;  // [L][ld] tau given per row (sequential level schedule), else computed
     float kappa = 0.f;     // Eq. 2.7 level-wise similarity update (0 = off; shared S only)
+    uint64_t wait_ns = 2000000000ull;  // limit of every bounded wait of the row pass
+    int debug = 0;         // 1: index checks that record ST_BOUNDS (see hap_options.debug_bounds)
 };
 
 struct LaunchShape {
@@ -103,6 +105,10 @@ cudaError_t launch_netsim(const void* S, int s_bf16, int64_t s_level_stride, con
                           const int32_t* e, int64_t N, int64_t ld, int L, double* ns,
                           cudaStream_t st);
 
+// Sets ST_BOUNDS in *status if any off-diagonal s_ij (i != j, j < N) of the
+// `levels` matrices ([levels][N][ld], level stride N*ld) is not finite.
+cudaError_t launch_check_finite(const void* S, int s_bf16, int levels, int64_t N, int64_t ld, unsigned* status,
+                                cudaStream_t st);
 cudaError_t launch_copy_similarity(void* dst, int dst_bf16, int64_t ld, const void* src,
                                    int src_bf16, int64_t ld_src, int64_t N, cudaStream_t st);
 cudaError_t launch_read_similarity(float* dst, const void* S, int s_bf16, const float* pref_l,

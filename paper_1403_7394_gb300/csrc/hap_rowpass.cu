@@ -25,6 +25,19 @@
 //
 // Every reduction is exact (max) or has a fixed order, so a run is bitwise
 // reproducible.  When S is shared by all levels it is read once per row.
+//
+// Bounded waits.  Every wait (ring stage, cluster exchange) gives up after
+// RowPassArgs::wait_ns and records ST_TIMEOUT.  A warp in which any thread
+// gave up leaves the step loop at once (the decision is warp-uniform, so
+// every warp-collective instruction still sees a converged warp); its
+// missing exchange messages then make every other warp of the cluster give
+// up within one more limit.  The ring is refilled only by the issuing thread
+// after its own wait on that stage succeeded, so each stage has at most one
+// copy in flight; after the loop that thread waits (bounded) for every copy
+// it issued and did not consume, so no bulk copy lands in the shared memory
+// of a CTA that has left.  The CTA (and, for clusters, the cluster) then
+// meets at one barrier before it frees tensor memory and exits, which orders
+// every exchange store into its shared memory before the exit.
 #include "hap_common.cuh"
 #include "hap_internal.h"
 
@@ -133,9 +146,17 @@ __global__ void __launch_bounds__(MAXT, 1) rowpass_kernel(const RowPassArgs p) {
         const uint32_t bar = bar0 + 8 * st;
         const uint32_t dst = sm0 + (uint32_t)(st * stage_bytes);
         const uint32_t bytes = (uint32_t)slice_len * (8u + (load_s ? (uint32_t)sizeof(ST) : 0u));
-        mbar_arrive_expect_tx(bar, bytes);
-        if (slice_len > 0) {
-            const int64_t off = ((int64_t)l * N + row) * ld + slice0;
+        const int64_t off = ((int64_t)l * N + row) * ld + slice0;
+        // debug_bounds: the copied slices must lie inside the messages; a
+        // failed check is recorded and the copy skipped (the stage then
+        // completes with no bytes)
+        const bool in_bounds = !p.debug || slice_len == 0 || (row < N && slice0 + slice_len <= ld &&
+                                            off + slice_len <= (int64_t)L * N * ld &&
+                                            (int64_t)(s_each_level ? l : 0) * p.s_level_stride + (int64_t)row * ld +
+                                                    slice0 + slice_len <= (s_each_level ? (int64_t)L : 1) * N * ld);
+        if (!in_bounds) atomicOr(p.status, ST_BOUNDS);
+        mbar_arrive_expect_tx(bar, in_bounds ? bytes : 0u);
+        if (slice_len > 0 && in_bounds) {
             bulk_g2s(dst, p.A + off, (uint32_t)slice_len * 4u, bar);
             bulk_g2s(dst + (uint32_t)a_bytes, p.R + off, (uint32_t)slice_len * 4u, bar);
             if (load_s)
@@ -143,8 +164,10 @@ __global__ void __launch_bounds__(MAXT, 1) rowpass_kernel(const RowPassArgs p) {
                          (uint32_t)slice_len * (uint32_t)sizeof(ST), bar);
         }
     };
+    // issuing thread only: steps issued, and steps whose stage it has waited for
+    int issued = 0, consumed = 0;
     if (tid == 0)
-        for (int q = 0; q < min(NST, nsteps); ++q) issue(q);
+        for (; issued < min(NST, nsteps); ++issued) issue(issued);
 
     float4 srow[K];
 #pragma unroll
@@ -175,7 +198,9 @@ __global__ void __launch_bounds__(MAXT, 1) rowpass_kernel(const RowPassArgs p) {
         const float* sA = reinterpret_cast<const float*>(base);
         const float* sR = reinterpret_cast<const float*>(base + a_bytes);
         const ST* sS = reinterpret_cast<const ST*>(base + 2 * a_bytes);
-        if (!bad) bad = !mbar_wait(bar0 + 8 * st, (uint32_t)(s / NST) & 1u, p.status);
+        if (!mbar_wait(bar0 + 8 * st, (uint32_t)(s / NST) & 1u, p.status, p.wait_ns)) bad = true;
+        if (__any_sync(0xffffffffu, bad)) { bad = true; break; }
+        if (tid == 0) consumed = s + 1;
 
         const bool new_s = s_each_level || l == 0;
         const int64_t voff = (int64_t)l * ld;
@@ -246,7 +271,8 @@ __global__ void __launch_bounds__(MAXT, 1) rowpass_kernel(const RowPassArgs p) {
             for (unsigned q = 0; q < C; ++q) st_async_f4(map_to_rank(slot, q), v, map_to_rank(xbar, q));
         }
         if (tid == 0) mbar_arrive_expect_tx(xbar, (uint32_t)(C * nw * 16));
-        if (!bad) bad = !mbar_wait(xbar, (uint32_t)(s >> 1) & 1u, p.status);
+        if (!mbar_wait(xbar, (uint32_t)(s >> 1) & 1u, p.status, p.wait_ns)) bad = true;
+        if (__any_sync(0xffffffffu, bad)) { bad = true; break; }
         m1 = m2 = cm = -kInf;
         k1 = 0x7fffffff;
         for (int q = lane; q < (int)C * 32; q += 32) {
@@ -257,8 +283,11 @@ __global__ void __launch_bounds__(MAXT, 1) rowpass_kernel(const RowPassArgs p) {
             }
         }
         warp_top2(m1, k1, m2, cm);
+        // debug_bounds: the row maximum of Eq. 2.1 must sit in a real column
+        // (alpha's padding is -inf; a NaN similarity leaves no maximum)
+        if (p.debug && tid == 0 && rank == 0 && (k1 < 0 || k1 >= N)) atomicOr(p.status, ST_BOUNDS);
         // every warp of this CTA has read stage st: refill it
-        if (tid == 0 && s + NST < nsteps) issue(s + NST);
+        if (tid == 0 && s + NST < nsteps) issue(issued++);
 
         // ---- inter-level messages of (i, l): Eqs. 2.4-2.6 --------------------
         const float cval = p.update_c ? cm : c_fixed;
@@ -313,8 +342,13 @@ __global__ void __launch_bounds__(MAXT, 1) rowpass_kernel(const RowPassArgs p) {
         if (++l == L) { l = 0; row += (int)G; }
     }
 
-    // ---- per-cluster column partials ------------------------------------------
-    for (int ll = 0; ll < L; ++ll) {
+    // ---- after a wait gave up: let this CTA's own bulk copies land ------------
+    if (tid == 0)
+        for (int q = consumed; q < issued; ++q)
+            mbar_wait(bar0 + 8 * (q % NST), (uint32_t)(q / NST) & 1u, p.status, kWaitNs);
+
+    // ---- per-cluster column partials (skipped by warps that gave up) ----------
+    for (int ll = 0; ll < L && !bad; ++ll) {
         if constexpr (TM) {
             float cur[4 * K];
             __syncwarp();
@@ -333,8 +367,12 @@ __global__ void __launch_bounds__(MAXT, 1) rowpass_kernel(const RowPassArgs p) {
         }
     }
     if constexpr (TM) {
+        __syncwarp();
+        tmem_store_wait();  // a warp that gave up may still have stores in flight
         tc_fence_before();
-        __syncthreads();
+    }
+    __syncthreads();
+    if constexpr (TM) {
         tc_fence_after();
         if (warp == 0) tmem_dealloc(*tslot, (uint32_t)tcols);
     }

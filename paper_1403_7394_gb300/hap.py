@@ -31,7 +31,7 @@ class HapOptions(ctypes.Structure):
                 ("s_per_level", ctypes.c_int), ("block_threads", ctypes.c_int),
                 ("cluster_size", ctypes.c_int), ("grid_clusters", ctypes.c_int),
                 ("elems_per_thread", ctypes.c_int), ("profile", ctypes.c_int), ("col_sums", ctypes.c_int),
-                ("kappa", ctypes.c_float)]
+                ("kappa", ctypes.c_float), ("wait_limit_ns", ctypes.c_int64), ("debug_bounds", ctypes.c_int)]
 
 
 def _load():
@@ -56,6 +56,7 @@ def _load():
         "hap_get_state": (i32, [vp, vp, vp, vp, ctypes.POINTER(i64)]),
         "hap_set_state": (i32, [vp, vp, vp, vp, i64]),
         "hap_sync": (i32, [vp]),
+        "hap_set_wait_limit": (i32, [vp, i64]),
         "hap_query": (i32, [vp, i32, ctypes.POINTER(i64)]),
         "hap_row_pass_time": (i32, [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64), i32]),
         "hap_strerror": (ctypes.c_char_p, [i32]),
@@ -131,7 +132,7 @@ def _ptr(t: torch.Tensor | None):
 
 def options(c_mode="paper", s_dtype="f32", s_per_level=False, block_threads=0, cluster_size=0,
             grid_clusters=0, elems_per_thread=0, profile=False, col_sums="auto", schedule="jacobi",
-            kappa=0.0) -> HapOptions:
+            kappa=0.0, wait_limit_ns=0, debug_bounds=False) -> HapOptions:
     o = HapOptions()
     lib.hap_default_options(ctypes.byref(o))
     o.c_mode = C_MODES[c_mode]
@@ -145,6 +146,8 @@ def options(c_mode="paper", s_dtype="f32", s_per_level=False, block_threads=0, c
     o.col_sums = COL_SUMS[col_sums]
     o.schedule = SCHEDULES[schedule]
     o.kappa = float(kappa)
+    o.wait_limit_ns = int(wait_limit_ns)
+    o.debug_bounds = int(bool(debug_bounds))
     return o
 
 
@@ -283,6 +286,10 @@ class HAP:
         check(lib.hap_set_state(self._h, _ptr(A), _ptr(R), _ptr(vecs), int(t)), "hap_set_state")
         self.sync()
 
+    def set_wait_limit(self, ns: int):
+        """Limit of the row pass's bounded device waits, in ns (0 = 2 s)."""
+        check(lib.hap_set_wait_limit(self._h, int(ns)), "hap_set_wait_limit")
+
     def sync(self):
         check(lib.hap_sync(self._h), "hap_sync")
 
@@ -321,15 +328,20 @@ def iterate_noalloc(N: int, L: int, damping: float, c_mode: str, S: torch.Tensor
     rounded up to 32): S (N, ld) float32/bfloat16, pref/c/tau/phi (L, ld),
     A/R (L, N, ld) float32.  Runs n iterations after t0, allocating nothing."""
     ld = (N + 31) // 32 * 32
+    if S.device.type != "cuda" or S.dtype not in (torch.float32, torch.bfloat16):
+        raise ValueError("S must be a float32 or bfloat16 CUDA tensor")
     for name, t, shape in (("S", S, (N, ld)), ("pref", pref, (L, ld)), ("A", A, (L, N, ld)), ("R", R, (L, N, ld)),
                            ("c", c, (L, ld)), ("tau", tau, (L, ld)), ("phi", phi, (L, ld))):
-        if tuple(t.shape) != shape or not t.is_contiguous() or t.device.type != "cuda":
-            raise ValueError(f"{name} must be a contiguous CUDA tensor of shape {shape}")
+        if tuple(t.shape) != shape or not t.is_contiguous() or t.device != S.device:
+            raise ValueError(f"{name} must be a contiguous tensor of shape {shape} on {S.device}")
+        if name != "S" and t.dtype != torch.float32:
+            raise ValueError(f"{name} must be float32")
     dt = {torch.float32: 0, torch.bfloat16: 1}[S.dtype]
-    st = stream if stream is not None else torch.cuda.current_stream(S.device)
-    check(lib.hap_iterate_noalloc(int(N), int(L), float(damping), C_MODES[c_mode], _ptr(S), dt, _ptr(pref),
-                                  _ptr(A), _ptr(R), _ptr(c), _ptr(tau), _ptr(phi), int(t0), int(n),
-                                  ctypes.c_void_p(st.cuda_stream)), "hap_iterate_noalloc")
+    with torch.cuda.device(S.device):  # the library uses the scratch array of the current device
+        st = stream if stream is not None else torch.cuda.current_stream(S.device)
+        check(lib.hap_iterate_noalloc(int(N), int(L), float(damping), C_MODES[c_mode], _ptr(S), dt, _ptr(pref),
+                                      _ptr(A), _ptr(R), _ptr(c), _ptr(tau), _ptr(phi), int(t0), int(n),
+                                      ctypes.c_void_p(st.cuda_stream)), "hap_iterate_noalloc")
 
 
 class HAPBatch:
