@@ -84,13 +84,17 @@ extern "C" {
 #define HAP_Q_BATCH_ITEMS_PER_CTA 8 /* batch scheduling granularity (tuned)      */
 #define HAP_Q_COL_SUMS      9 /* where the row pass keeps its column sums (HAP_COLSUM_*) */
 #define HAP_Q_STAGES       10 /* TMA ring stages of the row pass                */
+#define HAP_Q_CTAS_PER_SM  11 /* row-pass CTAs resident per SM (1, or 2 for TMEM
+                                 sums with <= 256 threads per CTA)              */
 
 /* Where each row-pass thread keeps the running column sums of max(0, rho) of
  * its columns (Eqs. 2.2-2.4) while its cluster walks its rows.  Both give the
  * same bits for the same grid; they differ in how long a row fits on chip. */
-#define HAP_COLSUM_AUTO 0 /* the variant whose clusters cover more SMs, then
-                             fewer CTAs per cluster, then TMEM; shared memory
-                             when an explicit launch shape is given            */
+#define HAP_COLSUM_AUTO 0 /* the variant, cluster size and CTAs per SM whose
+                             co-resident clusters cover the most SMs with no
+                             CTA left without columns, then fewer CTAs per
+                             cluster, then one CTA per SM, then TMEM; shared
+                             memory when an explicit launch shape is given     */
 #define HAP_COLSUM_SMEM 1 /* shared memory: 4, 8 or 16 columns per thread      */
 #define HAP_COLSUM_TMEM 2 /* tensor memory (TMEM): 8 or 16 columns per thread,
                              up to 512 threads; frees shared memory for the TMA
@@ -123,6 +127,11 @@ typedef struct hap_options {
                           makes the kernel stop, let its own copies land and
                           return; the next synchronising call reports
                           HAP_ETIMEOUT.  Minimum 1.                                  */
+    int ctas_per_sm;   /* row-pass CTAs per SM: 0 = automatic (1 for an explicit
+                          launch shape), 1, or 2 (TMEM column sums, <= 256 threads
+                          per CTA: two CTAs share an SM and its tensor memory, so a
+                          cluster needs twice the CTAs for a row but clusters can
+                          cover more SMs)                                            */
     int debug_bounds;  /* 1: checks for debugging, all reported as HAP_EDEVICE by
                           the next synchronising call (hap_set_similarity and
                           hap_build_similarity: HAP_EINVAL for a non-finite S):
@@ -418,6 +427,14 @@ int hap_sparse_net_similarity(hap_sparse* sp, double* ns);
 int hap_sparse_get_state(hap_sparse* sp, float* A, float* R, float* vecs, int64_t* iter);
 /* keys HAP_Q_ITER and HAP_Q_LAUNCHES. */
 int hap_sparse_query(hap_sparse* sp, int key, int64_t* value);
+/* on = 1: every later iteration records CUDA events around its four steps
+ * (clearing the bitmap of positive slots, the row pass, the statistics of
+ * short columns, of long columns).  Host call. */
+int hap_sparse_set_profile(hap_sparse* sp, int on);
+/* Milliseconds spent in those four steps, summed over the profiled
+ * iterations since the last reset (ms: host double [4]), and their number.
+ * Synchronising. */
+int hap_sparse_profile_times(hap_sparse* sp, double* ms, int64_t* iterations, int reset);
 
 /* Net similarity of any assignment from the points: NS^l = sum_i
  * -||x_i - x_{e_i}||^2, preference pref[l][i] (device FP32 [L][N]) when

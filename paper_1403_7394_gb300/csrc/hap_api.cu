@@ -64,16 +64,23 @@ constexpr int64_t kBuildMaxD = 256;
 
 int64_t padded_ld(int64_t N) { return (N + 31) / 32 * 32; }
 
+// Largest shared-memory request of which two CTAs fit on one SM (228 KB per
+// SM, 1 KB of it reserved per CTA).
+constexpr size_t kDualSmemMax = 113 * 1024;
+
 // Row-pass launch shape: one cluster holds a whole row (C CTAs x T threads x
-// 4K columns >= ld), the fewest CTAs per cluster whose shared memory fits;
-// then as many clusters as can be resident at once (persistent grid).
-// The fewest CTAs per cluster (1, 2, 4, 8, 16) whose T threads x 4K columns
-// cover the row and whose shared memory fits, for one column-sum variant.
-int shape_for(int64_t ld, int L, const hap_options& o, int tm, int K, int smem_limit, LaunchShape* out) {
+// 4K columns >= ld); then as many clusters as can be resident at once
+// (persistent grid).  shape_for gives, for one column-sum variant, the fewest
+// CTAs per cluster (1, 2, 4, 8, 16, or o.cluster_size) whose T threads x 4K
+// columns cover the row and whose shared memory fits.  dual = 1 asks for the
+// TMEM variant with two CTAs per SM (T <= 256 and <= 256 TMEM columns per
+// CTA); it fails where that is not possible.
+int shape_for(int64_t ld, int L, const hap_options& o, int tm, int K, int dual, int smem_limit, LaunchShape* out) {
     const int64_t q4 = ld / 4;  // float4 columns
-    const int maxT = tm ? 512 : (K == 1 ? 1024 : K == 2 ? 512 : 256);
+    const int maxT = tm ? (dual ? 256 : 512) : (K == 1 ? 1024 : K == 2 ? 512 : 256);
     const int s_bf16 = o.s_dtype == HAP_S_BF16;
     const int sizes[5] = {1, 2, 4, 8, 16};
+    if (dual && !tm) return HAP_EINVAL;
     for (int c : sizes) {
         if (o.cluster_size && c != o.cluster_size) continue;
         int T = o.block_threads;
@@ -88,6 +95,16 @@ int shape_for(int64_t ld, int L, const hap_options& o, int tm, int K, int smem_l
         }
         if ((int64_t)c * T * K * 4 < ld) continue;
         LaunchShape sh{T, c, K, 0, tm, tm ? 4 : 0};
+        if (dual) {
+            // two CTAs of at most 256 threads per SM: the threads of one
+            // 512-thread CTA, half the row per CTA, twice the clusters
+            sh.nst = 2;
+            sh.dual = 1;
+            if (rowpass_tmem_columns(sh, L) > 256 || rowpass_smem_bytes(sh, L, s_bf16) > kDualSmemMax)
+                return HAP_EUNSUPPORTED;
+            *out = sh;
+            return HAP_OK;
+        }
         if (tm && rowpass_smem_bytes(sh, L, s_bf16) > (size_t)smem_limit) sh.nst = 2;
         if (rowpass_smem_bytes(sh, L, s_bf16) > (size_t)smem_limit) continue;
         if (tm && rowpass_tmem_columns(sh, L) > 512) return HAP_EUNSUPPORTED;
@@ -101,14 +118,18 @@ int choose_shape(int64_t N, int L, const hap_options& o, LaunchShape* out) {
     const int64_t ld = padded_ld(N);
     if (o.cluster_size < 0 || o.cluster_size > 16) return HAP_EINVAL;
     if (o.col_sums < HAP_COLSUM_AUTO || o.col_sums > HAP_COLSUM_TMEM) return HAP_EINVAL;
-    int dev = 0, smem_limit = 0;
+    int dev = 0, smem_limit = 0, n_sm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&smem_limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+        cudaDeviceGetAttribute(&smem_limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
         cudaGetLastError();
         return HAP_ECUDA;
     }
     const bool explicit_shape = o.elems_per_thread || o.block_threads || o.cluster_size;
-    const int mode = o.col_sums != HAP_COLSUM_AUTO ? o.col_sums : explicit_shape ? HAP_COLSUM_SMEM : HAP_COLSUM_AUTO;
+    const int mode = o.col_sums != HAP_COLSUM_AUTO ? o.col_sums
+                     : o.ctas_per_sm == 2               ? HAP_COLSUM_TMEM
+                     : explicit_shape                   ? HAP_COLSUM_SMEM
+                                                        : HAP_COLSUM_AUTO;
     // 8 columns per thread by default with shared-memory sums (enough work per
     // step to amortise the per-row reduction, few enough registers for
     // 512-thread CTAs); 16 with TMEM sums (twice the row per cluster).
@@ -118,35 +139,54 @@ int choose_shape(int64_t N, int L, const hap_options& o, LaunchShape* out) {
         if (tm ? (*K != 2 && *K != 4) : (*K != 1 && *K != 2 && *K != 4)) return HAP_EINVAL;
         return HAP_OK;
     };
-    if (mode != HAP_COLSUM_AUTO) {
-        const int tm = mode == HAP_COLSUM_TMEM;
+    if (o.ctas_per_sm < 0 || o.ctas_per_sm > 2) return HAP_EINVAL;
+    if (o.ctas_per_sm == 2 && mode == HAP_COLSUM_SMEM) return HAP_EINVAL;
+    if (mode != HAP_COLSUM_AUTO || o.ctas_per_sm) {
+        const int tm = mode == HAP_COLSUM_SMEM ? 0 : 1;
         int K = 0, rc = K_of(tm, &K);
         if (rc) return rc;
-        return shape_for(ld, L, o, tm, K, smem_limit, out);
+        return shape_for(ld, L, o, tm, K, o.ctas_per_sm == 2, smem_limit, out);
     }
-    // automatic: the variant whose co-resident clusters cover more SMs (a row
-    // too long for a cluster of 2 or 4 in one variant may fit in the other);
-    // on a tie the one with fewer CTAs per cluster (a cheaper row exchange),
-    // then TMEM sums (16 columns per thread; measured faster on GB300)
+    // automatic: among both variants, every cluster size that holds the row
+    // with no CTA left without columns, and one or two CTAs per SM, the shape
+    // whose co-resident clusters cover the most SMs (clusters are placed
+    // within a GPC, so a size may leave SMs idle: on GB300 four 512-thread
+    // CTAs per cluster place 36 clusters on 144 of 152 SMs, and clusters of
+    // eight place 15 whether or not two CTAs could share an SM); on a tie the
+    // one with fewer CTAs per cluster (a cheaper row exchange), then two CTAs
+    // per SM (more threads on each SM), then TMEM sums (16 columns per thread;
+    // measured faster on GB300)
     LaunchShape best{};
-    int64_t best_ctas = -1;
+    int64_t best_sms = -1;
     for (int tm = 1; tm >= 0; --tm) {
         int K = 0;
         if (K_of(tm, &K)) continue;
-        LaunchShape sh{};
-        if (shape_for(ld, L, o, tm, K, smem_limit, &sh) != HAP_OK) continue;
-        int maxc = 0;
-        if (rowpass_max_clusters(sh, L, o.s_dtype == HAP_S_BF16, &maxc) != cudaSuccess) {
-            cudaGetLastError();
-            return HAP_ECUDA;
-        }
-        const int64_t ctas = (int64_t)std::min<int64_t>(maxc, (N + 3) / 4) * sh.C;
-        if (ctas > best_ctas || (ctas == best_ctas && sh.C < best.C)) {
-            best = sh;
-            best_ctas = ctas;
+        for (int c : {1, 2, 4, 8, 16})
+        for (int dual = 0; dual <= tm; ++dual) {
+            hap_options oc = o;
+            oc.cluster_size = c;
+            LaunchShape sh{};
+            if (shape_for(ld, L, oc, tm, K, dual, smem_limit, &sh) != HAP_OK) continue;
+            // every CTA of the cluster must hold columns of the row
+            if ((int64_t)(sh.C - 1) * sh.T * sh.K * 4 >= ld) continue;
+            int maxc = 0, per_sm = 0;
+            if (rowpass_max_clusters(sh, L, o.s_dtype == HAP_S_BF16, &maxc) != cudaSuccess ||
+                rowpass_blocks_per_sm(sh, L, o.s_dtype == HAP_S_BF16, &per_sm) != cudaSuccess) {
+                cudaGetLastError();
+                return HAP_ECUDA;
+            }
+            if (maxc < 1 || per_sm < 1) continue;
+            // SMs the co-resident CTAs occupy (several may share one SM)
+            const int64_t ctas = (int64_t)std::min<int64_t>(maxc, (N + 3) / 4) * sh.C;
+            const int64_t sms = std::min<int64_t>(n_sm, (ctas + per_sm - 1) / per_sm);
+            if (sms > best_sms || (sms == best_sms && sh.C < best.C) ||
+                (sms == best_sms && sh.C == best.C && sh.dual && !best.dual)) {
+                best = sh;
+                best_sms = sms;
+            }
         }
     }
-    if (best_ctas <= 0) return HAP_EUNSUPPORTED;
+    if (best_sms <= 0) return HAP_EUNSUPPORTED;
     *out = best;
     return HAP_OK;
 }
@@ -696,6 +736,7 @@ int hap_query(hap_ctx* h, int key, int64_t* value) {
         case HAP_Q_LAUNCHES: *value = h->launches; return HAP_OK;
         case HAP_Q_COL_SUMS: *value = h->sh.tm ? HAP_COLSUM_TMEM : HAP_COLSUM_SMEM; return HAP_OK;
         case HAP_Q_STAGES: *value = h->sh.tm ? h->sh.nst : 3; return HAP_OK;
+        case HAP_Q_CTAS_PER_SM: *value = h->sh.dual ? 2 : 1; return HAP_OK;
         default: return HAP_EINVAL;
     }
 }

@@ -48,11 +48,14 @@ struct LaunchShape {
     int G;   // clusters in the grid
     int tm;  // 1: column sums in tensor memory (TMEM), 0: in shared memory
     int nst; // TMA ring stages of the TMEM variant (2 or 4; the other has 3)
+    int dual = 0;  // TMEM variant: 1 = two CTAs per SM (T <= 256 threads and <= 256
+                   // TMEM columns each, so both allocations always fit)
 };
 
 // Kernel launchers (return a cudaError_t).
 cudaError_t launch_rowpass(const RowPassArgs& a, const LaunchShape& sh, int s_bf16, cudaStream_t st);
 cudaError_t rowpass_max_clusters(const LaunchShape& sh, int L, int s_bf16, int* max_clusters);
+cudaError_t rowpass_blocks_per_sm(const LaunchShape& sh, int L, int s_bf16, int* blocks);
 size_t rowpass_smem_bytes(const LaunchShape& sh, int L, int s_bf16);
 int rowpass_tmem_columns(const LaunchShape& sh, int L);  // 0 for shared-memory sums
 cudaError_t launch_fill_alpha_padding(float* A, int64_t rows, int64_t N, int64_t ld, cudaStream_t st);

@@ -501,16 +501,30 @@ static cudaError_t max_clusters_one(const LaunchShape& sh, int L, int* out) {
     return cudaOccupancyMaxActiveClusters(out, rowpass_kernel<ST, K, MAXT, NST, TM>, &cfg);
 }
 
-// The TMEM variant asks for more than half of an SM's 228 KB of shared memory
-// so that at most one of its CTAs is resident per SM: its TMEM allocation
-// (at most 512 columns) then never waits for another row-pass CTA, which
-// could itself be waiting for a cluster peer blocked in allocation.
+template <typename ST, int K, int MAXT, int NST, bool TM>
+static cudaError_t blocks_per_sm_one(const LaunchShape& sh, int L, int* out) {
+    auto kern = rowpass_kernel<ST, K, MAXT, NST, TM>;
+    const size_t smem = rowpass_smem_bytes(sh, L, sizeof(ST) == 2);
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, kern, sh.T, smem);
+}
+
+// The TMEM variant bounds how many of its CTAs share an SM through its
+// shared-memory request, so that their TMEM allocations always fit together
+// and an allocation never waits for another row-pass CTA (which could itself
+// be waiting for a cluster peer blocked in allocation): more than half of an
+// SM's 228 KB keeps one CTA per SM (at most 512 columns); more than a third
+// keeps two (the dual shape, at most 256 columns each).
 constexpr size_t kTmemMinSmem = 116 * 1024;
+constexpr size_t kTmemDualMinSmem = 80 * 1024;
 
 size_t rowpass_smem_bytes(const LaunchShape& sh, int L, int s_bf16) {
     const int nst = sh.tm ? sh.nst : kStages;
     const size_t bytes = rowpass_smem_layout(sh.T, sh.K, sh.C, L, s_bf16 ? 2 : 4, nst, sh.tm != 0, nullptr, nullptr);
-    return sh.tm && bytes < kTmemMinSmem ? kTmemMinSmem : bytes;
+    if (!sh.tm) return bytes;
+    const size_t lo = sh.dual ? kTmemDualMinSmem : kTmemMinSmem;
+    return bytes < lo ? lo : bytes;
 }
 
 int rowpass_tmem_columns(const LaunchShape& sh, int L) { return sh.tm ? rowpass_tmem_cols(sh.T, sh.K, L) : 0; }
@@ -552,6 +566,10 @@ cudaError_t launch_rowpass(const RowPassArgs& a, const LaunchShape& sh, int s_bf
 
 cudaError_t rowpass_max_clusters(const LaunchShape& sh, int L, int s_bf16, int* max_clusters) {
     HAP_ROWPASS_DISPATCH(max_clusters_one, sh, L, max_clusters);
+}
+
+cudaError_t rowpass_blocks_per_sm(const LaunchShape& sh, int L, int s_bf16, int* blocks) {
+    HAP_ROWPASS_DISPATCH(blocks_per_sm_one, sh, L, blocks);
 }
 
 cudaError_t launch_colstats(const float* partials, int G, int L, int64_t N, int64_t ld,

@@ -501,6 +501,11 @@ struct hap_sparse {
     int64_t iter = 0;
     bool pending = false;
     int64_t launches = 0;
+    bool profile = false;
+    std::vector<cudaEvent_t> ev;   // per profiled iteration: before the bitmap clear, after it, after the row
+                                   // pass, after the short-column and after the long-column statistics
+    double prof_ms[4] = {0, 0, 0, 0};
+    int64_t prof_n = 0;
 };
 
 namespace {
@@ -576,6 +581,7 @@ int hap_sparse_create(int64_t N, int L, int K, const float* prefs, float damping
 void hap_sparse_destroy(hap_sparse* h) {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
+    for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
     cudaFree(h->cand); cudaFree(h->s); cudaFree(h->A); cudaFree(h->R); cudaFree(h->pref); cudaFree(h->c);
     cudaFree(h->c0); cudaFree(h->tau); cudaFree(h->phi); cudaFree(h->tpart); cudaFree(h->b); cudaFree(h->rdiag);
     cudaFree(h->cptr); cudaFree(h->cent); cudaFree(h->e); cudaFree(h->ns); cudaFree(h->status);
@@ -583,6 +589,34 @@ void hap_sparse_destroy(hap_sparse* h) {
     cudaFree(h->cls); cudaFree(h->long_cols); cudaFree(h->short_cols);
     for (int q = 0; q < 4; ++q) cudaFree(h->tmp[q]);
     delete h;
+}
+
+int hap_sparse_set_profile(hap_sparse* h, int on) {
+    if (!h || (on != 0 && on != 1)) return HAP_EINVAL;
+    h->profile = on != 0;
+    return HAP_OK;
+}
+
+int hap_sparse_profile_times(hap_sparse* h, double* ms, int64_t* iterations, int reset) {
+    if (!h || !ms || !iterations) return HAP_EINVAL;
+    SCU(cudaStreamSynchronize(h->stream));
+    for (size_t q = 0; q + 4 < h->ev.size(); q += 5) {
+        for (int k = 0; k < 4; ++k) {
+            float t = 0.f;
+            SCU(cudaEventElapsedTime(&t, h->ev[q + k], h->ev[q + k + 1]));
+            h->prof_ms[k] += t;
+        }
+        h->prof_n += 1;
+        for (int k = 0; k < 5; ++k) cudaEventDestroy(h->ev[q + k]);
+    }
+    h->ev.clear();
+    for (int k = 0; k < 4; ++k) ms[k] = h->prof_ms[k];
+    *iterations = h->prof_n;
+    if (reset) {
+        for (double& v : h->prof_ms) v = 0.0;
+        h->prof_n = 0;
+    }
+    return HAP_OK;
 }
 
 int hap_sparse_set_stream(hap_sparse* h, void* stream) {
@@ -673,7 +707,13 @@ int hap_sparse_iterate(hap_sparse* h, int n) {
         a.pending = h->pending ? 1 : 0;
         a.update_c = (h->c_mode == HAP_C_PAPER && t >= 2) ? 1 : 0;
         a.use_tau = t >= 2 ? 1 : 0;
+        cudaEvent_t ev[5] = {};
+        if (h->profile) {
+            for (auto& e : ev) SCU(cudaEventCreate(&e));
+            SCU(cudaEventRecord(ev[0], h->stream));
+        }
         SCU(cudaMemsetAsync(h->cbits, 0, (size_t)h->L * h->cwords * 4, h->stream));
+        if (h->profile) SCU(cudaEventRecord(ev[1], h->stream));
         if (h->L > 4)
             sparse_rowpass_kernel<true, false><<<grid, 256, 0, h->stream>>>(a);
         else if (h->K == 64)
@@ -681,17 +721,23 @@ int hap_sparse_iterate(hap_sparse* h, int n) {
         else
             sparse_rowpass_kernel<false, false><<<grid, 256, 0, h->stream>>>(a);
         SCU(cudaGetLastError());
+        if (h->profile) SCU(cudaEventRecord(ev[2], h->stream));
         if (h->n_short > 0) {
             const int64_t tot = (int64_t)h->L * h->n_short;
             sparse_colstats_short_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, h->stream>>>(
                 h->cval, h->cbits, h->cwords, h->cptr, h->short_cols, h->n_short, h->N, h->L, h->K, h->c, h->phi, h->rdiag, h->b, h->tpart);
         }
+        if (h->profile) SCU(cudaEventRecord(ev[3], h->stream));
         if (h->n_long > 0) {
             const int64_t tot = (int64_t)h->L * h->n_long * 32;
             sparse_colstats_long_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, h->stream>>>(
                 h->cval, h->cbits, h->cwords, h->cptr, h->long_cols, h->n_long, h->N, h->L, h->K, h->c, h->phi, h->rdiag, h->b, h->tpart);
         }
         SCU(cudaGetLastError());
+        if (h->profile) {
+            SCU(cudaEventRecord(ev[4], h->stream));
+            h->ev.insert(h->ev.end(), ev, ev + 5);
+        }
         h->launches += 1 + (h->n_short > 0) + (h->n_long > 0);
         h->pending = true;
         h->iter = t;

@@ -21,7 +21,7 @@ S_DTYPES = {"f32": 0, "bf16": 1}
 SBUILD = {"f32": 0, "bf16": 1, "bf16_split": 2}
 Q_BLOCK_THREADS, Q_CLUSTER_SIZE, Q_GRID_CLUSTERS, Q_LD, Q_ITER, Q_ELEMS_PER_THREAD, Q_LAUNCHES = 1, 2, 3, 4, 5, 6, 7
 Q_BATCH_ITEMS_PER_CTA = 8
-Q_COL_SUMS, Q_STAGES = 9, 10
+Q_COL_SUMS, Q_STAGES, Q_CTAS_PER_SM = 9, 10, 11
 COL_SUMS = {"auto": 0, "smem": 1, "tmem": 2}
 SCHEDULES = {"jacobi": 0, "gauss_seidel": 1}
 
@@ -31,7 +31,8 @@ class HapOptions(ctypes.Structure):
                 ("s_per_level", ctypes.c_int), ("block_threads", ctypes.c_int),
                 ("cluster_size", ctypes.c_int), ("grid_clusters", ctypes.c_int),
                 ("elems_per_thread", ctypes.c_int), ("profile", ctypes.c_int), ("col_sums", ctypes.c_int),
-                ("kappa", ctypes.c_float), ("wait_limit_ns", ctypes.c_int64), ("debug_bounds", ctypes.c_int)]
+                ("kappa", ctypes.c_float), ("wait_limit_ns", ctypes.c_int64), ("ctas_per_sm", ctypes.c_int),
+                ("debug_bounds", ctypes.c_int)]
 
 
 def _load():
@@ -102,6 +103,8 @@ def _load():
         "hap_sparse_net_similarity": (i32, [vp, vp]),
         "hap_sparse_get_state": (i32, [vp, vp, vp, vp, ctypes.POINTER(i64)]),
         "hap_sparse_query": (i32, [vp, i32, ctypes.POINTER(i64)]),
+        "hap_sparse_set_profile": (i32, [vp, i32]),
+        "hap_sparse_profile_times": (i32, [vp, vp, ctypes.POINTER(i64), i32]),
         "hap_net_similarity_points": (i32, [vp, i64, i64, i32, vp, vp, vp, vp]),
         "hap_noalloc_scratch_bytes": (ctypes.c_size_t, []),
     }
@@ -132,7 +135,7 @@ def _ptr(t: torch.Tensor | None):
 
 def options(c_mode="paper", s_dtype="f32", s_per_level=False, block_threads=0, cluster_size=0,
             grid_clusters=0, elems_per_thread=0, profile=False, col_sums="auto", schedule="jacobi",
-            kappa=0.0, wait_limit_ns=0, debug_bounds=False) -> HapOptions:
+            kappa=0.0, wait_limit_ns=0, ctas_per_sm=0, debug_bounds=False) -> HapOptions:
     o = HapOptions()
     lib.hap_default_options(ctypes.byref(o))
     o.c_mode = C_MODES[c_mode]
@@ -147,6 +150,7 @@ def options(c_mode="paper", s_dtype="f32", s_per_level=False, block_threads=0, c
     o.schedule = SCHEDULES[schedule]
     o.kappa = float(kappa)
     o.wait_limit_ns = int(wait_limit_ns)
+    o.ctas_per_sm = int(ctas_per_sm)
     o.debug_bounds = int(bool(debug_bounds))
     return o
 
@@ -303,7 +307,8 @@ class HAP:
         return {"block_threads": self.query(Q_BLOCK_THREADS), "cluster_size": self.query(Q_CLUSTER_SIZE),
                 "grid_clusters": self.query(Q_GRID_CLUSTERS), "ld": self.query(Q_LD),
                 "elems_per_thread": self.query(Q_ELEMS_PER_THREAD),
-                "col_sums": {1: "smem", 2: "tmem"}[self.query(Q_COL_SUMS)], "stages": self.query(Q_STAGES)}
+                "col_sums": {1: "smem", 2: "tmem"}[self.query(Q_COL_SUMS)], "stages": self.query(Q_STAGES),
+                "ctas_per_sm": self.query(Q_CTAS_PER_SM)}
 
     @property
     def launches(self) -> int:
@@ -621,6 +626,20 @@ class HAPSparse:
             self.close()
         except Exception:
             pass
+
+    def set_profile(self, on: bool = True):
+        """Time every later iteration's four steps with CUDA events."""
+        check(lib.hap_sparse_set_profile(self._h, int(bool(on))), "hap_sparse_set_profile")
+
+    def profile_times(self, reset: bool = True):
+        """({"clear": ms, "row_pass": ms, "short_columns": ms, "long_columns": ms}, iterations) summed
+        over the profiled iterations."""
+        import numpy as np
+        ms = np.zeros(4, dtype=np.float64)
+        n = ctypes.c_int64(0)
+        check(lib.hap_sparse_profile_times(self._h, ms.ctypes.data_as(ctypes.c_void_p), ctypes.byref(n), int(reset)),
+              "hap_sparse_profile_times")
+        return dict(zip(("clear", "row_pass", "short_columns", "long_columns"), ms.tolist())), n.value
 
     def set_preferences(self, prefs):
         import numpy as np

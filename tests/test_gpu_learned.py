@@ -1,4 +1,8 @@
-"""What the trained proposal network gains over plain kNN candidates.
+"""What the trained proposal network gains over plain kNN candidates, and
+over hubs chosen without it (seeded random scores; a density score with no
+learning, -log of the distance to the 16th nearest neighbour), at the same
+K, hub count and number of nearest neighbours kept, averaged over three test
+instances.
 
 The network is trained on the GPU (hand-written forward/backward/Adam
 kernels) on exemplar labels from dense HAP runs of two training instances,
@@ -65,31 +69,46 @@ def test_learned_candidates_beat_nearest_neighbours(report):
         mlp.train_step(Fm, Y, posw, 3e-3)
     l1 = mlp.train_step(Fm, Y, posw, 3e-3, want_loss=True)
 
-    X32, _, prefs = _instance(3)
-    e_dense = _dense(hap, X32, prefs)
-    Xt = torch.from_numpy(X32).to(DEV)
-    pref_t = torch.from_numpy(np.repeat(prefs[:, None], N, axis=1)).to(DEV)
-    ns_dense = hap.net_similarity_points(Xt, torch.from_numpy(e_dense).to(DEV), pref_t)
-    pool, dist = hap.knn(Xt, 32)
-    f, _ = hap.knn_features(dist, 16)
-    score = mlp.forward(f)
-    hubs = hap.top_scores(score, N // 64)
-    hubnn, _ = hap.knn_subset(Xt, hubs, K)
-    res = {}
-    for name in ("knn", "learned"):
-        if name == "knn":
-            cand = hap.select_candidates(pool, K, K - 1, None)
-        else:
-            cand = hap.select_hub_candidates(pool, hubnn, K, K // 2)
-        sp = hap.HAPSparse(N, L, K, prefs=prefs, damping=LAM, c_mode="fixed", device=DEV)
-        sp.set_candidates(cand, Xt)
-        sp.iterate(T)
-        e = sp.exemplars().cpu().numpy()
-        ns = sp.net_similarity()
-        sp.close()
-        res[name] = {"ari": H.adjusted_rand_index(e[0], e_dense[0]),
-                     "gap": float((ns_dense[0] - ns[0]) / abs(ns_dense[0])), "n_exemplars": int(len(np.unique(e[0])))}
-    report(loss=[l0, l1], dense_exemplars=int(len(np.unique(e_dense[0]))), **res)
+    res = {k: {"ari": [], "gap": [], "n_exemplars": []} for k in ("knn", "learned", "random_hubs", "density_hubs")}
+    dense_ex = []
+    for seed in (3, 4, 5):  # three test instances
+        X32, _, prefs = _instance(seed)
+        e_dense = _dense(hap, X32, prefs)
+        dense_ex.append(int(len(np.unique(e_dense[0]))))
+        Xt = torch.from_numpy(X32).to(DEV)
+        pref_t = torch.from_numpy(np.repeat(prefs[:, None], N, axis=1)).to(DEV)
+        ns_dense = hap.net_similarity_points(Xt, torch.from_numpy(e_dense).to(DEV), pref_t)
+        pool, dist = hap.knn(Xt, 32)
+        f, _ = hap.knn_features(dist, 16)
+        scores = {"learned": mlp.forward(f),
+                  "random_hubs": torch.rand(N, generator=torch.Generator(device=DEV).manual_seed(seed), device=DEV),
+                  "density_hubs": -torch.log(dist[:, 15].clamp_min(1e-30))}
+        for name in res:
+            if name == "knn":
+                cand = hap.select_candidates(pool, K, K - 1, None)
+            else:
+                hubs = hap.top_scores(scores[name].contiguous(), N // 64)
+                hubnn, _ = hap.knn_subset(Xt, hubs, K)
+                cand = hap.select_hub_candidates(pool, hubnn, K, K // 2)
+            sp = hap.HAPSparse(N, L, K, prefs=prefs, damping=LAM, c_mode="fixed", device=DEV)
+            sp.set_candidates(cand, Xt)
+            sp.iterate(T)
+            e = sp.exemplars().cpu().numpy()
+            ns = sp.net_similarity()
+            sp.close()
+            res[name]["ari"].append(H.adjusted_rand_index(e[0], e_dense[0]))
+            res[name]["gap"].append(float((ns_dense[0] - ns[0]) / abs(ns_dense[0])))
+            res[name]["n_exemplars"].append(int(len(np.unique(e[0]))))
+    mean = {k: {m: float(np.mean(v[m])) for m in ("ari", "gap")} for k, v in res.items()}
+    report(loss=[l0, l1], dense_exemplars=dense_ex, mean=mean, **res)
+    print({"loss": [l0, l1], "dense_exemplars": dense_ex, "mean": mean, **res})
     assert l1 < l0
-    assert res["learned"]["ari"] >= res["knn"]["ari"] + 0.3
-    assert res["learned"]["gap"] < 0.25 * res["knn"]["gap"]
+    assert mean["learned"]["ari"] >= mean["knn"]["ari"] + 0.3
+    assert mean["learned"]["gap"] < 0.25 * mean["knn"]["gap"]
+    # the trained scores choose better hubs than chance (measured on GB300:
+    # gap 0.056 vs 0.258, ARI 0.922 vs 0.865) ...
+    assert mean["learned"]["gap"] < 0.5 * mean["random_hubs"]["gap"]
+    assert mean["learned"]["ari"] >= mean["random_hubs"]["ari"] + 0.02
+    # ... but not better than ranking by the 16th-neighbour distance alone
+    # (gap 0.059, ARI 0.927): the network has learned a density score.  This
+    # is reported (parity report and stdout), not asserted either way.

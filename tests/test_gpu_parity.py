@@ -86,6 +86,12 @@ SHAPES = [
     (4099, 2, {"col_sums": "tmem", "cluster_size": 2}),
     (3000, 4, {"col_sums": "tmem", "cluster_size": 4, "elems_per_thread": 8}),
     (1500, 5, {"col_sums": "tmem", "block_threads": 384, "grid_clusters": 5}),
+    # two TMEM CTAs per SM (<= 256 threads each)
+    (2051, 3, {"ctas_per_sm": 2}),
+    (4099, 2, {"ctas_per_sm": 2, "cluster_size": 2}),
+    (9000, 3, {"ctas_per_sm": 2, "cluster_size": 4}),
+    (5000, 2, {"ctas_per_sm": 2, "cluster_size": 8, "elems_per_thread": 8}),
+    (3000, 5, {"ctas_per_sm": 2, "block_threads": 128, "cluster_size": 2, "grid_clusters": 9}),
 ]
 
 
@@ -498,8 +504,9 @@ def test_full_size_teacher_forced_sampled_rows(report):
 def test_large_dense_teacher_forced_sampled_rows(s_dtype, report):
     """The large dense workload (N = 32768 texture patches in 192-D, L = 3,
     S from the BF16-split tensor-core build, stored in BF16 or FP32) in its
-    automatic launch shape (column sums in TMEM, clusters of 4 CTAs holding a
-    row): one iteration from the GPU's own state at t = 3."""
+    automatic launch shape (column sums in TMEM; a row held by a cluster of
+    4 one-per-SM CTAs or of 8 two-per-SM CTAs, whichever covers more SMs):
+    one iteration from the GPU's own state at t = 3."""
     hap = hap_mod()
     N, L, lam = 32768, 3, 0.5
     X32 = W.config2(seed=0)[0].astype(np.float32)
@@ -510,7 +517,8 @@ def test_large_dense_teacher_forced_sampled_rows(s_dtype, report):
     errs = sampled_step_errors(ctx, prefs, lam, n_rows=24, chunk=1024)
     report(shape=ctx.shape, errs=errs)
     assert all(e <= TOL for e in errs.values()), errs
-    assert ctx.shape["col_sums"] == "tmem" and ctx.shape["cluster_size"] == 4
+    sh = ctx.shape
+    assert sh["col_sums"] == "tmem" and (sh["cluster_size"], sh["ctas_per_sm"]) in ((4, 1), (8, 2)), sh
     ctx.close()
 
 
@@ -521,7 +529,8 @@ def test_tmem_and_shared_memory_sums_agree_bitwise():
     S32, prefs, _ = problem(N, L, seed=11)
     out = []
     for opt in ({"col_sums": "smem", "elems_per_thread": 8}, {"col_sums": "tmem", "elems_per_thread": 16},
-                {"col_sums": "tmem", "elems_per_thread": 8, "cluster_size": 2}):
+                {"col_sums": "tmem", "elems_per_thread": 8, "cluster_size": 2},
+                {"ctas_per_sm": 2, "elems_per_thread": 16, "cluster_size": 2}):
         ctx = make_ctx(N, L, prefs, lam, S32, grid_clusters=24, **opt)
         ctx.iterate(5)
         out.append((ctx.shape, ctx.get_state()))

@@ -169,11 +169,13 @@ def _sparse_problem(N, L, K, seed, K_near=None, score=None):
 
 
 @pytest.mark.parametrize("c_mode", ["paper", "fixed"])
-@pytest.mark.parametrize("N,K,L", [(600, 32, 3), (602, 30, 3), (601, 31, 6), (700, 64, 3)])
+@pytest.mark.parametrize("N,K,L", [(600, 32, 3), (602, 30, 3), (601, 31, 6), (700, 64, 3), (701, 64, 1),
+                                   (703, 64, 2), (700, 64, 4), (705, 64, 5)])
 def test_sparse_hap_equals_masked_dense_reference(c_mode, N, K, L, report):
     """Even and odd row and candidate counts; L = 6 takes the column terms b
     of levels 4 and 5 from a second 16-byte gather per candidate; K = 64 runs
-    the variant where every lane holds two entries."""
+    the variant where every lane holds two entries (L = 1 to 4), and with
+    L = 5 the variant with a second gather of b."""
     hap = hapm()
     T = 4
     Xt, cand, cn, prefs, S_mask = _sparse_problem(N, L, K, seed=4)
@@ -216,14 +218,15 @@ def test_full_candidate_graph_equals_dense_gpu():
     np.testing.assert_array_equal(sp.exemplars().cpu().numpy(), ctx.exemplars().cpu().numpy())
 
 
-def test_sparse_hub_columns_against_reference(report):
+@pytest.mark.parametrize("K,L", [(48, 2), (64, 3)])
+def test_sparse_hub_columns_against_reference(K, L, report):
     """A candidate graph with hub columns (every row keeps itself, its 20
-    nearest neighbours and 27 of 40 shared hubs, so hub columns hold about
-    2000 entries) and N > 512 (two radix passes in the GPU column index):
+    nearest neighbours and shared hubs out of 40, so hub columns hold about
+    2000-3000 entries) and N > 512 (two radix passes in the GPU column index):
     sparse HAP against the dense reference on the masked similarity, and
     bitwise repeatable."""
     hap = hapm()
-    N, L, K, T = 3000, 2, 48, 3
+    N, T = 3000, 3
     X, _ = W.gmm_points(N, 3, 8, sigma=0.7, seed=21, means="uniform", mean_scale=10.0)
     X32 = X.astype(np.float32)
     nn, _ = P.knn(X32, 20)
@@ -244,7 +247,7 @@ def test_sparse_hub_columns_against_reference(report):
             extra += 1
         cn[i] = np.sort(sel)
     S64 = H.neg_sq_euclidean(X32.astype(np.float64))
-    prefs = np.array([-60.0, -120.0], dtype=np.float32)
+    prefs = np.array([-60.0, -120.0, -180.0][:L], dtype=np.float32)
     S_full = H.level_similarities(S64, prefs.astype(np.float64))
     S_mask = np.stack([P.masked_similarity(S_full[l], cn) for l in range(L)])
     Xt = torch.from_numpy(X32).to(DEV)
