@@ -440,7 +440,7 @@ def main():
     bytes_per_launch = float(N) * N * (16 * L + s_bytes)
     avg_rp_s = (rp_ms / rp_n) / 1e3 if rp_n else float("nan")
     achieved = bytes_per_launch / avg_rp_s / 1e9
-    traffic = ncu_traffic(args.workload, args.s_dtype) if N == WORKLOADS[args.workload][0] else None
+    traffic = ncu_traffic(args.workload, args.s_dtype, N) if N == WORKLOADS[args.workload][0] else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "peak_source": peak_src,
             "kernel": "rowpass_kernel", "launches_timed": rp_n, "avg_launch_ms": avg_rp_s * 1e3,
@@ -844,9 +844,11 @@ def run_learned(args, world, rank, local):
         torch.distributed.destroy_process_group()
 
 
-def ncu_traffic(workload: str, s_dtype: str):
-    """DRAM bytes per row-pass launch from the committed ncu summary, if it was
-    taken on this workload with the current row-pass source (else None)."""
+def ncu_traffic(workload: str, s_dtype: str, N: int):
+    """DRAM bytes per row-pass launch at N points from the committed ncu
+    summary, if it was taken on this workload with the current row-pass
+    source (else None).  A summary taken on the first measured_n points is
+    scaled by (N / measured_n)^2: every term of the traffic grows as N^2."""
     import re
     p = os.path.join(ROOT, "profiles", f"rowpass_{workload}_ncu.md")
     if not os.path.exists(p):
@@ -854,7 +856,8 @@ def ncu_traffic(workload: str, s_dtype: str):
     fields = dict(re.findall(r"^\s+(\w+): (\S+)$", open(p).read(), flags=re.M))
     if fields.get("kernel_hash") != kernel_hash() or fields.get("s_dtype") != s_dtype:
         return None
-    return float(fields["dram_bytes_per_launch"])
+    n0 = int(fields.get("measured_n", N))
+    return float(fields["dram_bytes_per_launch"]) * (N / n0) ** 2
 
 
 def kernel_hash() -> str:

@@ -43,6 +43,7 @@ struct hap_ctx {
     int64_t launches = 0;  // kernels launched by this context
     int64_t iter = 0;
     bool pending = false;
+    bool e_valid = false;  // e holds Eq. 2.8 of the current messages
 
     std::vector<cudaEvent_t> ev;  // pairs (start, stop) of timed row-pass launches
     double prof_ms = 0.0;
@@ -292,6 +293,16 @@ int reset_messages(hap_ctx* h) {
     CU(cudaStreamSynchronize(h->stream));
     h->iter = 0;
     h->pending = false;
+    h->e_valid = false;
+    return HAP_OK;
+}
+
+// Eq. 2.8 of the current messages into h->e, once per change of the messages.
+int ensure_exemplars(hap_ctx* h) {
+    if (h->e_valid) return HAP_OK;
+    CU(launch_exemplars(h->A, h->R, h->b, h->pending, h->lam, 1.0f - h->lam, h->N, h->ld, h->L, h->e, h->stream));
+    h->launches += 1;
+    h->e_valid = true;
     return HAP_OK;
 }
 
@@ -582,6 +593,7 @@ static int iterate_gauss_seidel(hap_ctx* h, RowPassArgs a, int n) {
         }
         h->pending = false;
         h->iter += 1;
+        h->e_valid = false;
     }
     return HAP_OK;
 }
@@ -633,14 +645,15 @@ int hap_iterate(hap_ctx* h, int n) {
         h->launches += 2;
         h->pending = true;
         h->iter = t;
+        h->e_valid = false;
     }
     return HAP_OK;
 }
 
 int hap_exemplars(hap_ctx* h, int32_t* e, int on_host) {
     if (!h || !e || (on_host != 0 && on_host != 1)) return HAP_EINVAL;
-    CU(launch_exemplars(h->A, h->R, h->b, h->pending, h->lam, 1.0f - h->lam, h->N, h->ld, h->L, h->e, h->stream));
-    h->launches += 1;
+    const int rc = ensure_exemplars(h);
+    if (rc) return rc;
     const size_t bytes = (size_t)h->L * h->N * sizeof(int32_t);
     CU(cudaMemcpyAsync(e, h->e, bytes, on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, h->stream));
     if (on_host) return hap_sync(h);
@@ -649,18 +662,20 @@ int hap_exemplars(hap_ctx* h, int32_t* e, int on_host) {
 
 int hap_net_similarity(hap_ctx* h, double* ns) {
     if (!h || !ns) return HAP_EINVAL;
-    CU(launch_exemplars(h->A, h->R, h->b, h->pending, h->lam, 1.0f - h->lam, h->N, h->ld, h->L, h->e, h->stream));
+    const int rc = ensure_exemplars(h);
+    if (rc) return rc;
     CU(launch_netsim(h->S, h->opt.s_dtype == HAP_S_BF16, h->s_level_stride, h->pref, h->e, h->N, h->ld, h->L, h->ns, h->stream));
-    h->launches += 2;
+    h->launches += 1;
     CU(cudaMemcpyAsync(ns, h->ns, (size_t)h->L * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     return hap_sync(h);
 }
 
 int hap_acceptance(hap_ctx* h, int64_t* consistent, int64_t* exemplars) {
     if (!h) return HAP_EINVAL;
-    CU(launch_exemplars(h->A, h->R, h->b, h->pending, h->lam, 1.0f - h->lam, h->N, h->ld, h->L, h->e, h->stream));
+    const int rc0 = ensure_exemplars(h);
+    if (rc0) return rc0;
     CU(launch_acceptance(h->e, h->N, h->L, h->acc, h->stream));
-    h->launches += 2;
+    h->launches += 1;
     std::vector<long long> host((size_t)2 * h->L);
     CU(cudaMemcpyAsync(host.data(), h->acc, host.size() * sizeof(long long), cudaMemcpyDeviceToHost, h->stream));
     int rc = hap_sync(h);
@@ -708,6 +723,7 @@ int hap_set_state(hap_ctx* h, const float* A, const float* R, const float* vecs,
     h->launches += 1;
     h->iter = iter;
     h->pending = false;
+    h->e_valid = false;
     return HAP_OK;
 }
 
