@@ -94,21 +94,23 @@ def neg_sq_euclidean(X, rows=None) -> np.ndarray:
     return S
 
 
-def neg_sq_euclidean_fixed_order(X, block: int = 512) -> np.ndarray:
+def neg_sq_euclidean_fixed_order(X, block: int = 512, rows=None) -> np.ndarray:
     """The same similarity as ``neg_sq_euclidean`` (§2), with the sum over the
     coordinates taken in order k = 0, 1, ..., d-1, one correctly rounded
     float64 subtraction, multiplication and addition at a time.  Every
     IEEE-754 machine then produces the same bits, so a similarity built on
     one host can be rebuilt bit for bit on another (a library reduction may
-    change its summation order between builds)."""
+    change its summation order between builds).  ``rows`` selects the rows i
+    to compute (all by default)."""
     X = np.asarray(X, dtype=np.float64)
     n, d = X.shape
-    S = np.empty((n, n), dtype=np.float64)
-    for r0 in range(0, n, block):
-        r1 = min(n, r0 + block)
+    rows = np.arange(n) if rows is None else np.asarray(rows)
+    S = np.empty((rows.size, n), dtype=np.float64)
+    for r0 in range(0, rows.size, block):
+        r1 = min(rows.size, r0 + block)
         acc = np.zeros((r1 - r0, n), dtype=np.float64)
         for k in range(d):
-            diff = np.subtract.outer(X[r0:r1, k], X[:, k])
+            diff = np.subtract.outer(X[rows[r0:r1], k], X[:, k])
             acc += diff * diff
         S[r0:r1] = -acc
     return S

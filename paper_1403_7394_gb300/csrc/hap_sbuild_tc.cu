@@ -493,25 +493,28 @@ __global__ void __launch_bounds__(KT_THREADS, 1) knn_tc_kernel(const __grid_cons
             tc_fence_after();
             const int tt = t0 + t < ntiles ? t0 + t : t0 + t - ntiles;
             const bool full_tile = (tt + 1) * KBN <= p.Nc;
-            // 64 columns per round: two TMEM loads in flight, one wait; the
-            // accumulator goes back to the MMA warp as soon as the last
-            // round's values are in registers
+            // 128 columns per round: four TMEM loads in flight, one wait (the
+            // epilogue warp is alone on its sub-partition, so the load
+            // latency is paid once per round); the accumulator goes back to
+            // the MMA warp as soon as the last round's values are in registers
+            constexpr int RC = KBN < 128 ? KBN : 128;  // columns per round
 #pragma unroll 1
-            for (int hh = 0; hh < KBN / 64; ++hh) {
-                uint32_t r[2][32];
+            for (int hh = 0; hh < KBN / RC; ++hh) {
+                uint32_t r[RC / 32][32];
                 __syncwarp();
-                const uint32_t ta = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(buf * KBN + 64 * hh);
-                tmem_ld_32x32b_x32_nowait(ta, r[0]);
-                tmem_ld_32x32b_x32_nowait(ta + 32, r[1]);
+                const uint32_t ta = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(buf * KBN + RC * hh);
+#pragma unroll
+                for (int b = 0; b < RC / 32; ++b) tmem_ld_32x32b_x32_nowait(ta + 32 * b, r[b]);
                 tmem_wait_ld(r[0]);
-                tmem_tie(r[1]);
-                if (hh == KBN / 64 - 1) {
+#pragma unroll
+                for (int b = 1; b < RC / 32; ++b) tmem_tie(r[b]);
+                if (hh == KBN / RC - 1) {
                     tc_fence_before();
                     mbar_arrive(acc_empty + 8 * buf);
                 }
 #pragma unroll
-                for (int b = 0; b < 2; ++b) {
-                    const int jb = tt * KBN + 64 * hh + 32 * b;
+                for (int b = 0; b < RC / 32; ++b) {
+                    const int jb = tt * KBN + RC * hh + 32 * b;
                     if (max32(r[b]) > vthr) {
                         // PEND columns at a time, each part buffered then
                         // pushed (a later part sees the tightened threshold)

@@ -21,14 +21,17 @@ Inputs, rebuilt bit for bit by the GPU test on any IEEE-754 machine:
 Stored per checkpoint t: the exemplars of Eq. 2.8 (int16), 4096 sampled
 message entries of alpha and rho (512 of them on the diagonal), the largest
 |alpha| and |rho| over the whole tensors (the scale of the message error),
-and c, tau, phi of 512 sampled points; at t = 300 also the full c, tau, phi,
-the net similarity and each row's argmax margin (best minus second best
-alpha + rho), which shows how far rounding would have to move a message to
-change an exemplar.
+and c, tau, phi of 512 sampled points; at t = 300 also the net similarity and,
+per level, the smallest and the 1 % quantile of the rows' argmax margins
+(best minus second best alpha + rho), which show how far rounding would have
+to move a message to change an exemplar.
 
     python tests/golden/make_config1_free_running.py [paper|fixed ...]
+    python tests/golden/make_config1_free_running.py --trim FILE.npz ...
 
-Takes about 30 minutes and 16 GB per mode on one host core.
+Takes about an hour and 16 GB per mode on one host core.  --trim rewrites a
+file written by an earlier version of this script (which also kept the full
+final c, tau, phi and every row's margin) in the current format.
 """
 from __future__ import annotations
 
@@ -69,6 +72,23 @@ def sample_indices():
     j[n_off:] = i[n_off:]
     pts = np.sort(rng.choice(N, N_POINTS, replace=False))
     return lv.astype(np.int32), i.astype(np.int32), j.astype(np.int32), pts.astype(np.int32)
+
+
+def margin_summary(margin):
+    """Per level: the smallest and the 1 % quantile of the argmax margins."""
+    return {"margin_min": margin.min(axis=1), "margin_q01": np.quantile(margin, 0.01, axis=1)}
+
+
+def trim(path):
+    """Rewrites a file of an earlier version of this script in the current
+    format: the same stored values, without the full final c, tau, phi and
+    with the margins summarised."""
+    z = dict(np.load(path))
+    for k in ("c_final", "tau_final", "phi_final"):
+        z.pop(k, None)
+    if "margin" in z:
+        z.update(margin_summary(z.pop("margin")))
+    np.savez_compressed(path, **z)
 
 
 def main(modes):
@@ -112,11 +132,14 @@ def main(modes):
             A=np.stack(rec["A"]), R=np.stack(rec["R"]),
             scale_A=np.array(rec["scale_A"]), scale_R=np.array(rec["scale_R"]),
             c=np.stack(rec["c"]), tau=np.stack(rec["tau"]), phi=np.stack(rec["phi"]),
-            c_final=st.c, tau_final=st.tau, phi_final=st.phi, net_similarity=ns, margin=margin,
-            oracle_seconds=time.time() - t0)
+            net_similarity=ns, **margin_summary(margin), oracle_seconds=time.time() - t0)
         print(f"{mode}: wrote {out} ({os.path.getsize(out)} bytes, {time.time() - t0:.0f} s); "
               f"NS {ns.tolist()}", flush=True)
 
 
 if __name__ == "__main__":
-    main(sys.argv[1:] or ["paper", "fixed"])
+    if sys.argv[1:2] == ["--trim"]:
+        for f in sys.argv[2:]:
+            trim(f)
+    else:
+        main(sys.argv[1:] or ["paper", "fixed"])
