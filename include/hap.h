@@ -195,10 +195,14 @@ int hap_set_cluster_preferences(hap_ctx* ctx, const float* c0);
 int hap_set_similarity(hap_ctx* ctx, int level, const void* S, int64_t ld, int dtype);
 
 /* Builds s_ij = -||x_i - x_j||^2 (§2) on the GPU from X and resets the
- * messages.  X: device FP32 [N][d] row-major.  mode: HAP_SBUILD_*.  The result
- * is used at every level.  The tensor-core modes pack their BF16 operands into
- * the message storage, which the workspace sizes for d <= 256; beyond that
- * they may return HAP_EUNSUPPORTED (HAP_SBUILD_F32 has no limit). */
+ * messages.  X: FP32 [N][d] row-major, device memory, or host memory (pinned
+ * or pageable): the call then first copies it, on the bound stream, into the
+ * message storage it is about to reset, so a host buffer costs no device
+ * allocation.  mode: HAP_SBUILD_*.  The result is used at every level.  The
+ * tensor-core modes pack their BF16 operands into the message storage, which
+ * the workspace sizes for d <= 256; beyond that they may return
+ * HAP_EUNSUPPORTED (HAP_SBUILD_F32 has no limit), and so may a host X that does
+ * not fit beside the operands (not at N >= 1024).  Synchronising. */
 int hap_build_similarity(hap_ctx* ctx, const float* X, int64_t d, int mode);
 
 /* Copies the similarity the iterations use at `level` (0..L-1) into S: device

@@ -492,8 +492,25 @@ int hap_set_similarity(hap_ctx* h, int level, const void* S, int64_t ld, int dty
 
 int hap_build_similarity(hap_ctx* h, const float* X, int64_t d, int mode) {
     if (!h || !X || d < 1) return HAP_EINVAL;
+    if (mode != HAP_SBUILD_F32 && mode != HAP_SBUILD_BF16 && mode != HAP_SBUILD_BF16_SPLIT) return HAP_EINVAL;
     const int s_bf16 = h->opt.s_dtype == HAP_S_BF16;
     const size_t es = s_bf16 ? 2 : 4;
+    // Points in host memory are first copied into the end of the alpha and rho
+    // storage (the build resets the messages anyway), behind the operand
+    // scratch of the tensor-core modes.
+    cudaPointerAttributes pa{};
+    const cudaError_t pq = cudaPointerGetAttributes(&pa, X);
+    if (pq != cudaSuccess) cudaGetLastError();
+    if (pq != cudaSuccess || pa.type == cudaMemoryTypeHost || pa.type == cudaMemoryTypeUnregistered) {
+        const size_t xbytes = (size_t)h->N * d * sizeof(float);
+        const size_t ops = mode == HAP_SBUILD_F32 ? 0 : sbuild_tc_scratch_bytes(h->N, d, mode == HAP_SBUILD_BF16_SPLIT);
+        char* lo = reinterpret_cast<char*>(h->A);
+        char* end = static_cast<char*>(h->S);
+        if ((size_t)(end - lo) < ops + xbytes + 1024) return HAP_EUNSUPPORTED;
+        float* stage = reinterpret_cast<float*>(((uintptr_t)(end - xbytes)) & ~(uintptr_t)255);
+        CU(cudaMemcpyAsync(stage, X, xbytes, cudaMemcpyHostToDevice, h->stream));
+        X = stage;
+    }
     if (mode == HAP_SBUILD_F32) {
         CU(launch_sbuild_f32(X, h->N, d, h->S, s_bf16, h->ld, h->stream));
         h->launches += 1;

@@ -227,8 +227,11 @@ class HAP:
         check(lib.hap_set_similarity(self._h, int(level), _ptr(S), S.stride(0), dt), "hap_set_similarity")
 
     def build_similarity(self, X: torch.Tensor, mode: str = "bf16_split"):
-        if X.device != self.device or X.dtype != torch.float32 or X.dim() != 2 or X.shape[0] != self.N:
-            raise ValueError("X must be an (N, d) float32 tensor on the context's device")
+        """X: (N, d) float32 on the context's device, or on the host (the
+        library copies it in on its stream)."""
+        if X.device not in (self.device, torch.device("cpu")) or X.dtype != torch.float32 or X.dim() != 2 or \
+                X.shape[0] != self.N:
+            raise ValueError("X must be an (N, d) float32 tensor on the context's device or on the host")
         X = X.contiguous()
         check(lib.hap_build_similarity(self._h, _ptr(X), X.shape[1], SBUILD[mode]), "hap_build_similarity")
 

@@ -539,3 +539,22 @@ def test_tmem_and_shared_memory_sums_agree_bitwise():
     for shape, g in out[1:]:
         for f in ("A", "R", "c", "tau", "phi"):
             assert torch.equal(out[0][1][f], g[f]), (shape, f)
+
+
+@pytest.mark.parametrize("mode", ["f32", "bf16_split"])
+def test_similarity_build_from_host_points(mode):
+    """Points in pinned or pageable host memory are copied in by the library
+    on its stream; the similarity is the one built from the same points on
+    the device, bit for bit."""
+    hap = hap_mod()
+    N, L, d = 3000, 2, 48
+    X = np.random.default_rng(2).normal(size=(N, d)).astype(np.float32)
+    ref = hap.HAP(N, L, prefs=[-5.0, -10.0], device=DEV)
+    ref.build_similarity(torch.from_numpy(X).to(DEV), mode=mode)
+    want = ref.get_similarity(0)
+    for host in (torch.from_numpy(X), torch.from_numpy(X).pin_memory()):
+        ctx = hap.HAP(N, L, prefs=[-5.0, -10.0], device=DEV)
+        ctx.build_similarity(host, mode=mode)
+        assert torch.equal(ctx.get_similarity(0), want)
+        ctx.close()
+    ref.close()
