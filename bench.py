@@ -862,7 +862,7 @@ def kernel_hash() -> str:
     """Digest of the row-pass sources (kernel and the device helpers it uses)."""
     import hashlib
     h = hashlib.sha256()
-    for f in ("hap_rowpass.cu", "hap_common.cuh"):
+    for f in ("hap_rowpass.cu", "hap_rowpass_kernel.cuh", "hap_common.cuh"):
         h.update(open(os.path.join(ROOT, "paper_1403_7394_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 

@@ -54,6 +54,8 @@ struct LaunchShape {
 
 // Kernel launchers (return a cudaError_t).
 cudaError_t launch_rowpass(const RowPassArgs& a, const LaunchShape& sh, int s_bf16, cudaStream_t st);
+// the same with the debug_bounds index checks compiled in (hap_rowpass_dbg.cu)
+cudaError_t launch_rowpass_checked(const RowPassArgs& a, const LaunchShape& sh, int s_bf16, cudaStream_t st);
 cudaError_t rowpass_max_clusters(const LaunchShape& sh, int L, int s_bf16, int* max_clusters);
 cudaError_t rowpass_blocks_per_sm(const LaunchShape& sh, int L, int s_bf16, int* blocks);
 size_t rowpass_smem_bytes(const LaunchShape& sh, int L, int s_bf16);
