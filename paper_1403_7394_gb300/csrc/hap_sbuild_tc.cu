@@ -8,7 +8,10 @@
 // over K' = 3d of A_i = [hi_i, hi_i, lo_i] and B_j = [hi_j, lo_j, hi_j]
 // (the dropped lo.lo term is ~2^-16 of the product).
 //
-// Kernel layout: one CTA (4 warps) per 128 x 128 output tile.  Thread 0
+// Two kernels.  The symmetric persistent one (below, used whenever its
+// operands fit in shared memory) contracts only the tiles on and above the
+// diagonal and writes each tile twice.  The other, used for wider points:
+// one CTA (4 warps) per 128 x 128 output tile.  Thread 0
 // streams 128 x 64 BF16 K-chunks of A and B with TMA (128-byte swizzle) into
 // a shared-memory ring and issues the tcgen05.mma instructions (M = N = 128,
 // K = 16) accumulating in 128 TMEM columns; tcgen05.commit frees a ring stage
@@ -240,6 +243,358 @@ __global__ void __launch_bounds__(128, 1) sbuild_tc_kernel(const __grid_constant
     tc_fence_before();
     __syncthreads();
     if (warp == 0) tmem_dealloc(tmem, kTmemCols);
+}
+
+// ---- symmetric persistent build -----------------------------------------------
+// s is symmetric, so of the 128-row strips r and 256-column blocks J of the
+// padded N x N matrix only the tiles with 256 J + 255 >= 128 r are
+// contracted (M = 128, N = 256 per tcgen05.mma), and each 128 x 128 half
+// above the diagonal is written twice, as itself and transposed; a half on
+// the diagonal writes its upper triangle both ways (so S is symmetric bit for
+// bit) and a half below it (the first half of the first block of an odd
+// strip) is skipped.  That is about half the tensor work of the full tiling
+// for the same N^2 writes, and the 256-column tiles read 25 % fewer operand
+// bytes per output than 128-column ones.
+// Tile order: groups of kSyGroup strips, and within a group the blocks J in
+// order, each with the group's strips that need it; the persistent CTAs (one
+// per SM) take the tiles of that list round-robin.  At any moment the GPU
+// then works on a few A strips and B blocks, which stay in L2 (loads hinted
+// evict-last, the similarity stores evict-first) while N^2 results stream
+// through it; with a contiguous range of tiles per CTA the operands were
+// re-read from memory about 16 times.
+//   warp 4 (producer): TMA loads of the A and B K-chunks into a ring.
+//   warp 5 (MMA issuer): tcgen05.mma into one of two TMEM accumulators
+//     (256 columns each), so one tile's products overlap the previous tile's
+//     epilogue.
+//   warps 0-3 (epilogue; thread = tile row = TMEM lane): read a finished
+//     accumulator, hand it back, and write each 128 x 32 column block twice
+//     by TMA tensor stores from shared-memory boxes that the four warps fill
+//     together (the stores clip at N): as itself (128 rows x 32 columns,
+//     staged with the 128-byte (FP32) or 64-byte (BF16) swizzle, so the
+//     row-per-lane writes hit every bank) and transposed (32 rows x 128
+//     columns, staged row = column, where the 32 lanes of a warp write one
+//     contiguous piece).  Plain stores from registers, and 32 x 32 boxes
+//     per warp, measured slower.  The warps meet at named barriers, so every
+//     decision to stop is taken by all 128 epilogue threads together.
+constexpr int SY_THREADS = 192;  // 4 epilogue warps, 1 producer warp, 1 MMA warp
+constexpr int SY_BN = 256;       // tile columns
+constexpr int SY_RING_MAX = 8;
+constexpr int kSyGroup = 16;     // strips per group of the tile order
+constexpr uint32_t SY_TMEM_COLS = 2 * SY_BN;
+constexpr uint32_t SY_ACHUNK = BM * BK * 2;            // A K-chunk, 16 KB
+constexpr uint32_t SY_BCHUNK = SY_BN * BK * 2;         // B K-chunk, 32 KB
+constexpr uint32_t SY_BOX = 128 * 32 * 4;              // one staged 128 x 32 box (FP32 size)
+constexpr uint32_t SY_STG = 4 * SY_BOX;                // two buffers x {direct, transposed}
+constexpr uint32_t kSyIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(SY_BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+
+// Dynamic shared memory: alignment slack | ring stages [B | A] | staging
+// [2][2 boxes].  At least 116 KB: one CTA per SM, so its 512-column TMEM
+// allocation never waits.
+__host__ __device__ inline size_t sbuild_sym_smem_bytes(int ring) {
+    const size_t b = 1024 + (size_t)ring * (SY_BCHUNK + SY_ACHUNK) + (size_t)SY_STG;
+    return b < 116 * 1024 ? 116 * 1024 : b;
+}
+
+// Tiles of the symmetric build: strip r needs the blocks J = r/2 .. T2-1.
+__host__ __device__ inline int64_t sym_tile_count(int T) {
+    const int T2 = (T + 1) / 2;
+    int64_t n = 0;
+    for (int r = 0; r < T; ++r) n += T2 - r / 2;
+    return n;
+}
+// Group g (strips r0 .. r0+n-1, r0 = kSyGroup g): block J (>= r0 / 2) is
+// needed by the first c(J) = min(n, 2J + 2 - r0) strips; jf is the first
+// block all n need, and sp(J) the tiles of the blocks before J (J <= jf).
+struct SymGroup {
+    int r0, n, J0, jf;
+    __host__ __device__ SymGroup(int g, int T) {
+        r0 = g * kSyGroup;
+        n = (T - r0 < kSyGroup ? T - r0 : kSyGroup);
+        J0 = r0 / 2;
+        jf = (n + r0 - 1) / 2;  // ceil((n + r0 - 2) / 2)
+        if (jf < J0) jf = J0;
+    }
+    __host__ __device__ int count(int J) const { return 2 * J + 2 - r0 < n ? 2 * J + 2 - r0 : n; }
+    __host__ __device__ int64_t sp(int J) const { return (int64_t)(J - J0) * (2 - r0) + (int64_t)(J - J0) * (J0 + J - 1); }
+    __host__ __device__ int64_t total(int T2) const { return sp(jf) + (int64_t)(T2 - jf) * n; }
+    __host__ __device__ int64_t offset(int J) const { return J <= jf ? sp(J) : sp(jf) + (int64_t)(J - jf) * n; }
+};
+// The tile list (r << 16 | J) in that order: block g = group, thread J.
+__global__ void sym_order_kernel(int T, int32_t* __restrict__ tiles) {
+    const int g = blockIdx.x, J = threadIdx.x, T2 = (T + 1) / 2;
+    const SymGroup sg(g, T);
+    if (J < sg.J0 || J >= T2) return;
+    int64_t base = 0;
+    for (int q = 0; q < g; ++q) base += SymGroup(q, T).total(T2);
+    const int64_t o = base + sg.offset(J);
+    const int c = sg.count(J);
+    for (int i = 0; i < c; ++i) tiles[o + i] = ((sg.r0 + i) << 16) | J;
+}
+
+template <typename OT>
+HAP_DEV void store1(OT* dst, float v);
+template <>
+HAP_DEV void store1<float>(float* dst, float v) { *dst = v; }
+template <>
+HAP_DEV void store1<__nv_bfloat16>(__nv_bfloat16* dst, float v) { *dst = __float2bfloat16_rn(v); }
+
+// L2 eviction priorities: the operands (tens of MB, read by every CTA) stay
+// in L2 while the N^2 similarities stream through it to memory.
+HAP_DEV uint64_t l2_evict_last() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+HAP_DEV uint64_t l2_evict_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+// TMA tile load with an L2 cache policy.
+HAP_DEV void tma_load_2d_hint(uint32_t dst, const CUtensorMap* map, int c0, int c1, uint32_t bar, uint64_t pol) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1, {%2, %3}], [%4], %5;"
+        :: "r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(bar), "l"(pol) : "memory");
+}
+// TMA tensor store of a shared-memory box (bulk-group completion) with an L2
+// cache policy.
+HAP_DEV void tma_store_2d(const CUtensorMap* map, uint32_t src, int c0, int c1, uint64_t pol) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group.L2::cache_hint [%0, {%1, %2}], [%3], %4;"
+                 :: "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(src), "l"(pol) : "memory");
+}
+HAP_DEV void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// at most one committed group still reading shared memory
+HAP_DEV void bulk_wait_read_1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+// every committed group complete
+HAP_DEV void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+HAP_DEV void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Named barrier of the 128 epilogue threads; the _and form returns whether
+// every one of them passed `pred`.
+HAP_DEV void epi_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+HAP_DEV bool epi_all(bool pred) {
+    uint32_t r;
+    asm volatile("{\n\t.reg .pred p, q;\n\t"
+                 "setp.ne.u32 p, %1, 0;\n\t"
+                 "bar.red.and.pred q, 1, 128, p;\n\t"
+                 "selp.u32 %0, 1, 0, q;\n\t}"
+                 : "=r"(r) : "r"((uint32_t)pred) : "memory");
+    return r != 0;
+}
+
+// Thread `r`'s 32 values (row r of a 128 x 32 block) into the swizzled box.
+template <typename OT>
+HAP_DEV void stage_direct(unsigned char* box, int r, const float (&v)[32]);
+template <>
+HAP_DEV void stage_direct<float>(unsigned char* box, int r, const float (&v)[32]) {
+    // 128-byte rows, 16-byte chunk k stored at chunk k ^ (r % 8)
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+        *reinterpret_cast<float4*>(box + r * 128 + ((k ^ (r & 7)) << 4)) =
+            make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+}
+template <>
+HAP_DEV void stage_direct<__nv_bfloat16>(unsigned char* box, int r, const float (&v)[32]) {
+    // 64-byte rows, 16-byte chunk k stored at chunk k ^ ((r / 2) % 4)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        uint4 u;
+        __nv_bfloat162 p0 = __floats2bfloat162_rn(v[8 * k + 0], v[8 * k + 1]);
+        __nv_bfloat162 p1 = __floats2bfloat162_rn(v[8 * k + 2], v[8 * k + 3]);
+        __nv_bfloat162 p2 = __floats2bfloat162_rn(v[8 * k + 4], v[8 * k + 5]);
+        __nv_bfloat162 p3 = __floats2bfloat162_rn(v[8 * k + 6], v[8 * k + 7]);
+        u.x = *reinterpret_cast<uint32_t*>(&p0);
+        u.y = *reinterpret_cast<uint32_t*>(&p1);
+        u.z = *reinterpret_cast<uint32_t*>(&p2);
+        u.w = *reinterpret_cast<uint32_t*>(&p3);
+        *reinterpret_cast<uint4*>(box + r * 64 + ((k ^ ((r >> 1) & 3)) << 4)) = u;
+    }
+}
+
+template <typename OT>
+__global__ void __launch_bounds__(SY_THREADS, 1) sbuild_sym_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                                  const __grid_constant__ CUtensorMap tmB,
+                                                                  const __grid_constant__ CUtensorMap tmSd,
+                                                                  const __grid_constant__ CUtensorMap tmSt,
+                                                                  const float* __restrict__ norms,
+                                                                  const int32_t* __restrict__ tiles, OT* __restrict__ S,
+                                                                  int N, int64_t ld, int kchunks, int ring, int T,
+                                                                  int64_t total, unsigned* status) {
+    extern __shared__ unsigned char smem_raw[];
+    const uint32_t raw = smem_addr(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    const uint32_t stage_bytes = SY_BCHUNK + SY_ACHUNK;
+    const uint32_t sR = base;                               // ring: [B | A]
+    const uint32_t sS = sR + (uint32_t)ring * stage_bytes;  // staging
+    unsigned char* stg_all = smem_raw + (sS - raw);
+    // full[R], empty[R], acc_full[2], acc_empty[2], mma_done
+    __shared__ uint64_t bars[2 * SY_RING_MAX + 5];
+    __shared__ uint32_t tmem_slot;
+    __shared__ int s_abort;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t r_full = smem_addr(&bars[0]), r_empty = r_full + 8 * SY_RING_MAX;
+    const uint32_t acc_full = r_empty + 8 * SY_RING_MAX, acc_empty = acc_full + 16, mma_done = acc_empty + 16;
+    const int R = ring;
+    const int64_t t_first = blockIdx.x, t_step = gridDim.x;
+
+    if (tid == 0) {
+        for (int q = 0; q < R; ++q) {
+            mbar_init(r_full + 8 * q, 1);
+            mbar_init(r_empty + 8 * q, 1);
+        }
+        for (int q = 0; q < 2; ++q) {
+            mbar_init(acc_full + 8 * q, 1);
+            mbar_init(acc_empty + 8 * q, BM);
+        }
+        mbar_init(mma_done, 1);
+        s_abort = 0;
+        fence_mbarrier_init();
+    }
+    if (warp == 0) tmem_alloc(smem_addr(&tmem_slot), SY_TMEM_COLS);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+    volatile int* abort_flag = &s_abort;
+
+    if (warp == 4) {
+        if (lane == 0) {  // ---- producer
+            const uint64_t pol = l2_evict_last();
+            int g = 0;
+            bool ok = true;
+            for (int64_t t = t_first; t < total && ok && !*abort_flag; t += t_step) {
+                const int tr = __ldg(tiles + t) >> 16, tJ = __ldg(tiles + t) & 0xffff;
+                for (int kc = 0; kc < kchunks; ++kc, ++g) {
+                    const int st = g % R;
+                    if (g >= R && !(ok = mbar_wait(r_empty + 8 * st, (uint32_t)((g / R - 1) & 1), status))) break;
+                    const uint32_t dst = sR + (uint32_t)st * stage_bytes;
+                    mbar_arrive_expect_tx(r_full + 8 * st, stage_bytes);
+                    tma_load_2d_hint(dst, &tmB, kc * BK, tJ * SY_BN, r_full + 8 * st, pol);
+                    tma_load_2d_hint(dst + SY_BCHUNK, &tmA, kc * BK, tr * BM, r_full + 8 * st, pol);
+                }
+            }
+            if (!ok) *abort_flag = 1;
+            // no copy may land in shared memory after the CTA has left: wait for
+            // every issued copy (each is the last on its barrier)
+            for (int q = g > R ? g - R : 0; q < g; ++q) mbar_wait(r_full + 8 * (q % R), (uint32_t)((q / R) & 1), status);
+        }
+    } else if (warp == 5) {
+        if (lane == 0) {  // ---- MMA issuer
+            int g = 0, tl = 0;
+            bool ok = true;
+            for (int64_t t = t_first; t < total && ok && !*abort_flag; t += t_step, ++tl) {
+                const int buf = tl & 1;
+                if (tl >= 2 && !(ok = mbar_wait(acc_empty + 8 * buf, (uint32_t)((tl / 2 - 1) & 1), status))) break;
+                tc_fence_after();
+                for (int kc = 0; kc < kchunks; ++kc, ++g) {
+                    const int st = g % R;
+                    if (!(ok = mbar_wait(r_full + 8 * st, (uint32_t)((g / R) & 1), status))) break;
+                    tc_fence_after();
+                    const uint32_t stg = sR + (uint32_t)st * stage_bytes;
+                    const uint32_t a_s = stg + SY_BCHUNK;
+#pragma unroll
+                    for (int kk = 0; kk < BK / 16; ++kk)
+                        umma_bf16(tmem + (uint32_t)(buf * SY_BN), desc_kmajor_sw128(a_s + 32 * kk),
+                                  desc_kmajor_sw128(stg + 32 * kk), kSyIdesc, (kc > 0 || kk > 0) ? 1u : 0u);
+                    umma_commit(r_empty + 8 * st);
+                }
+                if (!ok) break;
+                umma_commit(acc_full + 8 * buf);
+            }
+            if (!ok) *abort_flag = 1;
+            // every issued MMA completes before tensor memory is freed
+            umma_commit(mma_done);
+            mbar_wait(mma_done, 0u, status);
+        }
+    } else {  // ---- epilogue: warps 0-3, thread = tile row = TMEM lane
+        const uint64_t pol = l2_evict_first();
+        int tl = 0, ch = 0;
+        for (int64_t t = t_first; t < total; t += t_step, ++tl) {
+            // one decision for all 128 epilogue threads (they meet at named
+            // barriers below, and the TMEM loads are warp-collective)
+            const int buf = tl & 1;
+            const bool got = *abort_flag == 0 && mbar_wait(acc_full + 8 * buf, (uint32_t)((tl >> 1) & 1), status);
+            if (!epi_all(got)) {
+                *abort_flag = 1;
+                break;
+            }
+            tc_fence_after();
+            const int wr = __ldg(tiles + t) >> 16, wJ = __ldg(tiles + t) & 0xffff;
+            const int r0 = wr * BM + 32 * warp, row = r0 + lane;
+            const float ni = row < N ? __ldg(norms + row) : 0.f;
+#pragma unroll 1
+            for (int h = 0; h < 2; ++h) {
+                const int cb = 2 * wJ + h;  // 128-column block of this half
+                // the whole half row into registers (four loads, one wait); after
+                // the second half the accumulator goes back to the MMA warp
+                uint32_t rg[4][32];
+                const bool need = cb >= wr && cb < T;
+                if (need) {
+                    __syncwarp();
+                    const uint32_t ta = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(buf * SY_BN + 128 * h);
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) tmem_ld_32x32b_x32_nowait(ta + 32 * b, rg[b]);
+                    tmem_wait_ld(rg[0]);
+#pragma unroll
+                    for (int b = 1; b < 4; ++b) tmem_tie(rg[b]);
+                }
+                if (h == 1) {
+                    tc_fence_before();
+                    mbar_arrive(acc_empty + 8 * buf);
+                }
+                if (!need) continue;
+                const bool diag = cb == wr;
+#pragma unroll
+                for (int cc = 0; cc < 4; ++cc) {
+                    const int c0 = cb * 128 + 32 * cc;
+                    float v[32];
+#pragma unroll
+                    for (int q = 0; q < 32; q += 4) {
+                        const float4 nj = __ldg(reinterpret_cast<const float4*>(norms + c0 + q));
+                        v[q + 0] = __fsub_rn(__fsub_rn(2.f * __uint_as_float(rg[cc][q + 0]), ni), nj.x);
+                        v[q + 1] = __fsub_rn(__fsub_rn(2.f * __uint_as_float(rg[cc][q + 1]), ni), nj.y);
+                        v[q + 2] = __fsub_rn(__fsub_rn(2.f * __uint_as_float(rg[cc][q + 2]), ni), nj.z);
+                        v[q + 3] = __fsub_rn(__fsub_rn(2.f * __uint_as_float(rg[cc][q + 3]), ni), nj.w);
+                    }
+                    const int m0 = wr * BM;
+                    if (m0 >= N || c0 >= N) continue;  // no element of this block inside S (uniform)
+                    if (!diag) {
+                        unsigned char* bd = stg_all + (ch & 1) * (2 * SY_BOX);
+                        OT* bt = reinterpret_cast<OT*>(bd + SY_BOX);
+                        // the stores issued from these boxes two blocks ago have read them
+                        if (tid == 0) bulk_wait_read_1();
+                        epi_sync();
+                        stage_direct<OT>(bd, tid, v);
+#pragma unroll
+                        for (int q = 0; q < 32; ++q) store1<OT>(bt + q * BM + tid, v[q]);
+                        fence_proxy_async_smem();
+                        epi_sync();
+                        if (tid == 0) {
+                            tma_store_2d(&tmSd, smem_addr(bd), c0, m0, pol);  // rows m0.., columns c0..
+                            tma_store_2d(&tmSt, smem_addr(bt), m0, c0, pol);  // rows c0.., columns m0..
+                            bulk_commit();
+                        }
+                        ++ch;
+                    } else if (row < N) {
+                        // diagonal block: S[row][j] for j >= row and S[j][row] for j > row
+#pragma unroll
+                        for (int q = 0; q < 32; ++q) {
+                            const int j = c0 + q;
+                            if (j < N && j >= row) store1<OT>(S + (int64_t)row * ld + j, v[q]);
+                            if (j < N && j > row) store1<OT>(S + (int64_t)j * ld + row, v[q]);
+                        }
+                    }
+                }
+            }
+        }
+        // the last stores must have read shared memory (and completed) before
+        // the CTA leaves
+        if (tid == 0) bulk_wait_all();
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, SY_TMEM_COLS);
 }
 
 // Operands of the contraction (zero-padded to [npad][kpad] BF16; A or B may
@@ -722,9 +1077,28 @@ bool encode_operand_map(CUtensorMap* map, void* ptr, int64_t rows, int64_t kpad,
            CUDA_SUCCESS;
 }
 
+// Tensor map of S (N x N, row stride ld) for the build's TMA stores: direct
+// boxes of 128 rows x 32 columns staged with the 128-byte (FP32 rows) or
+// 64-byte (BF16) swizzle, transposed boxes of 32 rows x 128 columns staged
+// plain.  Stores clip at N.
+bool encode_s_map(CUtensorMap* map, void* S, int64_t N, int64_t ld, int s_bf16, bool swizzled) {
+    auto enc = get_encode();
+    if (!enc) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)N, (cuuint64_t)N};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * (s_bf16 ? 2 : 4)};
+    const cuuint32_t box[2] = {swizzled ? 32u : 128u, swizzled ? 128u : 32u};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUtensorMapSwizzle sw = !swizzled ? CU_TENSOR_MAP_SWIZZLE_NONE
+                                  : s_bf16  ? CU_TENSOR_MAP_SWIZZLE_64B
+                                            : CU_TENSOR_MAP_SWIZZLE_128B;
+    return enc(map, s_bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, S, dims, strides,
+               box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 struct Scratch {
     int64_t npad, kpad;
-    size_t a_off, b_off, n_off, total;
+    size_t a_off, b_off, n_off, t_off, total;  // operands, norms, tile list of the symmetric build
 };
 Scratch scratch_layout(int64_t N, int64_t d, int split) {
     Scratch s;
@@ -734,7 +1108,8 @@ Scratch scratch_layout(int64_t N, int64_t d, int split) {
     s.a_off = 0;
     s.b_off = (op + 1023) / 1024 * 1024;
     s.n_off = s.b_off + (op + 1023) / 1024 * 1024;
-    s.total = s.n_off + (size_t)s.npad * 4 + 2048;
+    s.t_off = (s.n_off + (size_t)s.npad * 4 + 255) / 256 * 256;
+    s.total = s.t_off + (size_t)sym_tile_count((int)(s.npad / BM)) * 4 + 2048;
     return s;
 }
 
@@ -761,6 +1136,44 @@ cudaError_t launch_sbuild_tc(const float* X, int64_t N, int64_t d, int split, vo
     if (!encode_operand_map(&mA, A, sl.npad, sl.kpad) || !encode_operand_map(&mB, B, sl.npad, sl.kpad))
         return cudaErrorNotSupported;
     const int kchunks = (int)(sl.kpad / BK);
+    // the symmetric persistent kernel where a ring of at least two stages fits
+    int dev = 0, smem_optin = 0, n_sm = 0;
+    err = cudaGetDevice(&dev);
+    if (err == cudaSuccess) err = cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (err == cudaSuccess) err = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    if (err != cudaSuccess) return err;
+    const size_t room = (size_t)smem_optin - 1024;  // the kernel's static shared memory
+    int ring = SY_RING_MAX;
+    while (ring >= 2 && sbuild_sym_smem_bytes(ring) > room) --ring;
+    CUtensorMap mBw, mSd, mSt;
+    if (ring >= 2 && encode_operand_map(&mBw, B, sl.npad, sl.kpad, SY_BN) && encode_s_map(&mSd, S, N, ld, s_bf16, true) &&
+        encode_s_map(&mSt, S, N, ld, s_bf16, false)) {
+        const int T = (int)(sl.npad / BM), T2 = (T + 1) / 2;
+        const int64_t tiles = sym_tile_count(T);
+        int32_t* tlist = reinterpret_cast<int32_t*>(base + sl.t_off);
+        sym_order_kernel<<<(unsigned)((T + kSyGroup - 1) / kSyGroup), (unsigned)T2, 0, st>>>(T, tlist);
+        err = cudaGetLastError();
+        if (err != cudaSuccess) return err;
+        *kernels = 2;
+        const unsigned grid = (unsigned)(tiles < n_sm ? tiles : n_sm);
+        const size_t smem = sbuild_sym_smem_bytes(ring);
+        if (s_bf16) {
+            auto k = sbuild_sym_kernel<__nv_bfloat16>;
+            err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (err != cudaSuccess) return err;
+            k<<<grid, SY_THREADS, smem, st>>>(mA, mBw, mSd, mSt, norms, tlist, static_cast<__nv_bfloat16*>(S), (int)N, ld,
+                                               kchunks, ring, T, tiles, status);
+        } else {
+            auto k = sbuild_sym_kernel<float>;
+            err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (err != cudaSuccess) return err;
+            k<<<grid, SY_THREADS, smem, st>>>(mA, mBw, mSd, mSt, norms, tlist, static_cast<float*>(S), (int)N, ld, kchunks,
+                                               ring, T, tiles, status);
+        }
+        err = cudaGetLastError();
+        if (err == cudaSuccess) *kernels = 3;
+        return err;
+    }
     const size_t smem = (size_t)kRing * kChunkBytes + 1024;
     const dim3 grid((unsigned)(sl.npad / BN), (unsigned)(sl.npad / BM));
     if (s_bf16) {
