@@ -8,16 +8,9 @@
 // over K' = 3d of A_i = [hi_i, hi_i, lo_i] and B_j = [hi_j, lo_j, hi_j]
 // (the dropped lo.lo term is ~2^-16 of the product).
 //
-// Two kernels.  The symmetric persistent one (below, used whenever its
-// operands fit in shared memory) contracts only the tiles on and above the
-// diagonal and writes each tile twice.  The other, used for wider points:
-// one CTA (4 warps) per 128 x 128 output tile.  Thread 0
-// streams 128 x 64 BF16 K-chunks of A and B with TMA (128-byte swizzle) into
-// a shared-memory ring and issues the tcgen05.mma instructions (M = N = 128,
-// K = 16) accumulating in 128 TMEM columns; tcgen05.commit frees a ring stage
-// once the MMAs reading it finish.  The 4 warps then read their 32 TMEM
-// lanes (rows) with tcgen05.ld and write s to global memory.  The kernel is
-// bound by the N^2 output writes for d <= 192.
+// The build kernel (sbuild_sym_kernel, below) contracts only the tiles on and
+// above the diagonal and writes each tile twice; the same file holds the
+// tensor-core first pass of the exact kNN.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -29,10 +22,7 @@
 namespace hap {
 namespace {
 
-constexpr int BM = 128, BN = 128, BK = 64;  // tile and K-chunk (64 BF16 = 128 bytes)
-constexpr int kRing = 2;                     // K-chunk stages in shared memory (3 CTAs per SM)
-constexpr uint32_t kChunkBytes = (BM + BN) * BK * 2;
-constexpr uint32_t kTmemCols = 128;
+constexpr int BM = 128, BK = 64;  // operand rows per tile and K-chunk (64 BF16 = 128 bytes)
 
 // ---- tcgen05 / TMA PTX -------------------------------------------------------
 HAP_DEV void tma_load_2d(uint32_t dst, const CUtensorMap* map, int c0, int c1, uint32_t bar) {
@@ -100,21 +90,6 @@ HAP_DEV float max32(const uint32_t (&r)[32]) {
     return m[0];
 }
 
-HAP_DEV void tmem_ld_32x32b_x32(uint32_t taddr, float (&v)[32]) {
-    uint32_t r[32];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-                 "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-                 "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-                   "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-                   "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-                 : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
-}
-
 // Shared-memory matrix descriptor of a K-major operand tile written by TMA
 // with 128-byte swizzle: rows of 128 bytes, 8-row groups 1024 bytes apart.
 // Bits: [0,14) start >> 4, [16,30) leading offset >> 4 (unused here),
@@ -122,127 +97,6 @@ HAP_DEV void tmem_ld_32x32b_x32(uint32_t taddr, float (&v)[32]) {
 HAP_DEV uint64_t desc_kmajor_sw128(uint32_t saddr) {
     return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
            ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
-}
-// Instruction descriptor, kind::f16: D FP32 (bits 4-5 = 1), A and B BF16
-// (bits 7-9 = 1, 10-12 = 1), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
-
-template <typename OT>
-HAP_DEV void store4(OT* dst, float4 w);
-template <>
-HAP_DEV void store4<float>(float* dst, float4 w) { *reinterpret_cast<float4*>(dst) = w; }
-template <>
-HAP_DEV void store4<__nv_bfloat16>(__nv_bfloat16* dst, float4 w) {
-    __nv_bfloat162 p0 = __floats2bfloat162_rn(w.x, w.y), p1 = __floats2bfloat162_rn(w.z, w.w);
-    uint2 u;
-    u.x = *reinterpret_cast<uint32_t*>(&p0);
-    u.y = *reinterpret_cast<uint32_t*>(&p1);
-    *reinterpret_cast<uint2*>(dst) = u;
-}
-
-template <typename OT>
-__global__ void __launch_bounds__(128, 1) sbuild_tc_kernel(const __grid_constant__ CUtensorMap tmA,
-                                                          const __grid_constant__ CUtensorMap tmB,
-                                                          const float* __restrict__ norms, OT* __restrict__ S,
-                                                          int N, int64_t ld, int kchunks, unsigned* status) {
-    extern __shared__ unsigned char smem_raw[];
-    // 1024-byte aligned base for the 128-byte swizzled tiles
-    const uint32_t raw = smem_addr(smem_raw);
-    const uint32_t base = (raw + 1023u) & ~1023u;
-    __shared__ uint64_t bars[2 * kRing + 1];  // full[kRing], empty[kRing], done
-    __shared__ uint32_t tmem_base_slot;
-    __shared__ float col_norm[BN];
-
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-    const uint32_t bar_full = smem_addr(&bars[0]), bar_empty = smem_addr(&bars[kRing]), bar_done = smem_addr(&bars[2 * kRing]);
-
-    if (tid == 0) {
-        for (int q = 0; q < 2 * kRing + 1; ++q) mbar_init(smem_addr(&bars[q]), 1);
-        fence_mbarrier_init();
-    }
-    if (warp == 0) tmem_alloc(smem_addr(&tmem_base_slot), kTmemCols);
-    col_norm[tid] = (n0 + tid < N) ? norms[n0 + tid] : 0.f;
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = tmem_base_slot;
-
-    bool ok = true;
-    if (tid == 0) {
-        auto load_chunk = [&](int k) {
-            const int st = k % kRing;
-            const uint32_t sa = base + (uint32_t)st * kChunkBytes, sb = sa + BM * BK * 2;
-            mbar_arrive_expect_tx(bar_full + 8 * st, kChunkBytes);
-            tma_load_2d(sa, &tmA, k * BK, m0, bar_full + 8 * st);
-            tma_load_2d(sb, &tmB, k * BK, n0, bar_full + 8 * st);
-        };
-        for (int k = 0; k < kchunks && k < kRing; ++k) load_chunk(k);
-        for (int k = 0; k < kchunks && ok; ++k) {
-            const int st = k % kRing;
-            ok = mbar_wait(bar_full + 8 * st, (uint32_t)(k / kRing) & 1u, status);
-            if (!ok) break;
-            tc_fence_after();
-            const uint32_t sa = base + (uint32_t)st * kChunkBytes, sb = sa + BM * BK * 2;
-#pragma unroll
-            for (int kk = 0; kk < BK / 16; ++kk)  // 16 BF16 = 32 bytes per MMA along K
-                umma_bf16(tmem, desc_kmajor_sw128(sa + 32 * kk), desc_kmajor_sw128(sb + 32 * kk), kIdesc,
-                          (k > 0 || kk > 0) ? 1u : 0u);
-            umma_commit(bar_empty + 8 * st);
-            if (k + kRing < kchunks) {
-                ok = mbar_wait(bar_empty + 8 * st, (uint32_t)(k / kRing) & 1u, status);
-                if (ok) load_chunk(k + kRing);
-            }
-        }
-        if (ok) umma_commit(bar_done);
-        else mbar_arrive(bar_done);  // release the epilogue; results are flagged invalid
-    }
-    __syncwarp();
-    mbar_wait(bar_done, 0u, status);
-    __syncwarp();  // tcgen05.ld below is warp-collective
-    tc_fence_after();
-
-    // ---- epilogue: warp w owns TMEM lanes (tile rows) 32w .. 32w+31 ---------
-    // Each 32 x 32 block goes through shared memory (the K-chunk ring is idle
-    // once every MMA has completed) so that one store instruction writes
-    // four full 128-byte row segments instead of 32 scattered 16-byte pieces.
-    const int row = m0 + 32 * warp + lane;
-    const float ni = row < N ? norms[row] : 0.f;
-    constexpr int kStg = 36;  // staging row stride in floats (16-byte aligned rows)
-    float* stg = reinterpret_cast<float*>(smem_raw + (base - raw)) + warp * 32 * kStg;
-#pragma unroll 1
-    for (int cc = 0; cc < BN / 32; ++cc) {
-        float v[32];
-        tmem_ld_32x32b_x32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(32 * cc), v);
-#pragma unroll
-        for (int q = 0; q < 32; ++q) v[q] = __fsub_rn(__fsub_rn(2.f * v[q], ni), col_norm[32 * cc + q]);
-#pragma unroll
-        for (int q = 0; q < 32; q += 4)
-            *reinterpret_cast<float4*>(stg + lane * kStg + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
-        __syncwarp();
-        const int c0 = n0 + 32 * cc;
-#pragma unroll
-        for (int rr = 0; rr < 8; ++rr) {
-            const int r = 4 * rr + (lane >> 3), col = 4 * (lane & 7);
-            const int grow = m0 + 32 * warp + r;
-            const float4 w = *reinterpret_cast<const float4*>(stg + r * kStg + col);
-            if (grow < N) {
-                OT* dst = S + (int64_t)grow * ld + c0 + col;
-                if (c0 + col + 4 <= N) {
-                    store4<OT>(dst, w);
-                } else {
-                    const float wv[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        if (c0 + col + q < N) dst[q] = (OT)wv[q];
-                }
-            }
-        }
-        __syncwarp();  // the staging block is rewritten by the next chunk
-    }
-    tc_fence_before();
-    __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, kTmemCols);
 }
 
 // ---- symmetric persistent build -----------------------------------------------
@@ -430,6 +284,7 @@ __global__ void __launch_bounds__(SY_THREADS, 1) sbuild_sym_kernel(const __grid_
     unsigned char* stg_all = smem_raw + (sS - raw);
     // full[R], empty[R], acc_full[2], acc_empty[2], mma_done
     __shared__ uint64_t bars[2 * SY_RING_MAX + 5];
+    __shared__ __align__(16) float cnorm[2][SY_BN];  // column norms of the tile (by tile parity)
     __shared__ uint32_t tmem_slot;
     __shared__ int s_abort;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -511,18 +366,24 @@ __global__ void __launch_bounds__(SY_THREADS, 1) sbuild_sym_kernel(const __grid_
         const uint64_t pol = l2_evict_first();
         int tl = 0, ch = 0;
         for (int64_t t = t_first; t < total; t += t_step, ++tl) {
+            const int wr = __ldg(tiles + t) >> 16, wJ = __ldg(tiles + t) & 0xffff;
+            const int r0 = wr * BM + 32 * warp, row = r0 + lane;
+            const float ni = row < N ? __ldg(norms + row) : 0.f;
+            // the tile's column norms into shared memory (read as broadcasts
+            // below; the buffer of this parity was last read two tiles ago,
+            // before the barrier of the previous tile)
+            const int buf = tl & 1;
+            const int cj = wJ * SY_BN + tid;  // (the norms hold T * 128 values)
+            cnorm[buf][tid] = cj < T * BM ? __ldg(norms + cj) : 0.f;
+            cnorm[buf][tid + BM] = cj + BM < T * BM ? __ldg(norms + cj + BM) : 0.f;
             // one decision for all 128 epilogue threads (they meet at named
             // barriers below, and the TMEM loads are warp-collective)
-            const int buf = tl & 1;
             const bool got = *abort_flag == 0 && mbar_wait(acc_full + 8 * buf, (uint32_t)((tl >> 1) & 1), status);
             if (!epi_all(got)) {
                 *abort_flag = 1;
                 break;
             }
             tc_fence_after();
-            const int wr = __ldg(tiles + t) >> 16, wJ = __ldg(tiles + t) & 0xffff;
-            const int r0 = wr * BM + 32 * warp, row = r0 + lane;
-            const float ni = row < N ? __ldg(norms + row) : 0.f;
 #pragma unroll 1
             for (int h = 0; h < 2; ++h) {
                 const int cb = 2 * wJ + h;  // 128-column block of this half
@@ -551,7 +412,7 @@ __global__ void __launch_bounds__(SY_THREADS, 1) sbuild_sym_kernel(const __grid_
                     float v[32];
 #pragma unroll
                     for (int q = 0; q < 32; q += 4) {
-                        const float4 nj = __ldg(reinterpret_cast<const float4*>(norms + c0 + q));
+                        const float4 nj = *reinterpret_cast<const float4*>(&cnorm[buf][128 * h + 32 * cc + q]);
                         v[q + 0] = __fsub_rn(__fsub_rn(2.f * __uint_as_float(rg[cc][q + 0]), ni), nj.x);
                         v[q + 1] = __fsub_rn(__fsub_rn(2.f * __uint_as_float(rg[cc][q + 1]), ni), nj.y);
                         v[q + 2] = __fsub_rn(__fsub_rn(2.f * __uint_as_float(rg[cc][q + 2]), ni), nj.z);
@@ -1132,17 +993,17 @@ cudaError_t launch_sbuild_tc(const float* X, int64_t N, int64_t d, int split, vo
     err = cudaGetLastError();
     if (err != cudaSuccess) return err;
     *kernels = 1;
-    CUtensorMap mA, mB;
-    if (!encode_operand_map(&mA, A, sl.npad, sl.kpad) || !encode_operand_map(&mB, B, sl.npad, sl.kpad))
-        return cudaErrorNotSupported;
+    CUtensorMap mA;
+    if (!encode_operand_map(&mA, A, sl.npad, sl.kpad)) return cudaErrorNotSupported;
     const int kchunks = (int)(sl.kpad / BK);
-    // the symmetric persistent kernel where a ring of at least two stages fits
+    // the symmetric persistent kernel (a ring of at least two stages fits on
+    // every GPU this targets; otherwise the build is not supported)
     int dev = 0, smem_optin = 0, n_sm = 0;
     err = cudaGetDevice(&dev);
     if (err == cudaSuccess) err = cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (err == cudaSuccess) err = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
     if (err != cudaSuccess) return err;
-    const size_t room = (size_t)smem_optin - 1024;  // the kernel's static shared memory
+    const size_t room = (size_t)smem_optin - 4096;  // the kernel's static shared memory (2.2 KB)
     int ring = SY_RING_MAX;
     while (ring >= 2 && sbuild_sym_smem_bytes(ring) > room) --ring;
     CUtensorMap mBw, mSd, mSt;
@@ -1174,22 +1035,7 @@ cudaError_t launch_sbuild_tc(const float* X, int64_t N, int64_t d, int split, vo
         if (err == cudaSuccess) *kernels = 3;
         return err;
     }
-    const size_t smem = (size_t)kRing * kChunkBytes + 1024;
-    const dim3 grid((unsigned)(sl.npad / BN), (unsigned)(sl.npad / BM));
-    if (s_bf16) {
-        auto k = sbuild_tc_kernel<__nv_bfloat16>;
-        err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (err != cudaSuccess) return err;
-        k<<<grid, 128, smem, st>>>(mA, mB, norms, static_cast<__nv_bfloat16*>(S), (int)N, ld, kchunks, status);
-    } else {
-        auto k = sbuild_tc_kernel<float>;
-        err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (err != cudaSuccess) return err;
-        k<<<grid, 128, smem, st>>>(mA, mB, norms, static_cast<float*>(S), (int)N, ld, kchunks, status);
-    }
-    err = cudaGetLastError();
-    if (err == cudaSuccess) *kernels = 2;
-    return err;
+    return cudaErrorNotSupported;
 }
 
 
