@@ -49,6 +49,8 @@ LEARNED = {"c4": (262144, 32, 3, 64, 400,
                   "neighbours and its 59 nearest hubs (the N/16 points the MLP proposal scores highest; trained on "
                   "dense HAP labels of two N=8192 instances), sparse HAP 400 iterations, c fixed, lambda 0.9")}
 HUB_DIV, K_NEAR = 16, 4  # hubs = N / HUB_DIV; nearest neighbours kept besides the hubs
+REFINE = 0  # further sparse solves, each on every point's nearest exemplars of the previous one
+# (hap.refine_candidates; measured unstable on this workload, so off)
 CPU_SAMPLE_N = 4096
 CPU_SAMPLE_ITERS = 8  # about 10 s of single-threaded reference work
 CPU_CORES_N = 8192    # points of the all-cores reference sample
@@ -656,9 +658,9 @@ def run_learned(args, world, rank, local):
         p = np.float32(np.median(-np.einsum("kd,kd->k", df, df)))
         return X32, lab, np.array([4.0 * p * (1 + l) for l in range(L)], dtype=np.float32)
 
-    def dense(X32, prefs):
+    def dense(X32, prefs, **shape):
         n = X32.shape[0]
-        ctx = hap.HAP(n, L, prefs=prefs, damping=lam, device=dev, c_mode="fixed")
+        ctx = hap.HAP(n, L, prefs=prefs, damping=lam, device=dev, c_mode="fixed", **shape)
         ctx.build_similarity(torch.from_numpy(X32).to(dev), mode="bf16_split")
         ctx.iterate(T)
         e = ctx.exemplars()
@@ -685,7 +687,13 @@ def run_learned(args, world, rank, local):
     loss = mlp.train_step(Fm, Y, posw, 3e-3, want_loss=True)
     t_train = time.perf_counter() - t_train
 
-    def sparse_solve(Xt, prefs, score, k_near, iters):
+    def ctx_clusters(n):
+        c = hap.HAP(n, L, prefs=np.ones(L, np.float32) * -1.0, damping=lam, device=dev)
+        g = int(c.shape["grid_clusters"])
+        c.close()
+        return g
+
+    def sparse_solve(Xt, prefs, score, k_near, iters, refine=0):
         n = Xt.shape[0]
         if score == "mlp":
             pool, dist_ = hap.knn(Xt, M)
@@ -699,6 +707,9 @@ def run_learned(args, world, rank, local):
         sp = hap.HAPSparse(n, L, K, prefs=prefs, damping=lam, c_mode="fixed", device=dev)
         sp.set_candidates(cand, Xt)
         sp.iterate(iters)
+        for _ in range(refine):
+            sp.set_candidates(hap.refine_candidates(Xt, pool, sp.exemplars(), K, k_near), Xt)
+            sp.iterate(iters)
         e = sp.exemplars()
         ns = sp.net_similarity()
         sp.close()
@@ -714,8 +725,19 @@ def run_learned(args, world, rank, local):
         ns_d = hap.net_similarity_points(Xjt, e_d, ptj)
         ed = e_d.cpu().numpy()
         judge = {"n": args.judge_n, "dense_exemplars_level1": int(len(np.unique(ed[0])))}
-        for name, sc, kn in (("learned", "mlp", K_NEAR), ("knn", None, K - 1)):
-            e_s, ns_s = sparse_solve(Xjt, pj, sc, kn, T)
+        # the judge's own repeatability: dense HAP again with half the row-pass
+        # clusters, which sums the columns in another (equally valid) order
+        e_d2 = dense(Xj, pj, grid_clusters=max(1, ctx_clusters(args.judge_n) // 2))
+        ns_d2 = hap.net_similarity_points(Xjt, e_d2, ptj)
+        ed2 = e_d2.cpu().numpy()
+        judge["dense_other_order"] = {"ns_gap_level1": float((ns_d[0] - ns_d2[0]) / abs(ns_d[0])),
+                                      "ari_level1": ari(ed2[0], ed[0]),
+                                      "exemplars_level1": int(len(np.unique(ed2[0])))}
+        arms = [("learned", "mlp", K_NEAR, REFINE), ("knn", None, K - 1, 0)]
+        if REFINE:
+            arms.append(("learned_first_solve", "mlp", K_NEAR, 0))
+        for name, sc, kn, rf in arms:
+            e_s, ns_s = sparse_solve(Xjt, pj, sc, kn, T, rf)
             es = e_s.cpu().numpy()
             judge[name] = {"ns_gap_level1": float((ns_d[0] - ns_s[0]) / abs(ns_d[0])),
                            "ari_level1": ari(es[0], ed[0]),
@@ -733,6 +755,7 @@ def run_learned(args, world, rank, local):
     stream = torch.cuda.current_stream(dev)
     sp = hap.HAPSparse(N, L, K, prefs=prefs, damping=lam, c_mode="fixed", device=dev)
     e_out = torch.empty((L, N), dtype=torch.int32, device=dev)
+    e_mid = torch.empty((L, N), dtype=torch.int32, device=dev)
 
     def step(e_buf):
         pool, dist_ = hap.knn(Xt, M)
@@ -740,6 +763,10 @@ def run_learned(args, world, rank, local):
         hubnn, _ = hap.knn_subset(Xt, hap.top_scores(mlp.forward(f), N // HUB_DIV), K)
         sp.set_candidates(hap.select_hub_candidates(pool, hubnn, K, K_NEAR), Xt)
         sp.iterate(T)
+        for _ in range(REFINE):
+            sp.exemplars(e_mid)
+            sp.set_candidates(hap.refine_candidates(Xt, pool, e_mid, K, K_NEAR), Xt)
+            sp.iterate(T)
         sp.exemplars(e_buf)
         return sp.net_similarity()
 
@@ -810,7 +837,7 @@ def run_learned(args, world, rank, local):
     k1.record(stream)
     torch.cuda.synchronize()
     knn_ms = k0.elapsed_time(k1)
-    updates = float(N) * K * L * T
+    updates = float(N) * K * L * T * (1 + REFINE)
     value = world * args.steps * updates / (ms / 1e3)
     peaks, peak_src = measured_peaks()
     # per sparse update: alpha, rho read + write (16 B); per row entry once per iteration: s, the candidate
@@ -823,7 +850,8 @@ def run_learned(args, world, rank, local):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": args.workload, "desc": desc, "N": N, "K": K, "L": L, "iters": T,
-                       "updates_counted": "sparse N*K*L per iteration", "knn_ms": knn_ms,
+                       "updates_counted": "sparse N*K*L per iteration, %d solves of %d iterations" % (1 + REFINE, T),
+                       "hubs": "N/%d" % HUB_DIV, "near": K_NEAR, "refinement_solves": REFINE, "knn_ms": knn_ms,
                        "sparse_iteration_ms": it_ms, "sparse_step_ms": steps_ms, "train_s": t_train, "train_loss": loss, "judge": judge,
                        "judge_full_n": full_n},
             "e2e": {"value": world * max(1, args.e2e_steps) * updates / e2e_s, "unit": "updates/s",

@@ -363,6 +363,15 @@ int hap_knn_subset_with(const float* X, int64_t N, int64_t d, const int32_t* sub
  * ordered by decreasing score, into hubs device int32 [H].  Asynchronous. */
 int hap_top_scores(const float* score, int64_t N, int64_t H, int32_t* hubs, void* stream);
 
+/* The distinct points among n_e exemplar indices (device int32 e, e.g. the
+ * [L][N] output of hap_sparse_exemplars; entries outside [0, N) are
+ * ignored), in increasing order, into points (device int32, room for N);
+ * their number in *count (host).  Used to refine a candidate graph: every
+ * point's nearest exemplars of one sparse solve (hap_knn_subset with these
+ * points, then hap_select_hub_candidates) as the hubs of the next solve.
+ * Uses a stream-ordered temporary of about 8N bytes.  Synchronising. */
+int hap_exemplar_points(const int32_t* e, int64_t n_e, int64_t N, int32_t* points, int64_t* count, void* stream);
+
 /* Candidates per row: the row itself, its K_near nearest (pool [N][Mp]),
  * then its nearest hubs (hubnn [N][Mh], global indices) not already taken,
  * then further pool entries; sorted by index, K <= 64.  Asynchronous. */

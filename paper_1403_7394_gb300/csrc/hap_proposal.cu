@@ -167,6 +167,22 @@ __global__ void select_hub_candidates_kernel(const int32_t* __restrict__ pool, i
     for (int q = 0; q < K; ++q) cand[(int64_t)i * K + q] = q < ns ? sel[q] : -1;
 }
 
+// Distinct exemplars: flag every point chosen as an exemplar, then list the
+// flagged points in increasing order (exclusive prefix sum of the flags).
+__global__ void mark_points_kernel(const int32_t* __restrict__ e, int64_t n_e, int64_t N, int* __restrict__ flag) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_e) return;
+    const int32_t v = e[k];
+    if (v >= 0 && v < N) flag[v] = 1;
+}
+__global__ void compact_points_kernel(const int* __restrict__ flag, const int* __restrict__ off, int64_t N,
+                                      int32_t* __restrict__ points, int* __restrict__ count) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    if (flag[i]) points[off[i]] = (int32_t)i;
+    if (i == N - 1) *count = off[i] + flag[i];
+}
+
 // mean over rows of log(dist[i][F-1]) in FP64: per-block partials, fixed order
 __global__ void log_mean_partial_kernel(const float* __restrict__ dist, int N, int M, int col, double* __restrict__ part) {
     __shared__ double red[256];
@@ -635,6 +651,36 @@ int hap_top_scores(const float* score, int64_t N, int64_t H, int32_t* hubs, void
     cudaError_t err = cudaGetLastError();
     cudaFreeAsync(keys, st);
     PCU(err);
+    return HAP_OK;
+}
+
+int hap_exemplar_points(const int32_t* e, int64_t n_e, int64_t N, int32_t* points, int64_t* count, void* stream) {
+    if (!e || !points || !count || n_e < 1 || N < 1 || N > (1 << 30)) return HAP_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int64_t tiles = scan_tiles(N);
+    char* buf = nullptr;
+    const size_t fb = ((size_t)N * 4 + 255) / 256 * 256;
+    PCU(cudaMallocAsync(reinterpret_cast<void**>(&buf), 2 * fb + (size_t)tiles * 8 + 256, st));
+    int* flag = reinterpret_cast<int*>(buf);
+    int* off = reinterpret_cast<int*>(buf + fb);
+    int64_t* tsum = reinterpret_cast<int64_t*>(buf + 2 * fb);
+    int* cnt = reinterpret_cast<int*>(buf + 2 * fb + (size_t)tiles * 8);
+    cudaError_t err = cudaMemsetAsync(flag, 0, (size_t)N * 4, st);
+    if (err == cudaSuccess) {
+        mark_points_kernel<<<(unsigned)((n_e + 255) / 256), 256, 0, st>>>(e, n_e, N, flag);
+        err = scan_exclusive(flag, N, off, tsum, st);
+    }
+    if (err == cudaSuccess) {
+        compact_points_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(flag, off, N, points, cnt);
+        err = cudaGetLastError();
+    }
+    int c = 0;
+    if (err == cudaSuccess) err = cudaMemcpyAsync(&c, cnt, 4, cudaMemcpyDeviceToHost, st);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+    cudaFreeAsync(buf, st);
+    PCU(err);
+    g_launches += 5;  // mark, three scan launches, compact
+    *count = c;
     return HAP_OK;
 }
 

@@ -84,6 +84,7 @@ def _load():
         "hap_knn_subset": (i32, [vp, i64, i64, vp, i64, i32, vp, vp, vp]),
         "hap_top_scores": (i32, [vp, i64, i64, vp, vp]),
         "hap_select_hub_candidates": (i32, [vp, i64, i32, vp, i32, i32, i32, vp, vp]),
+        "hap_exemplar_points": (i32, [vp, i64, i64, vp, ctypes.POINTER(i64), vp]),
         "hap_mlp_create": (i32, [i32, vp, ctypes.POINTER(vp)]),
         "hap_mlp_destroy": (None, [vp]),
         "hap_mlp_set_stream": (i32, [vp, vp]),
@@ -503,6 +504,27 @@ def select_hub_candidates(pool: torch.Tensor, hubnn: torch.Tensor, K: int, K_nea
                                         int(K_near), _ptr(cand), _stream_ptr(pool.device, stream)),
           "hap_select_hub_candidates")
     return cand
+
+
+def exemplar_points(e: torch.Tensor, N: int, stream=None):
+    """The distinct points among the exemplar indices e (any shape, device
+    int32), in increasing order: a device int32 tensor (a view of length
+    count)."""
+    e = e.contiguous()
+    points = torch.empty(int(N), dtype=torch.int32, device=e.device)
+    count = ctypes.c_int64()
+    check(lib.hap_exemplar_points(_ptr(e), e.numel(), int(N), _ptr(points), ctypes.byref(count),
+                                  _stream_ptr(e.device, stream)), "hap_exemplar_points")
+    return points[: count.value]
+
+
+def refine_candidates(X: torch.Tensor, pool: torch.Tensor, e: torch.Tensor, K: int, K_near: int, stream=None):
+    """Candidates for a second sparse solve: every row keeps itself, its
+    K_near nearest neighbours (pool) and its nearest exemplars of the first
+    solve (e, all levels) as hubs (up to K in all)."""
+    hubs = exemplar_points(e, X.shape[0], stream)
+    hubnn, _ = knn_subset(X, hubs, min(int(K), hubs.numel()), stream)
+    return select_hub_candidates(pool, hubnn, K, K_near, stream)
 
 
 def knn_features(dist: torch.Tensor, F: int, stream=None):

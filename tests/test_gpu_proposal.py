@@ -152,6 +152,34 @@ def test_hub_selection_subset_knn_and_candidates():
     np.testing.assert_array_equal(c, P.select_hub_candidates(pool.cpu().numpy(), hubnn.cpu().numpy(), 40, 16))
 
 
+def test_exemplar_points_and_refined_candidates():
+    """hap_exemplar_points lists the distinct valid exemplar indices in
+    increasing order (np.unique); the refined candidates are the hub
+    candidates with exactly those points as hubs, also when there are fewer
+    exemplars than K."""
+    hap = hapm()
+    N, K, K_near = 2000, 32, 4
+    rng = np.random.default_rng(9)
+    e = rng.integers(-3, N + 3, size=(3, N)).astype(np.int32)  # entries outside [0, N) are ignored
+    e[:, ::7] = 5
+    pts = hap.exemplar_points(torch.from_numpy(e).to(DEV), N).cpu().numpy()
+    np.testing.assert_array_equal(pts, np.unique(e[(e >= 0) & (e < N)]))
+    X, _ = W.gmm_points(N, 8, 10, sigma=1.0, seed=12, means="normal", mean_scale=2.0)
+    X32 = X.astype(np.float32)
+    Xt = torch.from_numpy(X32).to(DEV)
+    pool, _ = hap.knn(Xt, 16)
+    for n_ex in (20, 300):  # fewer and more exemplars than K
+        ex = np.sort(rng.choice(N, n_ex, replace=False)).astype(np.int32)
+        e2 = ex[rng.integers(0, n_ex, size=(2, N))]
+        e2[0, :n_ex] = ex  # every one of them used
+        cand = hap.refine_candidates(Xt, pool, torch.from_numpy(e2).to(DEV), K, K_near).cpu().numpy()
+        hubnn, _ = hap.knn_subset(Xt, torch.from_numpy(ex).to(DEV), min(K, n_ex))
+        want = P.select_hub_candidates(pool.cpu().numpy(), hubnn.cpu().numpy(), K, K_near)
+        np.testing.assert_array_equal(cand, want)
+        ridx, _ = P.knn_subset(X32, ex, min(K, n_ex))
+        assert np.any(hubnn.cpu().numpy() != ridx, axis=1).mean() <= 0.01  # FP32 near-ties only
+
+
 def _sparse_problem(N, L, K, seed, K_near=None, score=None):
     hap = hapm()
     X, _ = W.gmm_points(N, 2, 6, sigma=0.6, seed=seed, means="uniform", mean_scale=10.0)
