@@ -614,7 +614,7 @@ def run_batched(args, world, rank, local):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": args.workload, "desc": desc, "instances": B, "iters": T,
                        "sum_N2L": float(sum(n * n * l for n, l in zip(Ns, Ls))), "sbuild": args.sbuild,
-                       "s_dtype": args.s_dtype, "items_per_cta": bt.query(8), "tuned_iteration_ms": tuned_ms,
+                       "s_dtype": args.s_dtype, "items_per_cta": bt.query(8), "elems_per_thread": bt.query(6), "tuned_iteration_ms": tuned_ms,
                        "l2": "inputs larger than L2"},
             "e2e": {"value": e2e, "unit": "updates/s", "h2d_bytes_per_step": int(X.nbytes),
                     "d2h_bytes_per_step": int(total * 4 + sum(Ls) * 8)},

@@ -304,12 +304,79 @@ int hap_batch_exemplars(hap_batch* batch, int32_t* e, int on_host);
 int hap_batch_net_similarity(hap_batch* batch, double* ns);
 /* Instance b's messages, as hap_get_state (device buffers for N[b], L[b]). */
 int hap_batch_get_state(hap_batch* batch, int b, float* A, float* R, float* vecs, int64_t* iter);
-/* Autotuner: times one steady-state iteration for several work-split
- * granularities (items per CTA) and keeps the fastest; resets the messages
- * to Algorithm 1's start.  best_ms (may be NULL) receives its time. */
+/* Autotuner: times one steady-state iteration for every tile width of the
+ * row pass (16 columns per thread with 8192-element ring steps, or 8 columns
+ * with 4096-element steps in a deeper ring; 16 needs every L[b] <= 8) and
+ * every work-split granularity (items per CTA), and keeps the fastest pair;
+ * resets the messages to Algorithm 1's start.  best_ms (may be NULL)
+ * receives its time; hap_batch_query gives the choice
+ * (HAP_Q_ELEMS_PER_THREAD, HAP_Q_BATCH_ITEMS_PER_CTA). */
 int hap_batch_tune(hap_batch* batch, double* best_ms);
+/* Sets the tile width by hand: elems_per_thread 16 or 8 (16 needs every
+ * L[b] <= 8, else HAP_EUNSUPPORTED).  Resets the messages.  Synchronising. */
+int hap_batch_set_tile(hap_batch* batch, int elems_per_thread);
 int hap_batch_query(hap_batch* batch, int key, int64_t* value);
 int hap_batch_sync(hap_batch* batch);
+
+/* ---- row bands ---------------------------------------------------------------
+ * One HAP problem split by rows (§3: MR-HAP keys the responsibility job by
+ * node i, so rows are independent given the column statistics, and the
+ * availability job keys by exemplar j, so columns need every row's rho).  A
+ * band holds rows row0 .. row0 + nrows - 1 of S, alpha and rho for all L
+ * levels; only column statistics cross bands, once per iteration:
+ *   1. hap_band_rows on every band: the row pass of one iteration (the same
+ *      kernels and equations as hap_iterate) over the band's rows, then the
+ *      band's exchange buffer xch [4][L][ld] float (device): its rows' part of
+ *      P_j = sum_i max(0, rho_ij), i != j (Eqs. 2.2-2.4), and the c (Eq. 2.6),
+ *      phi (Eq. 2.5) and rho_jj of the rows it owns (zero elsewhere);
+ *   2. the caller gathers every band's buffer, in band order, into one
+ *      device array xch_all [P][4][L][ld] (an all-gather between devices, or
+ *      plain copies when the bands share a device);
+ *   3. hap_band_columns on every band: P_j summed in band order (so every band
+ *      gets the same bits), c, phi and rho_jj of column j from the band owning
+ *      row j, then b_j and tau's column part for the next iteration.
+ * With one band covering all rows this gives the bits of hap_iterate with the
+ * same launch shape.  A band context allocates its own device memory.
+ *   N       points of the whole problem (2 .. 65536); L levels (1 .. 16)
+ *   row0, nrows  the band's rows, 0 <= row0, 1 <= nrows, row0 + nrows <= N
+ *   prefs   host [L] preferences, or NULL for 0
+ * Options: c_mode, s_dtype, launch-shape fields, wait_limit_ns; the level
+ * schedule must be JACOBI, kappa 0, s_per_level and debug_bounds 0 (else
+ * HAP_EUNSUPPORTED). */
+typedef struct hap_band hap_band;
+int hap_band_create(int64_t N, int64_t row0, int64_t nrows, int L, const float* prefs, float damping,
+                    const hap_options* opt, hap_band** out);
+void hap_band_destroy(hap_band* band);
+int hap_band_set_stream(hap_band* band, void* stream);
+/* Copies the band's rows of the similarity: S device, nrows rows (rows row0..
+ * of the problem's S) of ld_src >= N elements, dtype HAP_S_*; the diagonal
+ * (column row0 + i of row i) is ignored.  Resets the messages to Algorithm 1's
+ * start.  Synchronising. */
+int hap_band_set_similarity(hap_band* band, const void* S, int64_t ld_src, int dtype);
+/* Floats in one exchange buffer (4 * L * ld). Host call. */
+int hap_band_exchange_floats(hap_band* band, int64_t* n);
+/* Step 1 of an iteration: the row pass over the band, then its exchange
+ * buffer into xch (device float [4][L][ld]).  HAP_EINVAL if the previous
+ * iteration's hap_band_columns is missing.  Asynchronous. */
+int hap_band_rows(hap_band* band, float* xch);
+/* Step 3: column statistics from every band's buffer.  xch_all device float
+ * [P][4][L][ld] in band order; bounds host int64 [P + 1]: band r owns rows
+ * bounds[r] .. bounds[r+1] - 1 (bounds[0] = 0, bounds[P] = N, increasing, one
+ * band being this one); 1 <= P <= 64.  Completes the iteration.  HAP_EINVAL
+ * before hap_band_rows of the same iteration.  Asynchronous. */
+int hap_band_columns(hap_band* band, const float* xch_all, int P, const int64_t* bounds);
+/* The band's messages after hap_band_query(HAP_Q_ITER) iterations: A, R device
+ * float [L][nrows][N] (may be NULL); vecs device float [3][L][N]: c, tau, phi
+ * as this band holds them (c and phi of every point after hap_band_columns,
+ * tau of the band's own rows); iter host (may be NULL).  Asynchronous. */
+int hap_band_get_state(hap_band* band, float* A, float* R, float* vecs, int64_t* iter);
+/* Eq. 2.8 for the band's rows: e int32 [L][nrows] (global column indices);
+ * on_host as for hap_exemplars. */
+int hap_band_exemplars(hap_band* band, int32_t* e, int on_host);
+/* Waits for the bound stream and checks the device status word. */
+int hap_band_sync(hap_band* band);
+/* HAP_Q_* keys as for hap_query. Host call. */
+int hap_band_query(hap_band* band, int key, int64_t* value);
 
 /* ---- learned candidate proposal and sparse HAP ------------------------------
  * Not in the paper (its method is dense, §2): each row keeps K candidate

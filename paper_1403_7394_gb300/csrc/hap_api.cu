@@ -265,6 +265,24 @@ int plan(int64_t N, int L, const hap_options& o, LaunchShape* sh, Layout* y) {
     return HAP_OK;
 }
 
+}  // namespace
+
+// The row width fixes the shape (one cluster per row); the rows held only cap
+// the grid.
+int hap::plan_shape(int64_t N, int64_t nrows, int L, const hap_options& o, LaunchShape* sh) {
+    if (N < 2 || L < 1 || L > 16 || nrows < 1 || nrows > N) return HAP_EINVAL;
+    if (N > 65536) return HAP_EUNSUPPORTED;
+    int rc = check_opts(o);
+    if (rc) return rc;
+    rc = choose_shape(N, L, o, sh);
+    if (rc) return rc;
+    return finish_shape(nrows, L, o, sh);
+}
+
+int hap::check_options(const hap_options& o) { return check_opts(o); }
+
+namespace {
+
 #define CU(x)                                        \
     do {                                             \
         cudaError_t e_ = (x);                        \

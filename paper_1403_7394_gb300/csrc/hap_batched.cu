@@ -89,9 +89,6 @@ int batched_tmem_cols(int K, int maxL) {
 HAP_DEV void named_barrier(int id, int threads) {
     asm volatile("bar.sync %0, %1;" :: "r"(id), "r"(threads) : "memory");
 }
-HAP_DEV void mbar_arrive_local(uint32_t bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(bar) : "memory");
-}
 
 template <typename ST>
 HAP_DEV float4 bload_s(const ST* p);
@@ -546,6 +543,24 @@ void group_shape(int ld, int K, int* rps, int* g) {
     *rps = kBW / *g;
 }
 
+// Tile width of the batch's row pass: 4K columns per thread (16 with a 2-stage
+// ring of 8192-element steps, or 8 with a 4-stage ring of 4096-element steps),
+// with every instance's row groups re-derived from it.  16 columns need
+// every instance to have at most 8 levels (TMEM holds 4 warp slots x L x 16
+// columns).  The schedule is rebuilt by the caller.
+int set_tile(hap_batch* h, int K) {
+    if (K != 4 && K != 2) return HAP_EINVAL;
+    if (K == 4 && h->maxL > 8) return HAP_EUNSUPPORTED;
+    h->K = K;
+    h->tcols = batched_tmem_cols(K, h->maxL);
+    for (int b = 0; b < h->B; ++b) group_shape(h->ld[b], K, &h->inst[b].rps, &h->inst[b].g);
+    if (h->graph) {
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
+    return HAP_OK;
+}
+
 // Bands per instance (total ~ items_per_cta x grid, proportional to work) and
 // a longest-processing-time assignment of items to the persistent CTAs.
 int schedule(hap_batch* h) {
@@ -704,20 +719,24 @@ int hap_batch_create(int B, const int64_t* N, const int* L, float damping, const
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&smem_limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    const size_t smem = batched_smem_bytes(h->K, h->s_bf16 ? 2 : 4);
-    if (smem > (size_t)smem_limit || h->tcols > 512) { delete h; return HAP_EUNSUPPORTED; }
-    // the shared-memory opt-in is set here, never inside a stream capture
-    cudaError_t fa = h->K == 4
-        ? cudaFuncSetAttribute(h->s_bf16 ? (const void*)rowpass_batched_kernel<__nv_bfloat16, 4>
-                                         : (const void*)rowpass_batched_kernel<float, 4>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-        : cudaFuncSetAttribute(h->s_bf16 ? (const void*)rowpass_batched_kernel<__nv_bfloat16, 2>
-                                         : (const void*)rowpass_batched_kernel<float, 2>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (fa != cudaSuccess) {
-        cudaGetLastError();
-        delete h;
-        return HAP_ECUDA;
+    // the shared-memory opt-in of both tile widths is set here, never inside a
+    // stream capture (the autotuner may switch between them)
+    for (int K : {4, 2}) {
+        if (K == 4 && maxL > 8) continue;
+        const size_t smem = batched_smem_bytes(K, h->s_bf16 ? 2 : 4);
+        if (smem > (size_t)smem_limit || batched_tmem_cols(K, maxL) > 512) { delete h; return HAP_EUNSUPPORTED; }
+        cudaError_t fa = K == 4
+            ? cudaFuncSetAttribute(h->s_bf16 ? (const void*)rowpass_batched_kernel<__nv_bfloat16, 4>
+                                             : (const void*)rowpass_batched_kernel<float, 4>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+            : cudaFuncSetAttribute(h->s_bf16 ? (const void*)rowpass_batched_kernel<__nv_bfloat16, 2>
+                                             : (const void*)rowpass_batched_kernel<float, 2>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (fa != cudaSuccess) {
+            cudaGetLastError();
+            delete h;
+            return HAP_ECUDA;
+        }
     }
     h->grid = sms;
     // workspace: per instance A, R, S, 8 vectors (the partial rows are sized
@@ -971,43 +990,59 @@ int hap_batch_get_state(hap_batch* h, int b, float* A, float* R, float* vecs, in
     return HAP_OK;
 }
 
-// Autotuner: times one steady-state iteration (CUDA events) for each
-// scheduling granularity in {2, 4, 6, 8, 12, 16} items per CTA (finer items
-// balance the dynamic claiming better but cost a CTA barrier, TMEM
-// zeroing and partial rows each) and keeps the fastest; the messages are
-// reset to Algorithm 1's start afterwards.
+// Autotuner: times one steady-state iteration (CUDA events) for every tile
+// width (16 columns per thread and 8192-element steps in a 2-stage ring, or 8
+// columns and 4096-element steps in a 4-stage ring: narrow rows fill the
+// small steps, e.g. 16 rows of 256 columns, where they fill half a large one)
+// and every scheduling granularity in {2, 4, 6, 8, 12, 16} items per CTA
+// (finer items balance the dynamic claiming better but cost a CTA barrier,
+// TMEM zeroing and partial rows each), and keeps the fastest pair; the
+// messages are reset to Algorithm 1's start afterwards.
 int hap_batch_tune(hap_batch* h, double* best_ms) {
     if (!h) return HAP_EINVAL;
     const int cands[6] = {2, 4, 6, 8, 12, 16};
     double best = 1e30;
-    int best_c = h->items_per_cta;
+    int best_c = h->items_per_cta, best_k = h->K;
     cudaEvent_t e0, e1;
     BCU(cudaEventCreate(&e0));
     BCU(cudaEventCreate(&e1));
-    for (int c : cands) {
-        h->items_per_cta = c;
-        int rc = schedule(h);
-        if (rc) return rc;
-        rc = batch_reset(h);
-        if (rc) return rc;
-        BCU(launch_batched_iteration(h, 0, 0, 0, h->stream));  // warm-up (t = 1)
-        BCU(cudaEventRecord(e0, h->stream));
-        for (int r = 0; r < 3; ++r) BCU(launch_batched_iteration(h, 1, h->opt.c_mode == HAP_C_PAPER, 1, h->stream));
-        BCU(cudaEventRecord(e1, h->stream));
-        BCU(cudaEventSynchronize(e1));
-        float ms = 0.f;
-        BCU(cudaEventElapsedTime(&ms, e0, e1));
-        if (ms / 3 < best) {
-            best = ms / 3;
-            best_c = c;
+    for (int K : {4, 2}) {
+        if (set_tile(h, K) != HAP_OK) continue;
+        for (int c : cands) {
+            h->items_per_cta = c;
+            int rc = schedule(h);
+            if (rc) return rc;
+            rc = batch_reset(h);
+            if (rc) return rc;
+            BCU(launch_batched_iteration(h, 0, 0, 0, h->stream));  // warm-up (t = 1)
+            BCU(cudaEventRecord(e0, h->stream));
+            for (int r = 0; r < 3; ++r) BCU(launch_batched_iteration(h, 1, h->opt.c_mode == HAP_C_PAPER, 1, h->stream));
+            BCU(cudaEventRecord(e1, h->stream));
+            BCU(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            BCU(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms / 3 < best) {
+                best = ms / 3;
+                best_c = c;
+                best_k = K;
+            }
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    int rc = set_tile(h, best_k);
     h->items_per_cta = best_c;
-    int rc = schedule(h);
+    if (!rc) rc = schedule(h);
     if (!rc) rc = batch_reset(h);
     if (best_ms) *best_ms = best;
+    return rc;
+}
+
+int hap_batch_set_tile(hap_batch* h, int elems_per_thread) {
+    if (!h || (elems_per_thread != 16 && elems_per_thread != 8)) return HAP_EINVAL;
+    int rc = set_tile(h, elems_per_thread / 4);
+    if (!rc) rc = schedule(h);
+    if (!rc) rc = batch_reset(h);
     return rc;
 }
 
@@ -1018,6 +1053,7 @@ int hap_batch_query(hap_batch* h, int key, int64_t* value) {
         case HAP_Q_LAUNCHES: *value = h->launches; return HAP_OK;
         case HAP_Q_GRID_CLUSTERS: *value = h->grid; return HAP_OK;
         case HAP_Q_BATCH_ITEMS_PER_CTA: *value = h->items_per_cta; return HAP_OK;
+        case HAP_Q_ELEMS_PER_THREAD: *value = 4 * h->K; return HAP_OK;
         default: return HAP_EINVAL;
     }
 }

@@ -14,11 +14,11 @@ HAP_DEV float alpha_now(float a, float r, float b, bool diag, bool pending, floa
 // Eq. 2.8: one CTA per (l, i), argmax_j(alpha + rho) with the lowest index on ties.
 __global__ void exemplars_kernel(const float* __restrict__ A, const float* __restrict__ R,
                                  const float* __restrict__ b, int pending, float lam, float oml,
-                                 int64_t N, int64_t ld, int32_t* __restrict__ e) {
+                                 int64_t N, int64_t ld, int64_t NR, int64_t R0, int32_t* __restrict__ e) {
     __shared__ float sv[32];
     __shared__ int si[32];
-    const int64_t rowid = blockIdx.x;  // l * N + i
-    const int64_t l = rowid / N, i = rowid - l * N;
+    const int64_t rowid = blockIdx.x;  // l * NR + (i - R0): rows R0 .. R0 + NR - 1 are held
+    const int64_t l = rowid / NR, i = R0 + rowid - l * NR;
     const float* Ar = A + rowid * ld;
     const float* Rr = R + rowid * ld;
     const float* bl = b + l * ld;
@@ -55,9 +55,10 @@ __global__ void exemplars_kernel(const float* __restrict__ A, const float* __res
 // alpha of the current iteration into a dense [L][N][N] buffer.
 __global__ void materialize_A_kernel(float* __restrict__ dst, const float* __restrict__ A,
                                      const float* __restrict__ R, const float* __restrict__ b,
-                                     int pending, float lam, float oml, int64_t N, int64_t ld) {
+                                     int pending, float lam, float oml, int64_t N, int64_t ld, int64_t NR,
+                                     int64_t R0) {
     const int64_t rowid = blockIdx.x;
-    const int64_t l = rowid / N, i = rowid - l * N;
+    const int64_t l = rowid / NR, i = R0 + rowid - l * NR;
     for (int64_t j = threadIdx.x; j < N; j += blockDim.x) {
         const float a = A[rowid * ld + j], r = R[rowid * ld + j];
         dst[rowid * N + j] = alpha_now(a, r, pending ? b[l * ld + j] : 0.f, j == i, pending != 0, lam, oml);
@@ -204,17 +205,19 @@ __global__ void __launch_bounds__(256) sbuild_f32_kernel(const float* __restrict
 // ---------------------------------------------------------------------------
 cudaError_t launch_exemplars(const float* A, const float* R, const float* b, int pending,
                              float lam, float oml, int64_t N, int64_t ld, int L,
-                             int32_t* e, cudaStream_t st) {
+                             int32_t* e, cudaStream_t st, int64_t nrows, int64_t row0) {
     int threads = 256;
     if (N <= 1024) threads = 128;
-    exemplars_kernel<<<(unsigned)(L * N), threads, 0, st>>>(A, R, b, pending, lam, oml, N, ld, e);
+    const int64_t NR = nrows ? nrows : N;
+    exemplars_kernel<<<(unsigned)(L * NR), threads, 0, st>>>(A, R, b, pending, lam, oml, N, ld, NR, row0, e);
     return cudaGetLastError();
 }
 
 cudaError_t launch_materialize_A(float* dst, const float* A, const float* R, const float* b,
                                  int pending, float lam, float oml, int64_t N, int64_t ld, int L,
-                                 cudaStream_t st) {
-    materialize_A_kernel<<<(unsigned)(L * N), 256, 0, st>>>(dst, A, R, b, pending, lam, oml, N, ld);
+                                 cudaStream_t st, int64_t nrows, int64_t row0) {
+    const int64_t NR = nrows ? nrows : N;
+    materialize_A_kernel<<<(unsigned)(L * NR), 256, 0, st>>>(dst, A, R, b, pending, lam, oml, N, ld, NR, row0);
     return cudaGetLastError();
 }
 
@@ -233,8 +236,8 @@ cudaError_t launch_acceptance(const int32_t* e, int64_t N, int L, long long* out
 }
 
 cudaError_t launch_copy_similarity(void* dst, int dst_bf16, int64_t ld, const void* src,
-                                   int src_bf16, int64_t ld_src, int64_t N, cudaStream_t st) {
-    const unsigned grid = (unsigned)N;
+                                   int src_bf16, int64_t ld_src, int64_t N, cudaStream_t st, int64_t nrows) {
+    const unsigned grid = (unsigned)(nrows ? nrows : N);
     if (dst_bf16 && src_bf16)
         copy_similarity_kernel<<<grid, 256, 0, st>>>(static_cast<__nv_bfloat16*>(dst), ld, static_cast<const __nv_bfloat16*>(src), ld_src, N);
     else if (dst_bf16)

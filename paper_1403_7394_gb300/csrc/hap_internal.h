@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "hap.h"
+
 namespace hap {
 
 // Status-word bits written by kernels (the host maps them to HAP_E* codes).
@@ -39,6 +41,12 @@ struct RowPassArgs {
     float kappa = 0.f;     // Eq. 2.7 level-wise similarity update (0 = off; shared S only)
     uint64_t wait_ns = 2000000000ull;  // limit of every bounded wait of the row pass
     int debug = 0;         // 1: index checks that record ST_BOUNDS (see hap_options.debug_bounds)
+    // Row band: A, R and S hold rows row0 .. row0 + nrows - 1 of an N-point
+    // problem ([L][nrows][ld], [nrows][ld]); the [L][ld] vectors keep global
+    // indices.  nrows = 0: every row (row0 = 0).  Bands take the band
+    // instances of the kernel (no debug_bounds checks there).
+    int64_t row0 = 0;
+    int64_t nrows = 0;
 };
 
 struct LaunchShape {
@@ -56,6 +64,8 @@ struct LaunchShape {
 cudaError_t launch_rowpass(const RowPassArgs& a, const LaunchShape& sh, int s_bf16, cudaStream_t st);
 // the same with the debug_bounds index checks compiled in (hap_rowpass_dbg.cu)
 cudaError_t launch_rowpass_checked(const RowPassArgs& a, const LaunchShape& sh, int s_bf16, cudaStream_t st);
+// the same over a band of rows (a.nrows > 0; hap_rowpass_band.cu)
+cudaError_t launch_rowpass_band(const RowPassArgs& a, const LaunchShape& sh, int s_bf16, cudaStream_t st);
 cudaError_t rowpass_max_clusters(const LaunchShape& sh, int L, int s_bf16, int* max_clusters);
 cudaError_t rowpass_blocks_per_sm(const LaunchShape& sh, int L, int s_bf16, int* blocks);
 size_t rowpass_smem_bytes(const LaunchShape& sh, int L, int s_bf16);
@@ -98,12 +108,36 @@ cudaError_t launch_gs_availability(const GsArgs& a, int s_bf16, cudaStream_t st)
 cudaError_t launch_prepare_from_R(const float* R, int G, int L, int64_t N, int64_t ld,
                                   float* rdiag, float* tpart, cudaStream_t st);
 
+// Row bands (hap_band_*).  band_summary: the band's exchange buffer
+// xch [4][L][ld] = (P_j of the band's rows summed over its G cluster partials
+// in the column-statistics order, then c, phi and rho_jj of the band's own
+// rows j in [row0, row0 + nrows), zero elsewhere).
+cudaError_t launch_band_summary(const float* partials, int G, int L, int64_t N, int64_t ld, const float* c,
+                                const float* phi, const float* rdiag, int64_t row0, int64_t nrows, float* xch,
+                                cudaStream_t st);
+// band_columns: from every band's exchange buffer (xch_all [P][4][L][ld], in
+// band order; band r owns rows [bounds[r], bounds[r+1])): P_j summed in band
+// order, c, phi, rho_jj taken from the band that owns j; writes the full c,
+// phi, rdiag vectors, b = c + phi + rho_jj + P and tau's column part.
+constexpr int kMaxBands = 64;
+struct BandBounds {
+    int64_t lo[kMaxBands + 1];
+};
+cudaError_t launch_band_columns(const float* xch_all, int P, const BandBounds& bb, int L, int64_t N, int64_t ld,
+                                float* c, float* phi, float* rdiag, float* b, float* tpart, cudaStream_t st);
+// Launch shape of a context or band with nrows rows of an N-point problem;
+// option checks shared by both.
+int plan_shape(int64_t N, int64_t nrows, int L, const hap_options& o, LaunchShape* sh);
+int check_options(const hap_options& o);
+
+// nrows / row0 (band contexts): A, R and e hold rows row0 .. row0 + nrows - 1
+// of the N-point problem; nrows = 0 means all N rows.
 cudaError_t launch_exemplars(const float* A, const float* R, const float* b, int pending,
                              float lam, float oml, int64_t N, int64_t ld, int L,
-                             int32_t* e, cudaStream_t st);
+                             int32_t* e, cudaStream_t st, int64_t nrows = 0, int64_t row0 = 0);
 cudaError_t launch_materialize_A(float* dst, const float* A, const float* R, const float* b,
                                  int pending, float lam, float oml, int64_t N, int64_t ld, int L,
-                                 cudaStream_t st);
+                                 cudaStream_t st, int64_t nrows = 0, int64_t row0 = 0);
 // out: [2][L] counts, self-consistent points then exemplars per level
 cudaError_t launch_acceptance(const int32_t* e, int64_t N, int L, long long* out, cudaStream_t st);
 cudaError_t launch_netsim(const void* S, int s_bf16, int64_t s_level_stride, const float* pref,
@@ -114,8 +148,9 @@ cudaError_t launch_netsim(const void* S, int s_bf16, int64_t s_level_stride, con
 // `levels` matrices ([levels][N][ld], level stride N*ld) is not finite.
 cudaError_t launch_check_finite(const void* S, int s_bf16, int levels, int64_t N, int64_t ld, unsigned* status,
                                 cudaStream_t st);
+// nrows rows (0: N) of N similarities each
 cudaError_t launch_copy_similarity(void* dst, int dst_bf16, int64_t ld, const void* src,
-                                   int src_bf16, int64_t ld_src, int64_t N, cudaStream_t st);
+                                   int src_bf16, int64_t ld_src, int64_t N, cudaStream_t st, int64_t nrows = 0);
 cudaError_t launch_read_similarity(float* dst, const void* S, int s_bf16, const float* pref_l,
                                    int64_t N, int64_t ld, cudaStream_t st);
 cudaError_t launch_sbuild_f32(const float* X, int64_t N, int64_t d, void* S, int s_bf16,

@@ -120,6 +120,67 @@ __global__ void prepare_from_R_kernel(const float* __restrict__ R, int G, int L,
     if (l + 1 < L) tpart[(int64_t)(l + 1) * ld + j] = __fadd_rn(rd, P);
 }
 
+// Row bands.  The column statistics of a row-partitioned problem (§3: the
+// availability job keys its messages by column, so it needs every row's
+// responsibilities of that column) are exchanged once per iteration: each band
+// contributes its rows' part of P_j, summed over its cluster partials in the
+// order colstats_kernel uses, and the c, phi and rho_jj of the rows it owns.
+__global__ void __launch_bounds__(32 * kChunks) band_summary_kernel(
+    const float* __restrict__ partials, int G, int L, int64_t N, int64_t ld, const float* __restrict__ c,
+    const float* __restrict__ phi, const float* __restrict__ rdiag, int64_t row0, int64_t nrows,
+    float* __restrict__ xch) {
+    __shared__ float red[kChunks][32];
+    const int x = threadIdx.x, w = threadIdx.y;
+    const int64_t idx = (int64_t)blockIdx.x * 32 + x;
+    const bool valid = idx < (int64_t)L * N;
+    const int l = valid ? (int)(idx / N) : 0;
+    const int64_t j = valid ? idx - (int64_t)l * N : 0;
+    float acc = 0.f;
+    if (valid) {
+        const float* pp = partials + (int64_t)l * ld + j;
+        const int64_t gstride = (int64_t)L * ld;
+        const int q1 = chunk_lo(w + 1, G);
+        for (int q = chunk_lo(w, G); q < q1; ++q) acc = __fadd_rn(acc, pp[q * gstride]);
+    }
+    red[w][x] = acc;
+    __syncthreads();
+    if (w != 0 || !valid) return;
+    float P = red[0][x];
+#pragma unroll
+    for (int u = 1; u < kChunks; ++u) P = __fadd_rn(P, red[u][x]);
+    const int64_t v = (int64_t)l * ld + j, part = (int64_t)L * ld;
+    const bool own = j >= row0 && j < row0 + nrows;
+    xch[v] = P;
+    xch[part + v] = own ? c[v] : 0.f;
+    xch[2 * part + v] = own ? phi[v] : 0.f;
+    xch[3 * part + v] = own ? rdiag[v] : 0.f;
+}
+
+// Every band's exchange buffer in, the column statistics of the whole problem
+// out: P_j summed in band order (the same bits on every band), c, phi and
+// rho_jj from the band owning column j; b and tau's column part as in
+// colstats_kernel.
+__global__ void band_columns_kernel(const float* __restrict__ xch_all, int P, const BandBounds bb, int L,
+                                    int64_t N, int64_t ld, float* __restrict__ c, float* __restrict__ phi,
+                                    float* __restrict__ rdiag, float* __restrict__ b, float* __restrict__ tpart) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)L * N) return;
+    const int l = (int)(idx / N);
+    const int64_t j = idx - (int64_t)l * N;
+    const int64_t v = (int64_t)l * ld + j, part = (int64_t)L * ld, band = 4 * part;
+    float Ps = xch_all[v];
+    for (int r = 1; r < P; ++r) Ps = __fadd_rn(Ps, xch_all[r * band + v]);
+    int o = 0;
+    while (o + 1 < P && j >= bb.lo[o + 1]) ++o;
+    const float* own = xch_all + o * band;
+    const float cv = own[part + v], ph = own[2 * part + v], rd = own[3 * part + v];
+    c[v] = cv;
+    phi[v] = ph;
+    rdiag[v] = rd;
+    b[v] = __fadd_rn(__fadd_rn(__fadd_rn(cv, ph), rd), Ps);
+    if (l + 1 < L) tpart[v + ld] = __fadd_rn(rd, Ps);
+}
+
 template <typename ST, int K, int MAXT, int NST, bool TM>
 static cudaError_t max_clusters_one(const LaunchShape& sh, int L, int* out) {
     cudaLaunchConfig_t cfg = {};
@@ -166,6 +227,7 @@ cudaError_t launch_fill_alpha_padding(float* A, int64_t rows, int64_t N, int64_t
 }
 
 cudaError_t launch_rowpass(const RowPassArgs& a, const LaunchShape& sh, int s_bf16, cudaStream_t st) {
+    if (a.nrows) return launch_rowpass_band(a, sh, s_bf16, st);
     if (a.debug) return launch_rowpass_checked(a, sh, s_bf16, st);
     HAP_ROWPASS_DISPATCH(launch_plain, a, sh, st);
 }
@@ -184,6 +246,23 @@ cudaError_t launch_colstats(const float* partials, int G, int L, int64_t N, int6
     const int64_t total = (int64_t)L * N;
     const unsigned blocks = (unsigned)((total + 31) / 32);
     colstats_kernel<<<blocks, dim3(32, kChunks), 0, st>>>(partials, G, L, N, ld, c, phi, rdiag, b, tpart, tp_level);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_band_summary(const float* partials, int G, int L, int64_t N, int64_t ld, const float* c,
+                                const float* phi, const float* rdiag, int64_t row0, int64_t nrows, float* xch,
+                                cudaStream_t st) {
+    const int64_t total = (int64_t)L * N;
+    const unsigned blocks = (unsigned)((total + 31) / 32);
+    band_summary_kernel<<<blocks, dim3(32, kChunks), 0, st>>>(partials, G, L, N, ld, c, phi, rdiag, row0, nrows, xch);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_band_columns(const float* xch_all, int P, const BandBounds& bb, int L, int64_t N, int64_t ld,
+                                float* c, float* phi, float* rdiag, float* b, float* tpart, cudaStream_t st) {
+    const int64_t total = (int64_t)L * N;
+    const unsigned blocks = (unsigned)((total + 255) / 256);
+    band_columns_kernel<<<blocks, 256, 0, st>>>(xch_all, P, bb, L, N, ld, c, phi, rdiag, b, tpart);
     return cudaGetLastError();
 }
 

@@ -1,8 +1,9 @@
 // The fused row-pass kernel template (see hap_rowpass.cu for the schedule)
 // and its launch helpers, shared by the translation units that instantiate
-// it: hap_rowpass.cu (the kernels every iteration runs) and hap_rowpass_dbg.cu
+// it: hap_rowpass.cu (the kernels every iteration runs), hap_rowpass_dbg.cu
 // (the debug_bounds variants, whose index checks are compiled in only there,
-// so the kernels without them carry no dead branch).
+// so the kernels without them carry no dead branch) and hap_rowpass_band.cu
+// (the row-band variants, whose row offset is likewise compiled in only there).
 #pragma once
 
 #include "hap_common.cuh"
@@ -44,7 +45,9 @@ HAP_DEV float4 load_s_smem<__nv_bfloat16>(const __nv_bfloat16* p) {
     return SVec<__nv_bfloat16>::to_f4(*reinterpret_cast<const uint2*>(p));
 }
 
-template <typename ST, int K, int MAXT, int NST, bool TM, bool DBG>
+// BAND: A, R and S hold a band of rows (RowPassArgs::row0 / nrows); the other
+// instances have row0 = 0 and nrows = N folded in at compile time.
+template <typename ST, int K, int MAXT, int NST, bool TM, bool DBG, bool BAND = false>
 __global__ void __launch_bounds__(MAXT, 1) rowpass_kernel(const RowPassArgs p) {
     static_assert(!TM || K == 2 || K == 4, "TMEM column sums use 8 or 16 columns per thread");
     extern __shared__ __align__(128) unsigned char sm[];
@@ -52,7 +55,9 @@ __global__ void __launch_bounds__(MAXT, 1) rowpass_kernel(const RowPassArgs p) {
     const unsigned C = cluster_nctarank(), rank = cluster_ctarank();
     const unsigned g = cluster_id_x(), G = cluster_count_x();
     const int L = p.L;
-    const int N = (int)p.N;
+    const int N = (int)p.N;                            // columns (points)
+    const int NR = BAND ? (int)p.nrows : N;            // rows held: R0 .. R0 + NR - 1
+    const int R0 = BAND ? (int)p.row0 : 0;
     const int64_t ld = p.ld;
     const float lam = p.lam, oml = p.oml;
     const bool pending = p.pending != 0;
@@ -102,7 +107,7 @@ __global__ void __launch_bounds__(MAXT, 1) rowpass_kernel(const RowPassArgs p) {
         for (int ll = 0; ll < L; ++ll) tmem_store<4 * K>(tacc + (uint32_t)(ll * 4 * K), z);
     }
 
-    const int my_rows = N > (int)g ? (N - 1 - (int)g) / (int)G + 1 : 0;
+    const int my_rows = NR > (int)g ? (NR - 1 - (int)g) / (int)G + 1 : 0;
     const int nsteps = my_rows * L;
 
     // One elected thread streams the A, R (and, when needed, S) row slices of
@@ -113,14 +118,14 @@ __global__ void __launch_bounds__(MAXT, 1) rowpass_kernel(const RowPassArgs p) {
         const uint32_t bar = bar0 + 8 * st;
         const uint32_t dst = sm0 + (uint32_t)(st * stage_bytes);
         const uint32_t bytes = (uint32_t)slice_len * (8u + (load_s ? (uint32_t)sizeof(ST) : 0u));
-        const int64_t off = ((int64_t)l * N + row) * ld + slice0;
+        const int64_t off = ((int64_t)l * NR + row) * ld + slice0;
         // debug variant: the copied slices must lie inside the messages; a
         // failed check is recorded and the copy skipped (the stage then
         // completes with no bytes)
-        const bool in_bounds = !DBG || slice_len == 0 || (row < N && slice0 + slice_len <= ld &&
-                                            off + slice_len <= (int64_t)L * N * ld &&
+        const bool in_bounds = !DBG || slice_len == 0 || (row < NR && slice0 + slice_len <= ld &&
+                                            off + slice_len <= (int64_t)L * NR * ld &&
                                             (int64_t)(s_each_level ? l : 0) * p.s_level_stride + (int64_t)row * ld +
-                                                    slice0 + slice_len <= (s_each_level ? (int64_t)L : 1) * N * ld);
+                                                    slice0 + slice_len <= (s_each_level ? (int64_t)L : 1) * NR * ld);
         if (!in_bounds) atomicOr(p.status, ST_BOUNDS);
         mbar_arrive_expect_tx(bar, in_bounds ? bytes : 0u);
         if (slice_len > 0 && in_bounds) {
@@ -148,14 +153,15 @@ __global__ void __launch_bounds__(MAXT, 1) rowpass_kernel(const RowPassArgs p) {
     float4 nb[K];
     float npref = 0.f, nc = 0.f, ntp = 0.f, ntau = kInf;
     auto prefetch = [&](int prow, int pl) {
-        const int64_t pv = (int64_t)pl * ld;
+        const int64_t pv = (int64_t)pl * ld;  // level pl of a [L][ld] vector: b by column,
+        const int64_t pr = pv + R0 + prow;    // the row scalars at the row's index in the problem
 #pragma unroll
         for (int k = 0; k < K; ++k)
             nb[k] = (pending && ok[k]) ? __ldg(reinterpret_cast<const float4*>(p.b + pv + col[k])) : f4_splat(0.f);
-        npref = __ldg(p.pref + pv + prow);
-        nc = p.update_c ? 0.f : p.c[pv + prow];
-        ntp = (p.use_tau && pl > 0) ? __ldg(p.tpart + pv + prow) : 0.f;
-        if (p.tau_in) ntau = p.tau_in[pv + prow];
+        npref = __ldg(p.pref + pr);
+        nc = p.update_c ? 0.f : p.c[pr];
+        ntp = (p.use_tau && pl > 0) ? __ldg(p.tpart + pr) : 0.f;
+        if (p.tau_in) ntau = p.tau_in[pr];
     };
     if (nsteps > 0) prefetch(row, 0);
 
@@ -170,8 +176,9 @@ __global__ void __launch_bounds__(MAXT, 1) rowpass_kernel(const RowPassArgs p) {
         if (tid == 0) consumed = s + 1;
 
         const bool new_s = s_each_level || l == 0;
+        const int grow = R0 + row;  // this row's index in the problem (its diagonal column)
         const int64_t voff = (int64_t)l * ld;
-        const int64_t off = ((int64_t)l * N + row) * ld;
+        const int64_t off = ((int64_t)l * NR + row) * ld;
         float4 bcur[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) bcur[k] = nb[k];
@@ -204,7 +211,7 @@ __global__ void __launch_bounds__(MAXT, 1) rowpass_kernel(const RowPassArgs p) {
                 an.z = damp(a4.z, avail_target(b4.z, r4.z, false), lam, oml);
                 an.w = damp(a4.w, avail_target(b4.w, r4.w, false), lam, oml);
             }
-            const int dd = row - col[k];
+            const int dd = grow - col[k];
             if ((unsigned)dd < 4u) {  // this float4 holds the diagonal element
                 f4_set(s4, dd, pref_i);
                 if (pending) f4_set(an, dd, damp(f4_get(a4, dd), avail_target(f4_get(b4, dd), f4_get(r4, dd), true), lam, oml));
@@ -262,9 +269,9 @@ __global__ void __launch_bounds__(MAXT, 1) rowpass_kernel(const RowPassArgs p) {
         const float tauv = p.tau_in ? tau_given : (p.use_tau && l > 0) ? __fadd_rn(c_prev, tpart_i) : kInf;
         c_prev = cval;
         if (rank == 0 && tid == 0 && !bad) {
-            if (p.update_c) p.c[voff + row] = cval;
-            p.tau[voff + row] = tauv;
-            if (l > 0) p.phi[voff - ld + row] = m1;
+            if (p.update_c) p.c[voff + grow] = cval;
+            p.tau[voff + grow] = tauv;
+            if (l > 0) p.phi[voff - ld + grow] = m1;
         }
 
         // ---- pass 2: responsibilities (Eq. 2.1) and column sums -----------------
@@ -279,10 +286,10 @@ __global__ void __launch_bounds__(MAXT, 1) rowpass_kernel(const RowPassArgs p) {
             rn.z = damp(r4.z, __fadd_rn(s4.z, fminf(tauv, -(dk == 2 ? m2 : m1))), lam, oml);
             rn.w = damp(r4.w, __fadd_rn(s4.w, fminf(tauv, -(dk == 3 ? m2 : m1))), lam, oml);
             float4 add = make_float4(fmaxf(rn.x, 0.f), fmaxf(rn.y, 0.f), fmaxf(rn.z, 0.f), fmaxf(rn.w, 0.f));
-            const int dd = row - col[k];
+            const int dd = grow - col[k];
             if ((unsigned)dd < 4u) {
                 f4_set(add, dd, 0.f);
-                if (!bad) p.rdiag[voff + row] = f4_get(rn, dd);
+                if (!bad) p.rdiag[voff + grow] = f4_get(rn, dd);
             }
             if (ok[k] && !bad) st_stream(p.R + off + col[k], rn);
             if constexpr (TM) {
@@ -348,9 +355,9 @@ __global__ void __launch_bounds__(MAXT, 1) rowpass_kernel(const RowPassArgs p) {
     if (C > 1) cluster_barrier();
 }
 
-template <typename ST, int K, int MAXT, int NST, bool TM, bool DBG>
+template <typename ST, int K, int MAXT, int NST, bool TM, bool DBG, bool BAND = false>
 cudaError_t cluster_config(const LaunchShape& sh, int L, cudaLaunchConfig_t* cfg, cudaLaunchAttribute* attr) {
-    auto kern = rowpass_kernel<ST, K, MAXT, NST, TM, DBG>;
+    auto kern = rowpass_kernel<ST, K, MAXT, NST, TM, DBG, BAND>;
     const size_t smem = rowpass_smem_bytes(sh, L, sizeof(ST) == 2);
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
@@ -369,15 +376,15 @@ cudaError_t cluster_config(const LaunchShape& sh, int L, cudaLaunchConfig_t* cfg
     return cudaSuccess;
 }
 
-template <typename ST, int K, int MAXT, int NST, bool TM, bool DBG>
+template <typename ST, int K, int MAXT, int NST, bool TM, bool DBG, bool BAND = false>
 cudaError_t launch_one(const RowPassArgs& a, const LaunchShape& sh, cudaStream_t st) {
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
-    cudaError_t err = cluster_config<ST, K, MAXT, NST, TM, DBG>(sh, a.L, &cfg, attr);
+    cudaError_t err = cluster_config<ST, K, MAXT, NST, TM, DBG, BAND>(sh, a.L, &cfg, attr);
     if (err != cudaSuccess) return err;
     cfg.gridDim = dim3((unsigned)(sh.G * sh.C), 1, 1);
     cfg.stream = st;
-    return cudaLaunchKernelEx(&cfg, rowpass_kernel<ST, K, MAXT, NST, TM, DBG>, a);
+    return cudaLaunchKernelEx(&cfg, rowpass_kernel<ST, K, MAXT, NST, TM, DBG, BAND>, a);
 }
 
 template <typename ST, int K, int MAXT, int NST, bool TM>
@@ -387,6 +394,10 @@ cudaError_t launch_plain(const RowPassArgs& a, const LaunchShape& sh, cudaStream
 template <typename ST, int K, int MAXT, int NST, bool TM>
 cudaError_t launch_checked(const RowPassArgs& a, const LaunchShape& sh, cudaStream_t st) {
     return launch_one<ST, K, MAXT, NST, TM, true>(a, sh, st);
+}
+template <typename ST, int K, int MAXT, int NST, bool TM>
+cudaError_t launch_band(const RowPassArgs& a, const LaunchShape& sh, cudaStream_t st) {
+    return launch_one<ST, K, MAXT, NST, TM, false, true>(a, sh, st);
 }
 
 // Instantiated shapes: shared-memory sums with 4, 8 or 16 columns per thread

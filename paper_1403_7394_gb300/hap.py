@@ -73,6 +73,7 @@ def _load():
         "hap_batch_net_similarity": (i32, [vp, vp]),
         "hap_batch_get_state": (i32, [vp, i32, vp, vp, vp, ctypes.POINTER(i64)]),
         "hap_batch_tune": (i32, [vp, ctypes.POINTER(ctypes.c_double)]),
+        "hap_batch_set_tile": (i32, [vp, i32]),
         "hap_batch_query": (i32, [vp, i32, ctypes.POINTER(i64)]),
         "hap_batch_sync": (i32, [vp]),
         "hap_knn": (i32, [vp, i64, i64, i32, vp, vp, vp]),
@@ -108,6 +109,17 @@ def _load():
         "hap_sparse_profile_times": (i32, [vp, vp, ctypes.POINTER(i64), i32]),
         "hap_net_similarity_points": (i32, [vp, i64, i64, i32, vp, vp, vp, vp]),
         "hap_noalloc_scratch_bytes": (ctypes.c_size_t, []),
+        "hap_band_create": (i32, [i64, i64, i64, i32, vp, f32, ctypes.POINTER(HapOptions), ctypes.POINTER(vp)]),
+        "hap_band_destroy": (None, [vp]),
+        "hap_band_set_stream": (i32, [vp, vp]),
+        "hap_band_set_similarity": (i32, [vp, vp, i64, i32]),
+        "hap_band_exchange_floats": (i32, [vp, ctypes.POINTER(i64)]),
+        "hap_band_rows": (i32, [vp, vp]),
+        "hap_band_columns": (i32, [vp, vp, i32, vp]),
+        "hap_band_get_state": (i32, [vp, vp, vp, vp, ctypes.POINTER(i64)]),
+        "hap_band_exemplars": (i32, [vp, vp, i32]),
+        "hap_band_sync": (i32, [vp]),
+        "hap_band_query": (i32, [vp, i32, ctypes.POINTER(i64)]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(lib, name)
@@ -410,6 +422,14 @@ class HAPBatch:
         check(lib.hap_batch_tune(self._h, ctypes.byref(ms)), "hap_batch_tune")
         return ms.value
 
+    def set_tile(self, elems_per_thread: int):
+        """Columns per thread of the row pass (16 or 8); resets the messages."""
+        check(lib.hap_batch_set_tile(self._h, int(elems_per_thread)), "hap_batch_set_tile")
+
+    @property
+    def tile(self) -> dict:
+        return {"elems_per_thread": self.query(Q_ELEMS_PER_THREAD), "items_per_cta": self.query(Q_BATCH_ITEMS_PER_CTA)}
+
     def exemplars(self, out: torch.Tensor | None = None):
         """List of int32 (L[b], N[b]) tensors (views of one flat buffer)."""
         total = sum(n * l for n, l in zip(self.N, self.L))
@@ -707,3 +727,136 @@ class HAPSparse:
         check(lib.hap_sparse_get_state(self._h, _ptr(A), _ptr(R), _ptr(vecs), ctypes.byref(it)), "hap_sparse_get_state")
         self.stream.synchronize()
         return {"A": A, "R": R, "c": vecs[0], "tau": vecs[1], "phi": vecs[2], "t": it.value}
+
+
+class HAPBand:
+    """Rows row0 .. row0 + nrows - 1 of an N-point HAP problem (the row
+    partition of §3).  One iteration is ``rows(xch)`` on every band, then
+    ``columns(xch_all, bounds)`` on every band with all bands' exchange
+    buffers in band order: an all-gather of ``xch`` between devices, or, for
+    bands on one device, each band writing straight into its slot of one
+    ``(P, 4, L, ld)`` tensor (``BandGroup``)."""
+
+    def __init__(self, N: int, row0: int, nrows: int, L: int, prefs=None, damping: float = 0.5, device="cuda",
+                 stream: torch.cuda.Stream | None = None, **opt):
+        import numpy as np
+        self.N, self.row0, self.nrows, self.L = int(N), int(row0), int(nrows), int(L)
+        self.damping = float(damping)
+        self.device = torch.device(device)
+        self._opt = options(**opt)
+        p = None if prefs is None else np.ascontiguousarray(np.asarray(prefs, dtype=np.float32).reshape(self.L))
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            h = ctypes.c_void_p()
+            check(lib.hap_band_create(self.N, self.row0, self.nrows, self.L,
+                                      None if p is None else p.ctypes.data_as(ctypes.c_void_p), self.damping,
+                                      ctypes.byref(self._opt), ctypes.byref(h)), "hap_band_create")
+            self._h = h
+            check(lib.hap_band_set_stream(self._h, ctypes.c_void_p(self.stream.cuda_stream)), "hap_band_set_stream")
+        n = ctypes.c_int64(0)
+        check(lib.hap_band_exchange_floats(self._h, ctypes.byref(n)), "hap_band_exchange_floats")
+        self.exchange_floats = n.value
+        self.ld = self.query(Q_LD)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.hap_band_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_similarity(self, S_rows: torch.Tensor):
+        """S_rows: (nrows, >=N) row-major rows row0.. of the problem's S."""
+        if S_rows.device != self.device or S_rows.dim() != 2 or S_rows.shape[0] != self.nrows or \
+                S_rows.shape[1] < self.N or S_rows.stride(1) != 1:
+            raise ValueError("S_rows must be an (nrows, >=N) row-major tensor on the band's device")
+        dt = {torch.float32: 0, torch.bfloat16: 1}[S_rows.dtype]
+        self.stream.synchronize()
+        check(lib.hap_band_set_similarity(self._h, _ptr(S_rows), S_rows.stride(0), dt), "hap_band_set_similarity")
+
+    def rows(self, xch: torch.Tensor):
+        """Row pass of one iteration; writes the band's exchange buffer into
+        ``xch`` (float32, exchange_floats elements, on the band's device)."""
+        if xch.device != self.device or xch.dtype != torch.float32 or not xch.is_contiguous() or \
+                xch.numel() != self.exchange_floats:
+            raise ValueError("xch must be a contiguous float32 tensor of exchange_floats elements")
+        check(lib.hap_band_rows(self._h, _ptr(xch)), "hap_band_rows")
+
+    def columns(self, xch_all: torch.Tensor, bounds):
+        """Column statistics from every band's buffer (P, exchange_floats) in
+        band order; bounds: the P + 1 row boundaries of the bands."""
+        import numpy as np
+        b = np.ascontiguousarray(np.asarray(bounds, dtype=np.int64))
+        P = len(b) - 1
+        if xch_all.device != self.device or xch_all.dtype != torch.float32 or not xch_all.is_contiguous() or \
+                xch_all.numel() != P * self.exchange_floats:
+            raise ValueError("xch_all must be a contiguous float32 (P, exchange_floats) tensor")
+        check(lib.hap_band_columns(self._h, _ptr(xch_all), P, b.ctypes.data_as(ctypes.c_void_p)), "hap_band_columns")
+
+    def get_state(self):
+        A = torch.empty((self.L, self.nrows, self.N), dtype=torch.float32, device=self.device)
+        R = torch.empty_like(A)
+        vecs = torch.empty((3, self.L, self.N), dtype=torch.float32, device=self.device)
+        it = ctypes.c_int64(0)
+        check(lib.hap_band_get_state(self._h, _ptr(A), _ptr(R), _ptr(vecs), ctypes.byref(it)), "hap_band_get_state")
+        self.sync()
+        return {"A": A, "R": R, "c": vecs[0], "tau": vecs[1], "phi": vecs[2], "t": it.value}
+
+    def exemplars(self) -> torch.Tensor:
+        out = torch.empty((self.L, self.nrows), dtype=torch.int32, device=self.device)
+        check(lib.hap_band_exemplars(self._h, _ptr(out), 0), "hap_band_exemplars")
+        return out
+
+    def sync(self):
+        check(lib.hap_band_sync(self._h), "hap_band_sync")
+
+    def query(self, key: int) -> int:
+        v = ctypes.c_int64(0)
+        check(lib.hap_band_query(self._h, key, ctypes.byref(v)), "hap_band_query")
+        return v.value
+
+    @property
+    def launches(self) -> int:
+        return self.query(Q_LAUNCHES)
+
+
+class BandGroup:
+    """P row bands of one problem on one device, stepped together: every
+    band's row pass writes its exchange buffer straight into its slot of one
+    (P, 4, L, ld) tensor, which then feeds every band's column statistics."""
+
+    def __init__(self, N: int, L: int, bounds, prefs=None, damping: float = 0.5, device="cuda", **opt):
+        self.bounds = [int(x) for x in bounds]
+        self.N, self.L = int(N), int(L)
+        self.bands = [HAPBand(N, self.bounds[r], self.bounds[r + 1] - self.bounds[r], L, prefs, damping, device,
+                              **opt) for r in range(len(self.bounds) - 1)]
+        self.xch = torch.empty((len(self.bands), self.bands[0].exchange_floats), dtype=torch.float32,
+                               device=self.bands[0].device)
+
+    def set_similarity(self, S: torch.Tensor):
+        for r, b in enumerate(self.bands):
+            b.set_similarity(S[self.bounds[r]:self.bounds[r + 1]])
+
+    def iterate(self, n: int = 1):
+        for _ in range(int(n)):
+            for r, b in enumerate(self.bands):
+                b.rows(self.xch[r])
+            for b in self.bands:
+                b.columns(self.xch, self.bounds)
+
+    def get_state(self):
+        st = [b.get_state() for b in self.bands]
+        own = torch.cat([s["tau"][:, self.bounds[r]:self.bounds[r + 1]] for r, s in enumerate(st)], dim=1)
+        return {"A": torch.cat([s["A"] for s in st], dim=1), "R": torch.cat([s["R"] for s in st], dim=1),
+                "c": st[0]["c"], "tau": own, "phi": st[0]["phi"], "t": st[0]["t"], "per_band": st}
+
+    def exemplars(self) -> torch.Tensor:
+        return torch.cat([b.exemplars() for b in self.bands], dim=1)
+
+    def close(self):
+        for b in self.bands:
+            b.close()

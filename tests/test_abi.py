@@ -46,3 +46,7 @@ def test_host_only_calls(libpath):
     assert lib.hap_create(2, 1, None, ctypes.c_float(0.5), None, None, 0, None) == -1  # out == NULL
     assert lib.hap_iterate(None, 1) == -1
     assert lib.hap_sync(None) == -1
+    assert lib.hap_band_create(ctypes.c_int64(2), ctypes.c_int64(0), ctypes.c_int64(1), 1, None, ctypes.c_float(0.5),
+                               None, None) == -1  # out == NULL
+    assert lib.hap_band_rows(None, None) == -1
+    assert lib.hap_band_columns(None, None, 1, None) == -1

@@ -70,7 +70,7 @@ def test_batch_against_reference_and_tuner():
     for b, (_, S32, _) in enumerate(insts):
         bt.set_similarity(b, torch.from_numpy(S32).to(DEV))
     ms = bt.tune()
-    assert ms > 0 and bt.query(8) in (2, 4, 6, 8, 12, 16)
+    assert ms > 0 and bt.query(8) in (2, 4, 6, 8, 12, 16) and bt.tile["elems_per_thread"] in (8, 16)
     bt.iterate(4)
     for b, (_, S32, prefs) in enumerate(insts):
         ref = H.run(H.level_similarities(S32.astype(np.float64), prefs.astype(np.float64)), 4, 0.6, H.PAPER)
@@ -98,17 +98,22 @@ def test_batch_build_similarity_tensor_cores():
     bt.close()
 
 
-@pytest.mark.parametrize("Ns,Ls", [([2600, 3100, 1500, 40], [3, 2, 4, 2]),     # 6, 7, 3, 1 warps per row
-                                   ([700, 2000, 150], [9, 2, 10])])          # > 8 levels: 8 columns per thread
-def test_batch_row_group_shapes(Ns, Ls, report):
-    """Row groups of every width (1..8 warps) and the 8-column variant used
-    when an instance has more than 8 levels, against single-instance runs."""
+@pytest.mark.parametrize("Ns,Ls,tile", [([2600, 3100, 1500, 40], [3, 2, 4, 2], 0),     # 6, 7, 3, 1 warps per row
+                                        ([2600, 3100, 1500, 40], [3, 2, 4, 2], 8),     # 11, 13, 6, 1 at 8 columns
+                                        ([700, 2000, 150], [9, 2, 10], 0)])          # > 8 levels: 8 columns per thread
+def test_batch_row_group_shapes(Ns, Ls, tile, report):
+    """Row groups of every width (1..13 warps), at 16 and 8 columns per
+    thread (8 by hand, or because an instance has more than 8 levels),
+    against single-instance runs."""
     from paper_1403_7394_gb300 import hap
     insts = _instances(Ns, Ls, seed=40)
     bt = hap.HAPBatch(Ns, Ls, damping=0.5, device=DEV)
     bt.set_preferences([x[2] for x in insts])
     for b, (_, S32, _) in enumerate(insts):
         bt.set_similarity(b, torch.from_numpy(S32).to(DEV))
+    if tile:
+        bt.set_tile(tile)
+    assert bt.tile["elems_per_thread"] == (tile or (16 if max(Ls) <= 8 else 8))
     bt.iterate(5)
     worst = 0.0
     for b, (_, S32, prefs) in enumerate(insts):
@@ -119,7 +124,19 @@ def test_batch_row_group_shapes(Ns, Ls, report):
         worst = max(worst, max(errs.values()))
         assert all(e <= TOL for e in errs.values()), (b, errs)
         ctx.close()
-    report(worst=worst)
+    report(worst=worst, tile=bt.tile)
+    bt.close()
+
+
+def test_batch_tile_width_refused_beyond_8_levels():
+    from paper_1403_7394_gb300 import hap
+    bt = hap.HAPBatch([100, 200], [9, 2], damping=0.5, device=DEV)
+    with pytest.raises(hap.HapError) as e:
+        bt.set_tile(16)
+    assert e.value.code == hap.HAP_EUNSUPPORTED
+    with pytest.raises(hap.HapError) as e:
+        bt.set_tile(12)
+    assert e.value.code == hap.HAP_EINVAL
     bt.close()
 
 
