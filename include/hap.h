@@ -507,12 +507,12 @@ int hap_sparse_net_similarity(hap_sparse* sp, double* ns);
 int hap_sparse_get_state(hap_sparse* sp, float* A, float* R, float* vecs, int64_t* iter);
 /* keys HAP_Q_ITER and HAP_Q_LAUNCHES. */
 int hap_sparse_query(hap_sparse* sp, int key, int64_t* value);
-/* on = 1: every later iteration records CUDA events around its four steps
- * (clearing the bitmap of positive slots, the row pass, the statistics of
- * short columns, of long columns).  Host call. */
+/* on = 1: every later iteration records CUDA events around its two launches
+ * (the row pass; the column statistics, which also clear the bitmap of
+ * positive slots the next iteration fills).  Host call. */
 int hap_sparse_set_profile(hap_sparse* sp, int on);
-/* Milliseconds spent in those four steps, summed over the profiled
- * iterations since the last reset (ms: host double [4]), and their number.
+/* Milliseconds spent in those two launches, summed over the profiled
+ * iterations since the last reset (ms: host double [2]), and their number.
  * Synchronising. */
 int hap_sparse_profile_times(hap_sparse* sp, double* ms, int64_t* iterations, int reset);
 

@@ -39,7 +39,7 @@ struct SparseArgs {
     const int32_t* cand;
     const int32_t* pos;    // [N][K] CSC slot of every entry
     float* cval;           // [L][N*K] max(0, rho) in CSC order, valid where the slot's bit is set
-    unsigned* cbits;       // [L][cwords] bit e of level l set iff slot e holds a positive value; zeroed before the pass
+    unsigned* cbits;       // [L][cwords] bit e of level l set iff slot e holds a positive value; zero before the pass
     int64_t cwords;
     const float* s;
     float* A;
@@ -241,13 +241,12 @@ HAP_DEV void colstats_finish(int64_t j, int l, int L, int N, float P, const floa
     if (l + 1 < L) tpart[idx + N] = __fadd_rn(rd, P);
 }
 
-__global__ void sparse_colstats_short_kernel(const float* __restrict__ cval, const unsigned* __restrict__ cbits,
-                                             int64_t cwords, const int64_t* __restrict__ cptr,
-                                             const int32_t* __restrict__ cols, int ncols, int N, int L, int K,
-                                             const float* __restrict__ c, const float* __restrict__ phi,
-                                             const float* __restrict__ rdiag, float* __restrict__ b,
-                                             float* __restrict__ tpart) {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+// P_j of one short column (one thread, slots in order).
+HAP_DEV void colstats_short_column(int64_t t, int ncols, const float* __restrict__ cval,
+                                   const unsigned* __restrict__ cbits, int64_t cwords,
+                                   const int64_t* __restrict__ cptr, const int32_t* __restrict__ cols, int N, int L,
+                                   int K, const float* __restrict__ c, const float* __restrict__ phi,
+                                   const float* __restrict__ rdiag, float* __restrict__ b, float* __restrict__ tpart) {
     if (t >= (int64_t)L * ncols) return;
     const int l = (int)(t / ncols);
     const int64_t j = cols[t - (int64_t)l * ncols];
@@ -270,14 +269,14 @@ __global__ void sparse_colstats_short_kernel(const float* __restrict__ cval, con
     colstats_finish(j, l, L, N, P, c, phi, rdiag, b, tpart);
 }
 
-__global__ void sparse_colstats_long_kernel(const float* __restrict__ cval, const unsigned* __restrict__ cbits,
-                                            int64_t cwords, const int64_t* __restrict__ cptr,
-                                            const int32_t* __restrict__ cols, int ncols, int N, int L, int K,
-                                            const float* __restrict__ c, const float* __restrict__ phi,
-                                            const float* __restrict__ rdiag, float* __restrict__ b,
-                                            float* __restrict__ tpart) {
-    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
+// P_j of one long column (one warp): lane t sums the set slots of the
+// column's bitmap words t, t + 32, ... in slot order, four loads in flight,
+// then a fixed xor-shuffle tree.
+HAP_DEV void colstats_long_column(int64_t w, int lane, int ncols, const float* __restrict__ cval,
+                                  const unsigned* __restrict__ cbits, int64_t cwords,
+                                  const int64_t* __restrict__ cptr, const int32_t* __restrict__ cols, int N, int L,
+                                  int K, const float* __restrict__ c, const float* __restrict__ phi,
+                                  const float* __restrict__ rdiag, float* __restrict__ b, float* __restrict__ tpart) {
     if (w >= (int64_t)L * ncols) return;
     const int l = (int)(w / ncols);
     const int64_t j = cols[w - (int64_t)l * ncols];
@@ -285,14 +284,12 @@ __global__ void sparse_colstats_long_kernel(const float* __restrict__ cval, cons
     const unsigned* bits = cbits + l * cwords;
     const int64_t e0 = cptr[j], e1 = cptr[j + 1];
     float P = 0.f;
-    // lane t takes the bitmap words t, t + 32, ... of the column and adds the
-    // values of their set bits in slot order, four loads in flight
     const int64_t w0 = e0 >> 5, w1 = (e1 - 1) >> 5;
-    for (int64_t w = w0 + lane; e0 < e1 && w <= w1; w += 32) {
-        unsigned m = bits[w];
-        if (w == w0) m &= ~0u << (e0 & 31);
-        if (w == w1) m &= (2u << ((e1 - 1) & 31)) - 1u;
-        const float* vw = v + w * 32;
+    for (int64_t q = w0 + lane; e0 < e1 && q <= w1; q += 32) {
+        unsigned m = bits[q];
+        if (q == w0) m &= ~0u << (e0 & 31);
+        if (q == w1) m &= (2u << ((e1 - 1) & 31)) - 1u;
+        const float* vw = v + q * 32;
         while (m) {
             float x[4];
 #pragma unroll
@@ -306,6 +303,47 @@ __global__ void sparse_colstats_long_kernel(const float* __restrict__ cval, cons
     }
     for (int o = 16; o > 0; o >>= 1) P = __fadd_rn(P, __shfl_xor_sync(0xffffffffu, P, o));
     if (lane == 0) colstats_finish(j, l, L, N, P, c, phi, rdiag, b, tpart);
+}
+
+// The column statistics of one iteration in one launch: the first blocks sum
+// the long columns (a warp each; scheduled first, they take longest), the
+// next the short ones (a thread each), the last clear the bitmap the next
+// iteration's row pass will fill (bitmaps alternate between iterations, so
+// nothing reads it here).  The split depends only on the column's length, so
+// every sum has a fixed order.
+struct ColArgs {
+    const float* cval;
+    const unsigned* cbits;     // this iteration's bitmap [L][cwords]
+    unsigned* clear_bits;      // the next iteration's bitmap, zeroed here
+    int64_t cwords;            // words per level (a multiple of 4)
+    const int64_t* cptr;
+    const int32_t* long_cols;
+    const int32_t* short_cols;
+    int n_long, n_short, N, L, K;
+    const float* c;
+    const float* phi;
+    const float* rdiag;
+    float* b;
+    float* tpart;
+    unsigned long_blocks, short_blocks, clear_blocks;
+};
+__global__ void __launch_bounds__(256) sparse_colstats_kernel(const ColArgs p) {
+    const unsigned blk = blockIdx.x;
+    if (blk < p.long_blocks) {
+        const int64_t t = (int64_t)blk * blockDim.x + threadIdx.x;
+        colstats_long_column(t >> 5, threadIdx.x & 31, p.n_long, p.cval, p.cbits, p.cwords, p.cptr, p.long_cols, p.N,
+                             p.L, p.K, p.c, p.phi, p.rdiag, p.b, p.tpart);
+    } else if (blk < p.long_blocks + p.short_blocks) {
+        const int64_t t = (int64_t)(blk - p.long_blocks) * blockDim.x + threadIdx.x;
+        colstats_short_column(t, p.n_short, p.cval, p.cbits, p.cwords, p.cptr, p.short_cols, p.N, p.L, p.K, p.c,
+                              p.phi, p.rdiag, p.b, p.tpart);
+    } else {
+        const int64_t n4 = (int64_t)p.L * p.cwords / 4;
+        uint4* z = reinterpret_cast<uint4*>(p.clear_bits);
+        for (int64_t q = (int64_t)(blk - p.long_blocks - p.short_blocks) * blockDim.x + threadIdx.x; q < n4;
+             q += (int64_t)p.clear_blocks * blockDim.x)
+            z[q] = make_uint4(0u, 0u, 0u, 0u);
+    }
 }
 
 // Column classes: flag[j] = 1 for a long column; after the prefix sums the
@@ -482,8 +520,9 @@ struct hap_sparse {
     int32_t* cent = nullptr;
     int32_t* pos = nullptr;       // [N*K] CSC slot of every entry
     float* cval = nullptr;        // [L][N*K] max(0, rho) in CSC order
-    unsigned* cbits = nullptr;    // [L][cwords] bitmap of the positive slots
-    int64_t cwords = 0;
+    unsigned* cbits = nullptr;    // [2][L][cwords] bitmaps of the positive slots, used by alternate iterations
+    int64_t cwords = 0;           // words per level, a multiple of 4
+    int bm = 0;                   // the bitmap the next row pass fills
     int32_t* tmp[4] = {nullptr, nullptr, nullptr, nullptr};  // radix-sort key / value buffers
     int* cnt = nullptr;           // [N + 1] column counts
     int* cls = nullptr;           // [4][N + 1] column-class flags and positions
@@ -502,9 +541,9 @@ struct hap_sparse {
     bool pending = false;
     int64_t launches = 0;
     bool profile = false;
-    std::vector<cudaEvent_t> ev;   // per profiled iteration: before the bitmap clear, after it, after the row
-                                   // pass, after the short-column and after the long-column statistics
-    double prof_ms[4] = {0, 0, 0, 0};
+    std::vector<cudaEvent_t> ev;   // per profiled iteration: before the row pass, after it, after the
+                                   // column statistics
+    double prof_ms[2] = {0, 0};
     int64_t prof_n = 0;
 };
 
@@ -519,6 +558,8 @@ int sparse_reset(hap_sparse* h) {
     SCU(cudaMemsetAsync(h->tpart, 0, vec, h->stream));
     SCU(cudaMemsetAsync(h->b, 0, (size_t)h->N * ((h->L + 3) & ~3) * 4, h->stream));
     SCU(cudaMemsetAsync(h->rdiag, 0, vec, h->stream));
+    SCU(cudaMemsetAsync(h->cbits, 0, (size_t)2 * h->L * h->cwords * 4, h->stream));
+    h->bm = 0;
     std::vector<float> inf((size_t)h->L * h->N, __builtin_inff());
     SCU(cudaMemcpyAsync(h->tau, inf.data(), vec, cudaMemcpyHostToDevice, h->stream));
     SCU(cudaStreamSynchronize(h->stream));
@@ -542,7 +583,7 @@ int hap_sparse_create(int64_t N, int L, int K, const float* prefs, float damping
     h->K = K;
     h->lam = damping;
     h->c_mode = c_mode;
-    h->cwords = (int64_t)((N * K + 31) / 32);
+    h->cwords = (int64_t)((N * K + 127) / 128) * 4;
     const size_t nk = (size_t)N * K, mat = nk * L * 4, vec = (size_t)L * N * 4;
     bool ok = cudaMalloc(&h->cand, nk * 4) == cudaSuccess && cudaMalloc(&h->s, nk * 4) == cudaSuccess &&
               cudaMalloc(&h->A, mat) == cudaSuccess && cudaMalloc(&h->R, mat) == cudaSuccess &&
@@ -555,7 +596,7 @@ int hap_sparse_create(int64_t N, int L, int K, const float* prefs, float damping
               cudaMalloc(&h->e, (size_t)L * N * 4) == cudaSuccess && cudaMalloc(&h->ns, (size_t)L * (kNsChunks + 1) * 8) == cudaSuccess &&
               cudaMalloc(&h->status, 16) == cudaSuccess && cudaMalloc(&h->pos, nk * 4) == cudaSuccess &&
               cudaMalloc(&h->cval, mat) == cudaSuccess && cudaMalloc(&h->cnt, (N + 1) * 4) == cudaSuccess &&
-              cudaMalloc(&h->cbits, (size_t)L * ((nk + 31) / 32) * 4) == cudaSuccess &&
+              cudaMalloc(&h->cbits, (size_t)2 * L * h->cwords * 4) == cudaSuccess &&
               cudaMalloc(&h->cls, (size_t)4 * (N + 1) * 4) == cudaSuccess &&
               cudaMalloc(&h->long_cols, (size_t)N * 4) == cudaSuccess &&
               cudaMalloc(&h->short_cols, (size_t)N * 4) == cudaSuccess;
@@ -600,17 +641,17 @@ int hap_sparse_set_profile(hap_sparse* h, int on) {
 int hap_sparse_profile_times(hap_sparse* h, double* ms, int64_t* iterations, int reset) {
     if (!h || !ms || !iterations) return HAP_EINVAL;
     SCU(cudaStreamSynchronize(h->stream));
-    for (size_t q = 0; q + 4 < h->ev.size(); q += 5) {
-        for (int k = 0; k < 4; ++k) {
+    for (size_t q = 0; q + 2 < h->ev.size(); q += 3) {
+        for (int k = 0; k < 2; ++k) {
             float t = 0.f;
             SCU(cudaEventElapsedTime(&t, h->ev[q + k], h->ev[q + k + 1]));
             h->prof_ms[k] += t;
         }
         h->prof_n += 1;
-        for (int k = 0; k < 5; ++k) cudaEventDestroy(h->ev[q + k]);
+        for (int k = 0; k < 3; ++k) cudaEventDestroy(h->ev[q + k]);
     }
     h->ev.clear();
-    for (int k = 0; k < 4; ++k) ms[k] = h->prof_ms[k];
+    for (int k = 0; k < 2; ++k) ms[k] = h->prof_ms[k];
     *iterations = h->prof_n;
     if (reset) {
         for (double& v : h->prof_ms) v = 0.0;
@@ -693,7 +734,7 @@ int hap_sparse_set_candidates(hap_sparse* h, const int32_t* cand, const float* X
 int hap_sparse_iterate(hap_sparse* h, int n) {
     if (!h || n < 0) return HAP_EINVAL;
     SparseArgs a;
-    a.cand = h->cand; a.pos = h->pos; a.cval = h->cval; a.cbits = h->cbits; a.cwords = h->cwords;
+    a.cand = h->cand; a.pos = h->pos; a.cval = h->cval; a.cwords = h->cwords;
     a.s = h->s; a.A = h->A; a.R = h->R; a.pref = h->pref; a.c = h->c; a.tau = h->tau;
     a.phi = h->phi; a.tpart = h->tpart; a.b = h->b; a.rdiag = h->rdiag; a.status = h->status;
     a.N = h->N; a.L = h->L; a.K = h->K; a.Lb = (h->L + 3) & ~3; a.lam = h->lam; a.oml = 1.0f - h->lam;
@@ -702,18 +743,27 @@ int hap_sparse_iterate(hap_sparse* h, int n) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int64_t warps = std::min<int64_t>(h->N, (int64_t)sms * 64);
     const unsigned grid = (unsigned)((warps * 32 + 255) / 256);
+    ColArgs ca;
+    ca.cval = h->cval; ca.cwords = h->cwords; ca.cptr = h->cptr; ca.long_cols = h->long_cols;
+    ca.short_cols = h->short_cols; ca.n_long = h->n_long; ca.n_short = h->n_short; ca.N = h->N; ca.L = h->L;
+    ca.K = h->K; ca.c = h->c; ca.phi = h->phi; ca.rdiag = h->rdiag; ca.b = h->b; ca.tpart = h->tpart;
+    ca.long_blocks = (unsigned)(((int64_t)h->L * h->n_long * 32 + 255) / 256);
+    ca.short_blocks = (unsigned)(((int64_t)h->L * h->n_short + 255) / 256);
+    ca.clear_blocks = (unsigned)sms * 2;
+    const size_t bm_words = (size_t)h->L * h->cwords;
     for (int it = 0; it < n; ++it) {
         const int64_t t = h->iter + 1;
         a.pending = h->pending ? 1 : 0;
         a.update_c = (h->c_mode == HAP_C_PAPER && t >= 2) ? 1 : 0;
         a.use_tau = t >= 2 ? 1 : 0;
-        cudaEvent_t ev[5] = {};
+        a.cbits = h->cbits + (size_t)h->bm * bm_words;
+        ca.cbits = a.cbits;
+        ca.clear_bits = h->cbits + (size_t)(h->bm ^ 1) * bm_words;
+        cudaEvent_t ev[3] = {};
         if (h->profile) {
             for (auto& e : ev) SCU(cudaEventCreate(&e));
             SCU(cudaEventRecord(ev[0], h->stream));
         }
-        SCU(cudaMemsetAsync(h->cbits, 0, (size_t)h->L * h->cwords * 4, h->stream));
-        if (h->profile) SCU(cudaEventRecord(ev[1], h->stream));
         if (h->L > 4)
             sparse_rowpass_kernel<true, false><<<grid, 256, 0, h->stream>>>(a);
         else if (h->K == 64)
@@ -721,24 +771,15 @@ int hap_sparse_iterate(hap_sparse* h, int n) {
         else
             sparse_rowpass_kernel<false, false><<<grid, 256, 0, h->stream>>>(a);
         SCU(cudaGetLastError());
-        if (h->profile) SCU(cudaEventRecord(ev[2], h->stream));
-        if (h->n_short > 0) {
-            const int64_t tot = (int64_t)h->L * h->n_short;
-            sparse_colstats_short_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, h->stream>>>(
-                h->cval, h->cbits, h->cwords, h->cptr, h->short_cols, h->n_short, h->N, h->L, h->K, h->c, h->phi, h->rdiag, h->b, h->tpart);
-        }
-        if (h->profile) SCU(cudaEventRecord(ev[3], h->stream));
-        if (h->n_long > 0) {
-            const int64_t tot = (int64_t)h->L * h->n_long * 32;
-            sparse_colstats_long_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, h->stream>>>(
-                h->cval, h->cbits, h->cwords, h->cptr, h->long_cols, h->n_long, h->N, h->L, h->K, h->c, h->phi, h->rdiag, h->b, h->tpart);
-        }
+        if (h->profile) SCU(cudaEventRecord(ev[1], h->stream));
+        sparse_colstats_kernel<<<ca.long_blocks + ca.short_blocks + ca.clear_blocks, 256, 0, h->stream>>>(ca);
         SCU(cudaGetLastError());
         if (h->profile) {
-            SCU(cudaEventRecord(ev[4], h->stream));
-            h->ev.insert(h->ev.end(), ev, ev + 5);
+            SCU(cudaEventRecord(ev[2], h->stream));
+            h->ev.insert(h->ev.end(), ev, ev + 3);
         }
-        h->launches += 1 + (h->n_short > 0) + (h->n_long > 0);
+        h->launches += 2;
+        h->bm ^= 1;
         h->pending = true;
         h->iter = t;
     }

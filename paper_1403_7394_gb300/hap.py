@@ -677,14 +677,14 @@ class HAPSparse:
         check(lib.hap_sparse_set_profile(self._h, int(bool(on))), "hap_sparse_set_profile")
 
     def profile_times(self, reset: bool = True):
-        """({"clear": ms, "row_pass": ms, "short_columns": ms, "long_columns": ms}, iterations) summed
-        over the profiled iterations."""
+        """({"row_pass": ms, "column_statistics": ms}, iterations) summed over
+        the profiled iterations."""
         import numpy as np
-        ms = np.zeros(4, dtype=np.float64)
+        ms = np.zeros(2, dtype=np.float64)
         n = ctypes.c_int64(0)
         check(lib.hap_sparse_profile_times(self._h, ms.ctypes.data_as(ctypes.c_void_p), ctypes.byref(n), int(reset)),
               "hap_sparse_profile_times")
-        return dict(zip(("clear", "row_pass", "short_columns", "long_columns"), ms.tolist())), n.value
+        return dict(zip(("row_pass", "column_statistics"), ms.tolist())), n.value
 
     def set_preferences(self, prefs):
         import numpy as np
