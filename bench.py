@@ -658,12 +658,31 @@ def run_learned(args, world, rank, local):
         p = np.float32(np.median(-np.einsum("kd,kd->k", df, df)))
         return X32, lab, np.array([4.0 * p * (1 + l) for l in range(L)], dtype=np.float32)
 
-    def dense(X32, prefs, **shape):
+    def timed(fn):
+        """fn() on the current stream, with its device time in ms (CUDA events)."""
+        st = torch.cuda.current_stream(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(st)
+        out = fn()
+        b.record(st)
+        torch.cuda.synchronize()
+        return out, a.elapsed_time(b)
+
+    solve_ms = {}
+
+    def dense(X32, prefs, key=None, **shape):
         n = X32.shape[0]
         ctx = hap.HAP(n, L, prefs=prefs, damping=lam, device=dev, c_mode="fixed", **shape)
-        ctx.build_similarity(torch.from_numpy(X32).to(dev), mode="bf16_split")
-        ctx.iterate(T)
-        e = ctx.exemplars()
+        Xg = torch.from_numpy(X32).to(dev)
+
+        def work():  # S build from resident points, T iterations, Eq. 2.8
+            ctx.build_similarity(Xg, mode="bf16_split")
+            ctx.iterate(T)
+            return ctx.exemplars()
+        e, ms = timed(work)
+        if key:
+            solve_ms[key] = ms
         ctx.close()
         return e
 
@@ -693,24 +712,29 @@ def run_learned(args, world, rank, local):
         c.close()
         return g
 
-    def sparse_solve(Xt, prefs, score, k_near, iters, refine=0):
+    def sparse_solve(Xt, prefs, score, k_near, iters, refine=0, key=None):
         n = Xt.shape[0]
-        if score == "mlp":
-            pool, dist_ = hap.knn(Xt, M)
-            f, _ = hap.knn_features(dist_, F)
-            hubs = hap.top_scores(mlp.forward(f), n // HUB_DIV)
-            hubnn, _ = hap.knn_subset(Xt, hubs, K)
-            cand = hap.select_hub_candidates(pool, hubnn, K, k_near)
-        else:
-            pool, _ = hap.knn(Xt, K - 1)
-            cand = hap.select_candidates(pool, K, K - 1, None)
         sp = hap.HAPSparse(n, L, K, prefs=prefs, damping=lam, c_mode="fixed", device=dev)
-        sp.set_candidates(cand, Xt)
-        sp.iterate(iters)
-        for _ in range(refine):
-            sp.set_candidates(hap.refine_candidates(Xt, pool, sp.exemplars(), K, k_near), Xt)
+
+        def work():  # candidates from the points, the sparse solve, Eq. 2.8
+            if score == "mlp":
+                pool, dist_ = hap.knn(Xt, M)
+                f, _ = hap.knn_features(dist_, F)
+                hubs = hap.top_scores(mlp.forward(f), n // HUB_DIV)
+                hubnn, _ = hap.knn_subset(Xt, hubs, K)
+                cand = hap.select_hub_candidates(pool, hubnn, K, k_near)
+            else:
+                pool, _ = hap.knn(Xt, K - 1)
+                cand = hap.select_candidates(pool, K, K - 1, None)
+            sp.set_candidates(cand, Xt)
             sp.iterate(iters)
-        e = sp.exemplars()
+            for _ in range(refine):
+                sp.set_candidates(hap.refine_candidates(Xt, pool, sp.exemplars(), K, k_near), Xt)
+                sp.iterate(iters)
+            return sp.exemplars()
+        e, ms = timed(work)
+        if key:
+            solve_ms[key] = ms
         ns = sp.net_similarity()
         sp.close()
         return e, ns
@@ -720,7 +744,7 @@ def run_learned(args, world, rank, local):
     if args.judge_n:
         Xj, _, pj = instance(args.judge_n, 303 + rank)
         Xjt = torch.from_numpy(Xj).to(dev)
-        e_d = dense(Xj, pj)
+        e_d = dense(Xj, pj, key="dense")
         ptj = torch.from_numpy(np.repeat(pj[:, None], args.judge_n, axis=1)).to(dev)
         ns_d = hap.net_similarity_points(Xjt, e_d, ptj)
         ed = e_d.cpu().numpy()
@@ -737,11 +761,13 @@ def run_learned(args, world, rank, local):
         if REFINE:
             arms.append(("learned_first_solve", "mlp", K_NEAR, 0))
         for name, sc, kn, rf in arms:
-            e_s, ns_s = sparse_solve(Xjt, pj, sc, kn, T, rf)
+            e_s, ns_s = sparse_solve(Xjt, pj, sc, kn, T, rf, key=name)
             es = e_s.cpu().numpy()
             judge[name] = {"ns_gap_level1": float((ns_d[0] - ns_s[0]) / abs(ns_d[0])),
                            "ari_level1": ari(es[0], ed[0]),
-                           "exemplars_level1": int(len(np.unique(es[0])))}
+                           "exemplars_level1": int(len(np.unique(es[0]))),
+                           "solve_ms": solve_ms[name], "speedup_vs_dense": solve_ms["dense"] / solve_ms[name]}
+        judge["dense_solve_ms"] = solve_ms["dense"]
 
     # timed: the whole learned-sparse pipeline at full N (the sparse context's
     # buffers are allocated once, like any solver workspace)
