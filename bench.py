@@ -74,6 +74,8 @@ def parse():
     ap.add_argument("--iters", type=int, default=0, help="override the iteration count")
     ap.add_argument("--n", type=int, default=0, help="first n points only (a smaller case for profiling)")
     ap.add_argument("--instances", type=int, default=0, help="first B instances only (batched; for profiling)")
+    ap.add_argument("--uniform-n", type=int, default=0,
+                    help="batched: every instance of this size with L = 3 (a batch of one size class)")
     ap.add_argument("--cpu-baseline", type=int, default=1)
     ap.add_argument("--e2e-steps", type=int, default=2)
     for k in ("block_threads", "cluster_size", "grid_clusters", "elems_per_thread", "ctas_per_sm"):
@@ -530,7 +532,11 @@ def run_batched(args, world, rank, local):
     B, d, T, desc = BATCHED[args.workload]
     if args.iters:
         T = args.iters
-    insts = W.batch_instances(B, d=d, seed=rank)
+    if args.uniform_n:
+        insts = W.batch_instances(B, n_range=(args.uniform_n, args.uniform_n), levels=(3,), d=d, seed=rank)
+        desc = f"{B} instances of N={args.uniform_n}, L=3, d={d} GMMs (5-50 components each), {T} iterations"
+    else:
+        insts = W.batch_instances(B, d=d, seed=rank)
     if args.instances:
         B = min(B, args.instances)
         insts = insts[:B]
