@@ -278,8 +278,8 @@ int hap_row_pass_time(hap_ctx* ctx, double* ms, int64_t* launches, int reset);
  * schedule as hap_iterate (data-parallel schedule, kappa = 0).  The context
  * allocates its own device memory (hap_batch_destroy frees it).
  *   N, L   host arrays of B entries.
- * Options used: c_mode, s_dtype (opt may be NULL); another schedule or
- * kappa != 0 gives HAP_EUNSUPPORTED. */
+ * Options used: c_mode, s_dtype, wait_limit_ns (opt may be NULL); another
+ * schedule or kappa != 0 gives HAP_EUNSUPPORTED. */
 typedef struct hap_batch hap_batch;
 int hap_batch_create(int B, const int64_t* N, const int* L, float damping, const hap_options* opt,
                      hap_batch** out);
@@ -316,7 +316,16 @@ int hap_batch_tune(hap_batch* batch, double* best_ms);
  * L[b] <= 8, else HAP_EUNSUPPORTED).  Resets the messages.  Synchronising. */
 int hap_batch_set_tile(hap_batch* batch, int elems_per_thread);
 int hap_batch_query(hap_batch* batch, int key, int64_t* value);
+/* Waits for the bound stream and checks the device status word: every wait
+ * of the batched row pass gives up after the wait limit (hap_options.
+ * wait_limit_ns at creation, or hap_batch_set_wait_limit) and reports
+ * HAP_ETIMEOUT; the messages are then undefined until hap_batch_set_similarity
+ * or hap_batch_build_similarity gives the batch a new state (which clears
+ * the report). */
 int hap_batch_sync(hap_batch* batch);
+/* Changes the wait limit (ns >= 1; 0 = 2 s) for the following iterations.
+ * Host call. */
+int hap_batch_set_wait_limit(hap_batch* batch, int64_t ns);
 
 /* ---- row bands ---------------------------------------------------------------
  * One HAP problem split by rows (§3: MR-HAP keys the responsibility job by

@@ -69,6 +69,7 @@ struct BatchArgs {
     unsigned* status;
     float lam, oml;
     int pending, update_c, use_tau;
+    uint64_t wait_ns;      // limit of every bounded wait
 };
 
 size_t batched_smem_bytes(int K, int s_elem) {
@@ -169,7 +170,12 @@ __global__ void __launch_bounds__(kBT, 1) rowpass_batched_kernel(const BatchArgs
         const int nrows = min(in.rps, in.N - i0);
         const int st = issued % NST;
         // the stage's previous contents (step issued - NST) must be released by every warp
-        if (issued >= NST && !bad) bad = !mbar_wait(empty0 + 8 * st, (uint32_t)((issued / NST - 1) & 1), p.status);
+        if (issued >= NST && !bad) bad = !mbar_wait(empty0 + 8 * st, (uint32_t)((issued / NST - 1) & 1), p.status, p.wait_ns);
+        // after a wait gave up nothing more is issued (the stage may still be read)
+        if (bad) {
+            *prod = c;
+            return false;
+        }
         const uint32_t bar = full0 + 8 * st, dst = sm0 + (uint32_t)st * STAGE;
         const bool load_s = l == 0;
         const uint32_t n = (uint32_t)nrows * (uint32_t)in.ld;
@@ -188,7 +194,8 @@ __global__ void __launch_bounds__(kBT, 1) rowpass_batched_kernel(const BatchArgs
             if (!issue_next()) break;
     __syncthreads();  // the first claimed item is in fifo[0]
 
-    int step = 0;  // consumer step counter of this CTA (ring position)
+    int step = 0;    // consumer step counter of this CTA (ring position)
+    int waited = 0;  // steps whose copies this thread saw land
     for (int kit = 0;; ++kit) {
         // read by every thread after a CTA barrier: the item is CTA-uniform
         const int it = fifo[kit % F];
@@ -252,7 +259,10 @@ __global__ void __launch_bounds__(kBT, 1) rowpass_batched_kernel(const BatchArgs
             const float* sA = reinterpret_cast<const float*>(base) + (size_t)rr0 * ld;
             const float* sR = reinterpret_cast<const float*>(base + A_BYTES) + (size_t)rr0 * ld;
             const ST* sS = reinterpret_cast<const ST*>(base + 2 * A_BYTES) + (size_t)rr0 * ld;
-            if (!bad) bad = !mbar_wait(full0 + 8 * st, (uint32_t)(step / NST) & 1u, p.status);
+            if (!bad) {
+                bad = !mbar_wait(full0 + 8 * st, (uint32_t)(step / NST) & 1u, p.status, p.wait_ns);
+                if (!bad) ++waited;
+            }
             const int64_t voff = (int64_t)l * ld;
             const int64_t off = ((int64_t)l * N + row) * ld;
 
@@ -378,6 +388,13 @@ __global__ void __launch_bounds__(kBT, 1) rowpass_batched_kernel(const BatchArgs
         // work uniformly (the status word already records it).
         if (__syncthreads_or(bad)) break;
     }
+    // After a wait gave up: every bulk copy this CTA issued lands before it
+    // leaves (thread 0 issued them all and saw the first `waited` land; each
+    // stage has at most one copy in flight, since a stage is re-armed only
+    // after its previous copy was consumed).
+    if (tid == 0)
+        for (int q = waited; q < prod->issued; ++q)
+            mbar_wait(full0 + 8 * (q % NST), (uint32_t)(q / NST) & 1u, p.status, kWaitNs);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -628,7 +645,10 @@ int schedule(hap_batch* h) {
     return HAP_OK;
 }
 
+// Algorithm 1's initial values for every instance; clears a reported device
+// error.
 int batch_reset(hap_batch* h) {
+    BCU(cudaMemsetAsync(h->status, 0, 16, h->stream));
     for (int b = 0; b < h->B; ++b) {
         const BInst& in = h->inst[b];
         const size_t mat = (size_t)in.L * in.N * in.ld * 4, vec = (size_t)in.L * in.ld * 4;
@@ -658,6 +678,7 @@ cudaError_t launch_batched_iteration(hap_batch* h, int pending, int update_c, in
     cudaError_t err0 = cudaMemsetAsync(h->d_counter, 0, sizeof(int), st);
     if (err0 != cudaSuccess) return err0;
     a.status = h->status;
+    a.wait_ns = h->opt.wait_limit_ns > 0 ? (uint64_t)h->opt.wait_limit_ns : 2000000000ull;
     a.lam = h->lam;
     a.oml = 1.0f - h->lam;
     a.pending = pending;
@@ -1056,6 +1077,16 @@ int hap_batch_query(hap_batch* h, int key, int64_t* value) {
         case HAP_Q_ELEMS_PER_THREAD: *value = 4 * h->K; return HAP_OK;
         default: return HAP_EINVAL;
     }
+}
+
+int hap_batch_set_wait_limit(hap_batch* h, int64_t ns) {
+    if (!h || ns < 0) return HAP_EINVAL;
+    h->opt.wait_limit_ns = ns;
+    if (h->graph) {  // the captured launches carry the old limit
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
+    return HAP_OK;
 }
 
 int hap_batch_sync(hap_batch* h) {

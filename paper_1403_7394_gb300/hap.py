@@ -74,6 +74,7 @@ def _load():
         "hap_batch_get_state": (i32, [vp, i32, vp, vp, vp, ctypes.POINTER(i64)]),
         "hap_batch_tune": (i32, [vp, ctypes.POINTER(ctypes.c_double)]),
         "hap_batch_set_tile": (i32, [vp, i32]),
+        "hap_batch_set_wait_limit": (i32, [vp, i64]),
         "hap_batch_query": (i32, [vp, i32, ctypes.POINTER(i64)]),
         "hap_batch_sync": (i32, [vp]),
         "hap_knn": (i32, [vp, i64, i64, i32, vp, vp, vp]),
@@ -421,6 +422,10 @@ class HAPBatch:
         ms = ctypes.c_double(0.0)
         check(lib.hap_batch_tune(self._h, ctypes.byref(ms)), "hap_batch_tune")
         return ms.value
+
+    def set_wait_limit(self, ns: int):
+        """Limit of the batched row pass's bounded device waits, in ns (0 = 2 s)."""
+        check(lib.hap_batch_set_wait_limit(self._h, int(ns)), "hap_batch_set_wait_limit")
 
     def set_tile(self, elems_per_thread: int):
         """Columns per thread of the row pass (16 or 8); resets the messages."""

@@ -6,6 +6,11 @@
   context stays usable: the same library context, given its default limit
   and a new state, then runs bit for bit like a fresh one.  Cluster size 1
   only: the expiry path there involves no peer CTA.
+* The batched row pass (one persistent launch over many instances) the same
+  way: with a 1 ns limit its waits give up, nothing more is issued, every CTA
+  lets its own copies land and leaves; HAP_ETIMEOUT is reported and the batch,
+  given its default limit and new similarities, runs bit for bit like a fresh
+  one.
 * debug_bounds: a non-finite similarity is refused (HAP_EINVAL), and the row
   pass's index checks change no bit of the result.
 """
@@ -50,6 +55,41 @@ def test_wait_expiry_reports_timeout_and_the_context_recovers(opt):
     fresh.iterate(4)
     _states_equal(ctx, fresh)
     ctx.close()
+    fresh.close()
+
+
+def test_batched_wait_expiry_reports_timeout_and_the_batch_recovers():
+    hap = hap_mod()
+    Ns, Ls = [1500, 700, 3000, 90], [3, 2, 2, 4]
+    probs = [problem(n, l, seed=20 + q) for q, (n, l) in enumerate(zip(Ns, Ls))]
+
+    def make():
+        bt = hap.HAPBatch(Ns, Ls, damping=0.5, device=DEV)
+        bt.set_preferences([p[1] for p in probs])
+        for b, p in enumerate(probs):
+            bt.set_similarity(b, torch.from_numpy(p[0]).to(DEV))
+        return bt
+
+    bt = make()
+    bt.set_wait_limit(1)
+    bt.iterate(3)  # a direct launch, then graph replays carrying the 1 ns limit
+    with pytest.raises(hap.HapError) as err:
+        bt.sync()
+    assert err.value.code == HAP_ETIMEOUT
+    torch.cuda.synchronize()  # no sticky CUDA error: every CTA returned
+    bt.set_wait_limit(0)
+    for b, p in enumerate(probs):  # a new state clears the report
+        bt.set_similarity(b, torch.from_numpy(p[0]).to(DEV))
+    bt.iterate(4)
+    bt.sync()
+    fresh = make()
+    fresh.iterate(4)
+    fresh.sync()
+    for b in range(len(Ns)):
+        ga, gb = bt.get_state(b), fresh.get_state(b)
+        for k in ("A", "R", "c", "tau", "phi"):
+            assert torch.equal(ga[k], gb[k]), (b, k)
+    bt.close()
     fresh.close()
 
 
