@@ -341,13 +341,13 @@ __global__ void __launch_bounds__(kBT, 1) rowpass_batched_kernel(const BatchArgs
                 float4 s4 = (ok[k] && rv) ? srow[k] : f4_splat(0.f);
                 const int dd = row - col[k];
                 if ((unsigned)dd < 4u) f4_set(s4, dd, pref_i);
-                float4 rn;
-                rn.x = damp(r4.x, __fadd_rn(s4.x, mm1), lam, oml);
-                rn.y = damp(r4.y, __fadd_rn(s4.y, mm1), lam, oml);
-                rn.z = damp(r4.z, __fadd_rn(s4.z, mm1), lam, oml);
-                rn.w = damp(r4.w, __fadd_rn(s4.w, mm1), lam, oml);
+                // min(tau, -max_{k != j}): mm2 at the row's argmax k1, mm1 elsewhere
                 const int dk = k1 - col[k];
-                if ((unsigned)dk < 4u) f4_set(rn, dk, damp(f4_get(r4, dk), __fadd_rn(f4_get(s4, dk), mm2), lam, oml));
+                float4 rn;
+                rn.x = damp(r4.x, __fadd_rn(s4.x, dk == 0 ? mm2 : mm1), lam, oml);
+                rn.y = damp(r4.y, __fadd_rn(s4.y, dk == 1 ? mm2 : mm1), lam, oml);
+                rn.z = damp(r4.z, __fadd_rn(s4.z, dk == 2 ? mm2 : mm1), lam, oml);
+                rn.w = damp(r4.w, __fadd_rn(s4.w, dk == 3 ? mm2 : mm1), lam, oml);
                 float4 add = make_float4(fmaxf(rn.x, 0.f), fmaxf(rn.y, 0.f), fmaxf(rn.z, 0.f), fmaxf(rn.w, 0.f));
                 if (!(ok[k] && rv)) add = f4_splat(0.f);
                 if ((unsigned)dd < 4u) {
