@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--c-mode", default="paper", choices=["paper", "fixed"],
                     help="Eq. 2.6 applied every iteration (paper) or c held at 0 (fixed)")
     ap.add_argument("--judge-n", type=int, default=32768, help="dense-vs-sparse judging size (learned workload)")
+    ap.add_argument("--hub-div", type=int, default=HUB_DIV, help="learned workload: hubs = N / hub-div")
+    ap.add_argument("--judge-seed", type=int, default=303, help="learned workload: seed of the judging instance")
     ap.add_argument("--judge-full", type=int, default=1,
                     help="judge the learned candidates against exact-kNN ones at full N (learned workload)")
     ap.add_argument("--sbuild", default="bf16_split", choices=["bf16_split", "bf16", "f32"])
@@ -652,6 +654,7 @@ def run_learned(args, world, rank, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     N, d, L, K, T, desc = LEARNED[args.workload]
+    desc = desc.replace("the N/%d points" % HUB_DIV, "the N/%d points" % args.hub_div)
     if args.iters:
         T = args.iters
     lam, M, F = 0.9, 16, 16  # kNN pool of 16 (the features use all 16 distances)
@@ -726,7 +729,7 @@ def run_learned(args, world, rank, local):
             if score == "mlp":
                 pool, dist_ = hap.knn(Xt, M)
                 f, _ = hap.knn_features(dist_, F)
-                hubs = hap.top_scores(mlp.forward(f), n // HUB_DIV)
+                hubs = hap.top_scores(mlp.forward(f), n // args.hub_div)
                 hubnn, _ = hap.knn_subset(Xt, hubs, K)
                 cand = hap.select_hub_candidates(pool, hubnn, K, k_near)
             else:
@@ -748,7 +751,7 @@ def run_learned(args, world, rank, local):
     # judging at --judge-n: dense HAP vs learned / nearest-neighbour candidates
     judge = {}
     if args.judge_n:
-        Xj, _, pj = instance(args.judge_n, 303 + rank)
+        Xj, _, pj = instance(args.judge_n, args.judge_seed + rank)
         Xjt = torch.from_numpy(Xj).to(dev)
         e_d = dense(Xj, pj, key="dense")
         ptj = torch.from_numpy(np.repeat(pj[:, None], args.judge_n, axis=1)).to(dev)
@@ -792,7 +795,7 @@ def run_learned(args, world, rank, local):
     def step(e_buf):
         pool, dist_ = hap.knn(Xt, M)
         f, _ = hap.knn_features(dist_, F)
-        hubnn, _ = hap.knn_subset(Xt, hap.top_scores(mlp.forward(f), N // HUB_DIV), K)
+        hubnn, _ = hap.knn_subset(Xt, hap.top_scores(mlp.forward(f), N // args.hub_div), K)
         sp.set_candidates(hap.select_hub_candidates(pool, hubnn, K, K_NEAR), Xt)
         sp.iterate(T)
         for _ in range(REFINE):
@@ -883,7 +886,7 @@ def run_learned(args, world, rank, local):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": args.workload, "desc": desc, "N": N, "K": K, "L": L, "iters": T,
                        "updates_counted": "sparse N*K*L per iteration, %d solves of %d iterations" % (1 + REFINE, T),
-                       "hubs": "N/%d" % HUB_DIV, "near": K_NEAR, "refinement_solves": REFINE, "knn_ms": knn_ms,
+                       "hubs": "N/%d" % args.hub_div, "judge_seed": args.judge_seed, "near": K_NEAR, "refinement_solves": REFINE, "knn_ms": knn_ms,
                        "sparse_iteration_ms": it_ms, "sparse_step_ms": steps_ms, "train_s": t_train, "train_loss": loss, "judge": judge,
                        "judge_full_n": full_n},
             "e2e": {"value": world * max(1, args.e2e_steps) * updates / e2e_s, "unit": "updates/s",
