@@ -68,6 +68,7 @@ def parse():
                     help="Eq. 2.6 applied every iteration (paper) or c held at 0 (fixed)")
     ap.add_argument("--judge-n", type=int, default=32768, help="dense-vs-sparse judging size (learned workload)")
     ap.add_argument("--hub-div", type=int, default=HUB_DIV, help="learned workload: hubs = N / hub-div")
+    ap.add_argument("--near", type=int, default=K_NEAR, help="learned workload: nearest neighbours kept besides the hubs")
     ap.add_argument("--judge-seed", type=int, default=303, help="learned workload: seed of the judging instance")
     ap.add_argument("--judge-full", type=int, default=1,
                     help="judge the learned candidates against exact-kNN ones at full N (learned workload)")
@@ -655,6 +656,8 @@ def run_learned(args, world, rank, local):
     dev = torch.device("cuda", local)
     N, d, L, K, T, desc = LEARNED[args.workload]
     desc = desc.replace("the N/%d points" % HUB_DIV, "the N/%d points" % args.hub_div)
+    desc = desc.replace("its %d nearest neighbours and its %d nearest hubs" % (K_NEAR, K - 1 - K_NEAR),
+                        "its %d nearest neighbours and its %d nearest hubs" % (args.near, K - 1 - args.near))
     if args.iters:
         T = args.iters
     lam, M, F = 0.9, 16, 16  # kNN pool of 16 (the features use all 16 distances)
@@ -766,9 +769,9 @@ def run_learned(args, world, rank, local):
         judge["dense_other_order"] = {"ns_gap_level1": float((ns_d[0] - ns_d2[0]) / abs(ns_d[0])),
                                       "ari_level1": ari(ed2[0], ed[0]),
                                       "exemplars_level1": int(len(np.unique(ed2[0])))}
-        arms = [("learned", "mlp", K_NEAR, REFINE), ("knn", None, K - 1, 0)]
+        arms = [("learned", "mlp", args.near, REFINE), ("knn", None, K - 1, 0)]
         if REFINE:
-            arms.append(("learned_first_solve", "mlp", K_NEAR, 0))
+            arms.append(("learned_first_solve", "mlp", args.near, 0))
         for name, sc, kn, rf in arms:
             e_s, ns_s = sparse_solve(Xjt, pj, sc, kn, T, rf, key=name)
             es = e_s.cpu().numpy()
@@ -796,11 +799,11 @@ def run_learned(args, world, rank, local):
         pool, dist_ = hap.knn(Xt, M)
         f, _ = hap.knn_features(dist_, F)
         hubnn, _ = hap.knn_subset(Xt, hap.top_scores(mlp.forward(f), N // args.hub_div), K)
-        sp.set_candidates(hap.select_hub_candidates(pool, hubnn, K, K_NEAR), Xt)
+        sp.set_candidates(hap.select_hub_candidates(pool, hubnn, K, args.near), Xt)
         sp.iterate(T)
         for _ in range(REFINE):
             sp.exemplars(e_mid)
-            sp.set_candidates(hap.refine_candidates(Xt, pool, e_mid, K, K_NEAR), Xt)
+            sp.set_candidates(hap.refine_candidates(Xt, pool, e_mid, K, args.near), Xt)
             sp.iterate(T)
         sp.exemplars(e_buf)
         return sp.net_similarity()
@@ -886,7 +889,7 @@ def run_learned(args, world, rank, local):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": args.workload, "desc": desc, "N": N, "K": K, "L": L, "iters": T,
                        "updates_counted": "sparse N*K*L per iteration, %d solves of %d iterations" % (1 + REFINE, T),
-                       "hubs": "N/%d" % args.hub_div, "judge_seed": args.judge_seed, "near": K_NEAR, "refinement_solves": REFINE, "knn_ms": knn_ms,
+                       "hubs": "N/%d" % args.hub_div, "judge_seed": args.judge_seed, "near": args.near, "refinement_solves": REFINE, "knn_ms": knn_ms,
                        "sparse_iteration_ms": it_ms, "sparse_step_ms": steps_ms, "train_s": t_train, "train_loss": loss, "judge": judge,
                        "judge_full_n": full_n},
             "e2e": {"value": world * max(1, args.e2e_steps) * updates / e2e_s, "unit": "updates/s",
