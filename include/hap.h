@@ -349,6 +349,9 @@ int hap_batch_set_wait_limit(hap_batch* batch, int64_t ns);
  *   N       points of the whole problem (2 .. 65536); L levels (1 .. 16)
  *   row0, nrows  the band's rows, 0 <= row0, 1 <= nrows, row0 + nrows <= N
  *   prefs   host [L] preferences, or NULL for 0
+ *   damping lambda in (0, 1), as for hap_create
+ * The messages start at Algorithm 1's initial values; creation is
+ * synchronising.
  * Options: c_mode, s_dtype, launch-shape fields, wait_limit_ns; the level
  * schedule must be JACOBI, kappa 0, s_per_level and debug_bounds 0 (else
  * HAP_EUNSUPPORTED). */
